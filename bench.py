@@ -1,0 +1,349 @@
+"""Benchmark: one Cool-chic overfitting iteration (forward, backward, Adam) over all pixels
+of a 512x768 synthetic image with the 2300-MAC decoder, on the CUDA library.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one iteration over the whole image.  `value` is whole-job throughput in
+Mpixel-iterations/s with the state resident in HBM, each iteration timed with CUDA events
+on the library's stream and L2 flushed (256 MB write) between timed iterations.  Under
+torchrun each rank overfits its own image (independent replicas, weak scaling); the time
+is the max over ranks.  `e2e` runs the same iterations through the C ABI with host
+buffers: each step uploads the image from pinned host memory and reads the step's loss
+back.  `--impl reference` times the FP64 CPU oracle on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encode Mpixel-iter/s (fwd+bwd+Adam) vs plain; s to RD-cost within 1% of plain"
+UNIT = "Mpixel-iter/s"
+PAPER_DERIVED_MPXIT = 22.5   # 512x768, 2300-MAC, 102 950 iterations in ~30 min (Sec. V, Fig. 5)
+FP32_LANES_PER_SM = 128
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def workload(cfgd):
+    return {"workload": f"{cfgd['H']}x{cfgd['W']} synthetic image, 2300-MAC decoder "
+                        f"(ARM 24-24-24-2, per-level 8x8 upsampling, synthesis 7-40-3 + 2 x 3x3 "
+                        f"residual), lambda {cfgd['lam']}, one iteration per step",
+            "H": cfgd["H"], "W": cfgd["W"], "lam": cfgd["lam"],
+            "arm": "24-24-24-2", "synthesis": "7-40-3 + 2x3x3", "upsampling": "8x8 per level",
+            "l2": "flushed between timed iterations (256 MB write)",
+            "parallelism": "independent replicas, one image per GPU"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def arm_flops_per_launch(cfgd, n_lat):
+    """Algorithmic FLOPs of the ARM kernel: forward, input gradient, weight gradient."""
+    n, nl = cfgd["arm_ctx"], cfgd["arm_layers"]
+    mac = nl * n * n + 2 * n
+    return 3 * 2 * mac * n_lat
+
+
+def decoder_macs_per_pixel(cfgd, H, W):
+    """kappa_dec of the configuration for this image (eq. (2) counts 3 kappa_dec / iteration)."""
+    shapes = [(-(-H // (1 << l)), -(-W // (1 << l))) for l in range(7)]
+    n, nl, k, c = cfgd["arm_ctx"], cfgd["arm_layers"], cfgd["up_kernel"], cfgd["syn_hidden"]
+    lat = sum(h * w for h, w in shapes)
+    ups = sum(sum(shapes[j][0] * shapes[j][1] for j in range(l)) for l in range(1, 7))
+    macs = (nl * n * n + 2 * n) * lat + (k // 2) ** 2 * ups + (7 * c + 3 * c + 81 * cfgd["syn_res3x3"]) * H * W
+    return macs / (H * W)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def oracle_rate(cfgd, budget_s, H, W, seed=0, max_iters=None):
+    """Time FP64 oracle iterations on an H x W image until budget_s is used (>= 1 timed)."""
+    import torch
+    from oracle import coolchic as oc
+    from paper_2403_11651_gb300 import synthetic as syn
+    arch = oc.Arch(arm_ctx=cfgd["arm_ctx"], arm_layers=cfgd["arm_layers"],
+                   up_kernel=cfgd["up_kernel"], up_per_level=cfgd["up_per_level"],
+                   syn_hidden=cfgd["syn_hidden"], syn_res3x3=cfgd["syn_res3x3"])
+    enc = oc.OracleEncoder(syn.synthetic_image(H, W, seed), arch,
+                           oc.Train(lam=cfgd["lam"], lr=cfgd["lr"], total_iters=cfgd["total_iters"],
+                                    ste_frac=cfgd["ste_frac"], seed=seed),
+                           syn.initial_parameters(syn.ArchSizes.from_config(cfgd), seed))
+    enc.step()  # warm-up
+    n, t0 = 0, time.perf_counter()
+    while True:
+        enc.step()
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= budget_s or (max_iters and n >= max_iters):
+            break
+    return H * W * n / dt / 1e6, n, dt, torch.get_num_threads()
+
+
+def run_reference(a, cfgd):
+    rank, _, world = dist_env()
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("gloo")
+        if rank != 0:
+            td.barrier()
+            td.destroy_process_group()
+            return
+    H, W = cfgd["H"], cfgd["W"]
+    # calibrate one full-size iteration, then size each step's sample so the run fits ~150 s
+    v_full, _, dt_full, _ = oracle_rate(cfgd, 0.0, H, W, max_iters=1)
+    per_step = 150.0 / max(1, a.steps + a.warmup)
+    frac = min(1.0, per_step / dt_full)
+    h = max(16, int(round(H * frac ** 0.5 / 16)) * 16)
+    w = max(16, int(round(W * frac ** 0.5 / 16)) * 16)
+    import torch
+    from oracle import coolchic as oc
+    from paper_2403_11651_gb300 import synthetic as syn
+    arch = oc.Arch(arm_ctx=cfgd["arm_ctx"], arm_layers=cfgd["arm_layers"],
+                   up_kernel=cfgd["up_kernel"], up_per_level=cfgd["up_per_level"],
+                   syn_hidden=cfgd["syn_hidden"], syn_res3x3=cfgd["syn_res3x3"])
+    enc = oc.OracleEncoder(syn.synthetic_image(h, w, 0), arch,
+                           oc.Train(lam=cfgd["lam"], lr=cfgd["lr"], total_iters=cfgd["total_iters"],
+                                    ste_frac=cfgd["ste_frac"], seed=0),
+                           syn.initial_parameters(syn.ArchSizes.from_config(cfgd), 0))
+    for _ in range(a.warmup):
+        enc.step()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        enc.step()
+    dt = time.perf_counter() - t0
+    v = h * w * a.steps / dt / 1e6
+    sample = (f"each step: one FP64 oracle iteration (fwd+bwd+Adam) on a {h}x{w} crop-size "
+              f"synthetic image of the same generator and decoder")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload(cfgd),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": torch.get_num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as td
+        td.barrier()
+        td.destroy_process_group()
+
+
+def run_ours(a, cfgd):
+    import torch
+    from paper_2403_11651_gb300 import coolchic as cc
+    from paper_2403_11651_gb300 import synthetic as syn
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    td = None
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl", device_id=dev)
+    H, W = cfgd["H"], cfgd["W"]
+    cfg = cc.make_config(cfgd, seed=rank)
+    rgb = syn.synthetic_image(H, W, rank)
+    init = cc.flatten_params(syn.initial_parameters(syn.ArchSizes.from_config(cfgd), rank), cfg)
+    n_lat = cc.cc_latent_count(cfg, H, W)
+    stream = torch.cuda.current_stream(dev)
+    ws_bytes = cc.cc_workspace_size(cfg, H, W)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    ctx = cc.cc_init_image_ws(cfg, torch.from_numpy(rgb).to(dev), H, W,
+                              torch.from_numpy(init).to(dev), stream, ws, ws_bytes)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if td:
+            td.barrier()
+        torch.cuda.synchronize(dev)
+
+    cc.cc_encode_iters(ctx, a.warmup)
+    kernels = cc.cc_graph_kernel_count(ctx)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    barrier()
+    with ClockSampler(local) as clk:
+        for k in range(a.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            cc.cc_encode_iters(ctx, 1)
+            ends[k].record(stream)
+        barrier()
+        total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+        # dominant kernel (ARM + rate, forward and backward), timed live with CUDA events
+        phases = cc.cc_profile_phases(ctx, max(3, min(20, a.steps)))
+    clocks = clk.summary()
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if td:
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * H * W * a.steps / (total_ms / 1e3) / 1e6
+
+    # end to end through the C ABI with host buffers
+    pinned = torch.from_numpy(rgb).pin_memory()
+    n_e2e = max(3, min(a.steps, 200))
+    barrier()
+    t0 = time.perf_counter()
+    last = None
+    for k in range(n_e2e):
+        cc.cc_set_image(ctx, pinned)
+        cc.cc_encode_iters(ctx, 1)
+        it = cc.cc_iteration(ctx)
+        last = cc.cc_get_losses(ctx, it - 1, 1)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if td:
+        td.all_reduce(te, op=td.ReduceOp.MAX)
+    e2e_value = world * H * W * n_e2e / float(te.item()) / 1e6
+
+    # the full schedule once, for time to the final RD cost of the plain method
+    ctx2 = cc.cc_init_image(cfg, rgb, H, W, init, stream)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    cc.cc_encode_iters(ctx2, cfgd["total_iters"])
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    full_s = ev0.elapsed_time(ev1) / 1e3
+    final = cc.cc_rd_cost(ctx2, True)
+    cc.cc_free(ctx2)
+
+    pk, src = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    clk_max = float(pk.get("sm_max_mhz", 2070.0))
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * clk_max * 1e6 / 1e12
+    arm_ms = float(phases[1])
+    arm_tflops = arm_flops_per_launch(cfgd, n_lat) / (arm_ms / 1e3) / 1e12
+    kappa = decoder_macs_per_pixel(cfgd, H, W)
+    it_ms = total_ms / a.steps
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": it_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_DERIVED_MPXIT / world if world else None,
+        "dtype": "f32", "data": "synthetic", "config": workload(cfgd),
+        "roofline": {"bound": "alu", "kernel": "k_arm<24,2,true> (ARM + rate, fwd+bwd)",
+                     "achieved": arm_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": arm_tflops / peak_tflops, "traffic": None,
+                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {clk_max:.0f} MHz "
+                                   f"(sm_max_mhz, {src})",
+                     "arm_ms": arm_ms,
+                     "phase_ms": {n: float(v) for n, v in zip(cc.PHASES, phases)}},
+        "whole_iteration": {"flop_per_pixel_iter": 6 * kappa,
+                            "tflops": 6 * kappa * H * W / (it_ms / 1e3) / 1e12,
+                            "frac_of_alu_peak": 6 * kappa * H * W / (it_ms / 1e3) / 1e12 / peak_tflops},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * H * W,
+                "d2h_bytes_per_step": 24, "steps": n_e2e},
+        "gpu_launches": kernels * a.steps,
+        "time_to_final_rd_s": {"iters": cfgd["total_iters"], "seconds": full_s,
+                               "final_hard_rd": {"D": final[0], "R_bpp": final[1],
+                                                 "cost": final[2]}},
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        v, n, dt, cores = oracle_rate(cfgd, 15.0, H, W)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"{n} FP64 oracle iterations (fwd+bwd+Adam) on the "
+                                         f"full {H}x{W} image, {dt:.1f} s"}
+    cc.cc_free(ctx)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if td:
+        td.barrier()
+        td.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    a = ap.parse_args()
+    if a.warmup < 3:
+        a.warmup = 3
+    with open(os.path.join(ROOT, "paper_2403_11651_gb300", "configs", a.config + ".json")) as f:
+        cfgd = json.load(f)
+    if a.impl == "reference":
+        run_reference(a, cfgd)
+    else:
+        run_ours(a, cfgd)
+
+
+if __name__ == "__main__":
+    main()

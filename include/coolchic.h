@@ -1,0 +1,184 @@
+/*
+ * coolchic.h -- C ABI of the GB300 (sm_103a) Cool-chic overfitting library.
+ *
+ * One call of cc_encode_iters runs n iterations of the encoder optimisation of
+ * Blard et al., "Overfitted image coding at reduced complexity", Sec. II, eq. (1):
+ *
+ *     min over (y, psi, upsilon, theta) of  D(x, f_theta(f_upsilon(Q(y)))) + lambda R(Q(y)),
+ *     R = -log2 p_psi(Q(y)),
+ *
+ * where y is the L = 7 level latent pyramid (Sec. II "Decoding" item i), p_psi the
+ * auto-regressive probability model (item ii), f_upsilon the learned 2x upsampling and
+ * f_theta the synthesis (item iii), with the layer lists of Table 1.  One iteration is the
+ * forward pass, its backward pass (Sec. IV-A, "Shorter training": weight and input
+ * gradients of every layer) and one Adam update of every latent and parameter.
+ *
+ * Conventions for every entry point:
+ *   - return 0 (CC_OK) on success, a negative CC_E* code otherwise; nothing throws;
+ *   - pointers documented "host or device" may point to either (CUDA unified addressing);
+ *   - input buffers stay owned by the caller and are copied in before the call returns
+ *     (or, for asynchronous calls, before any later call on the same context);
+ *   - the context owns its device memory (or borrows a caller workspace) until cc_free;
+ *   - all GPU work of a context is issued on the stream given to cc_init_image;
+ *   - the images are 8-bit RGB, row-major, channels last (H x W x 3); the library uses
+ *     x = v / 255 in float32.
+ *
+ * Flat parameter order (cc_get_state, cc_get_grads, init_params):
+ *   ARM:        for i < arm_layers: W_i (N x N, row-major out x in), b_i (N);
+ *               W_out (2 x N), b_out (2)                 -- outputs (mu, log-scale)
+ *   upsampling: one k x k filter per level l = 1..L-1 (up_per_level = 1) or one shared
+ *               filter (up_per_level = 0), row-major
+ *   synthesis:  W_a (C x L), b_a (C), W_b (3 x C), b_b (3),
+ *               for each 3x3 layer: W (3 out x 3 in x 3 x 3), b (3)
+ * Flat latent order: level 0 .. L-1, each level row-major, ceil(H/2^l) x ceil(W/2^l).
+ *
+ * Device memory per 512 x 768 image with the 2300-MAC decoder: about 120 MB.
+ */
+#ifndef COOLCHIC_H
+#define COOLCHIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    CC_OK = 0,
+    CC_EINVAL = -1,       /* bad argument or unsupported configuration */
+    CC_ENOMEM = -2,       /* device allocation failed or workspace too small */
+    CC_ECUDA = -3,        /* a CUDA runtime call failed (see cc_last_cuda_error) */
+    CC_ETIMEOUT = -4,     /* a bounded device wait gave up */
+    CC_ENONFINITE = -5,   /* the loss became NaN or infinite */
+    CC_ESTATE = -6        /* state blob of the wrong size, version or shape */
+};
+
+typedef struct cc_ctx cc_ctx;
+
+/* Architecture and training schedule.  Table 1 notation: N-N-LinR layers, N-2-Lin,
+ * 1-1-TConv-k, 7-C-Conv-1, C-3-Conv-1, 3-3-ConvR-3. */
+typedef struct {
+    int levels;        /* L: number of latent grids; must be 7                          */
+    int arm_ctx;       /* N: causal context size = ARM width; 8, 16 or 24               */
+    int arm_layers;    /* number of N-N-LinR layers; 1 or 2                              */
+    int up_kernel;     /* k of the stride-2 transposed conv; 4 or 8                      */
+    int up_per_level;  /* 1: one filter per level; 0: one shared filter                 */
+    int syn_hidden;    /* C of the 7-C-Conv-1 layer; 8, 16 or 40                         */
+    int syn_res3x3;    /* number of 3-3-ConvR-3 layers; 1 or 2                           */
+    float lam;         /* lambda of eq. (1)                                              */
+    float lr;          /* Adam learning rate                                             */
+    int total_iters;   /* schedule length; decides where straight-through rounding starts */
+    float ste_frac;    /* last fraction of total_iters using rint + straight-through     */
+    uint64_t seed;     /* key of the Philox4x32-10 quantisation noise                    */
+} cc_config;
+
+/* Number of decoder parameters of a configuration (Table 1 "Param" column). */
+int cc_param_count(const cc_config* cfg, int* n_params);
+
+/* Number of latents sum_l ceil(H/2^l) ceil(W/2^l). */
+int cc_latent_count(const cc_config* cfg, int H, int W, int* n_latents);
+
+/* Bytes of device workspace cc_init_image_ws needs for this image size. */
+int cc_workspace_size(const cc_config* cfg, int H, int W, size_t* bytes);
+
+/* Create a context for one image: copies the image (host or device, H x W x 3 uint8),
+ * sets y = 0, the parameters to init_params (host or device, cc_param_count floats;
+ * NULL = the library's seeded default: uniform +-1/sqrt(fan_in) weights, zero biases,
+ * resampling-filter upsampling), Adam moments to 0 and the iteration counter to 0.
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream).  The library
+ * allocates its device memory with cudaMalloc.  Synchronises before returning. */
+int cc_init_image(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
+                  const float* init_params, void* cuda_stream, cc_ctx** out);
+
+/* Same as cc_init_image, but all device memory is carved from a caller-owned device
+ * workspace of ws_bytes >= cc_workspace_size bytes (e.g. a PyTorch allocation), which
+ * must stay valid until cc_free.  Returns CC_ENOMEM if ws_bytes is too small. */
+int cc_init_image_ws(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
+                     const float* init_params, void* cuda_stream,
+                     void* device_workspace, size_t ws_bytes, cc_ctx** out);
+
+/* Replace the image of a context by another one of the same size (host or device);
+ * asynchronous on the context stream. */
+int cc_set_image(cc_ctx* ctx, const uint8_t* rgb_hwc);
+
+/* Run n_iters overfitting iterations (forward, backward, Adam), asynchronously on the
+ * context stream, replaying a CUDA graph of one iteration.  Iteration t (counted from 0
+ * since cc_init_image) uses noise quantisation while t < round(total_iters (1 -
+ * ste_frac)) and rint + straight-through after.  Per-iteration D, R and loss are logged
+ * on the device (see cc_get_losses). */
+int cc_encode_iters(cc_ctx* ctx, int n_iters);
+
+/* Rate-distortion cost of the current state, eq. (1): D = mean squared error over the
+ * 3HW values, R_bpp = bits / (H W), cost = D + lambda R.  hard_round = 1: rint latents
+ * (the decoded image); 0: the current iteration's noisy latents.  Synchronises. */
+int cc_rd_cost(cc_ctx* ctx, int hard_round, double* D, double* R_bpp, double* cost);
+
+/* Decoded image x_hat = f_theta(f_upsilon(rint(y))) as H x W x 3 float32 (host or
+ * device, caller-owned), not clamped.  Synchronises. */
+int cc_decode(cc_ctx* ctx, float* rgb_out_hwc);
+
+/* One forward and backward pass at the current iteration without any update.
+ * noise_override (host or device, n_latents floats in flat latent order) replaces the
+ * quantisation noise, or NULL for the iteration's own noise / rounding.  grads_out
+ * (host or device): n_latents + n_params floats, dL/dy then dL/dparams, flat orders.
+ * Synchronises. */
+int cc_get_grads(cc_ctx* ctx, const float* noise_override, float* grads_out);
+
+/* cc_get_grads with the loss terms of that pass and an explicit mode:
+ * hard = 1 forces rint latents (noise_override ignored), 0 forces noise, -1 follows the
+ * schedule.  D, R_bpp may be NULL. */
+int cc_forward_backward(cc_ctx* ctx, const float* noise_override, int hard,
+                        float* grads_out, double* D, double* R_bpp);
+
+/* D, R_bpp and loss of iterations first .. first+count-1 (3 doubles each, host or
+ * device).  Only the last 4096 iterations are kept.  Synchronises. */
+int cc_get_losses(cc_ctx* ctx, int first, int count, double* out);
+
+/* Overwrite / read the latents y (n_latents floats, flat latent order) or the parameters
+ * (cc_param_count floats, flat parameter order); host or device buffers.  The setters are
+ * asynchronous on the context stream; the getters synchronise.  Adam moments and the
+ * iteration counter are left unchanged. */
+int cc_set_latents(cc_ctx* ctx, const float* y_flat);
+int cc_get_latents(cc_ctx* ctx, float* y_flat);
+int cc_set_params(cc_ctx* ctx, const float* params);
+int cc_get_params(cc_ctx* ctx, float* params);
+
+/* Number of iterations run so far. */
+int cc_iteration(cc_ctx* ctx, int* iter);
+
+/* The quantisation noise of iteration iter, n_latents floats in flat latent order
+ * (host or device).  Synchronises. */
+int cc_noise(cc_ctx* ctx, int iter, float* out);
+
+/* Measurement support.  cc_profile_phases runs `reps` full iterations eagerly on the
+ * context stream (forward, backward and update: the state advances by `reps` iterations),
+ * recording CUDA events around each phase, and writes the mean milliseconds per phase to
+ * ms_out[CC_N_PHASES] (host): 0 weight upload + quantisation, 1 ARM + rate forward and
+ * backward, 2 upsampling forward, 3 synthesis forward + distortion, 4 synthesis backward,
+ * 5 upsampling backward, 6 reductions + Adam + loss bookkeeping.  Synchronises.
+ * cc_graph_kernel_count gives the number of kernel launches in one captured iteration. */
+#define CC_N_PHASES 7
+int cc_profile_phases(cc_ctx* ctx, int reps, float* ms_out);
+int cc_graph_kernel_count(cc_ctx* ctx, int* n_kernels);
+
+/* Checkpoint: a flat versioned blob with y, parameters, Adam moments, the iteration
+ * counter and the seed.  With buf = NULL, *nbytes receives the size.  cc_set_state
+ * restores a blob written for the same configuration and image size; resuming replays
+ * the same noise, so a resumed run matches an uninterrupted one. */
+int cc_get_state(cc_ctx* ctx, void* buf, size_t* nbytes);
+int cc_set_state(cc_ctx* ctx, const void* buf, size_t nbytes);
+
+/* Release the context and its device memory (not a caller workspace). */
+void cc_free(cc_ctx* ctx);
+
+/* Static description of an error code. */
+const char* cc_strerror(int code);
+
+/* Text of the last CUDA error seen by the library in this thread ("" if none). */
+const char* cc_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COOLCHIC_H */

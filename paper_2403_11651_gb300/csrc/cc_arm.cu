@@ -1,0 +1,405 @@
+// Auto-regressive probability model p_psi and the rate term of eq. (1).
+//
+// Sec. II "Decoding" item ii: the ARM is an MLP f_psi of the N causal neighbours of a
+// latent in its own grid; Table 1 gives its layers (N-N-LinR x arm_layers, N-2-Lin).  Its
+// two outputs are the mean mu and log-scale s of a Laplace law, and the rate of a latent
+// is -log2 P(y_hat) with P the mass of [y_hat - 1/2, y_hat + 1/2] (eq. (1)).
+//
+// One thread owns one latent.  The weights live in a __constant__ bank refreshed before
+// every pass, so every multiply-add of the forward and input-gradient passes takes its
+// weight straight from the constant cache (all lanes read the same weight at once).  The
+// weight gradients, sum over latents of dz (x) input, are contracted per tile of 128
+// latents from shared memory: each thread owns an RB x RB block of one weight matrix
+// for one interleaved quarter of the tile's latents and keeps it in registers for the
+// whole persistent loop, so a CTA writes one partial sum per parameter at the end.
+// Every sum has a fixed order, so results are bit-reproducible on a given device.
+#include "cc_internal.cuh"
+
+namespace cc {
+
+constexpr int kMaxN = 24;
+constexpr int kMaxArmParams = 2 * (kMaxN * kMaxN + kMaxN) + 2 * kMaxN + 2;
+__constant__ float c_arm[kMaxArmParams];
+__constant__ int2 c_off[kMaxN];  // (dy, dx) of each context slot, raster order
+
+struct ArmArgs {
+  const float* yhat;
+  float* dctx;       // [N][n_pad]: d bits(p) / d context slot k of p
+  float* gself;      // [n_pad]:    d bits(p) / d yhat(p)
+  float* part_grad;  // [gridDim.x][n_arm]: per-CTA d bits / d psi
+  float* part_bits;  // [gridDim.x]
+  const int2* tiles; // (level, first latent of the tile within the level)
+  int n_tiles;
+  Geo g;
+};
+
+struct LapOut {
+  float bits, g_y, g_mu, g_s;  // bits and its derivatives wrt y_hat, mu, s
+};
+
+// -log2 P(y_hat) for the Laplace law (mu, b = exp(clamp(s))), P floored at 2^-16.
+// With d = y_hat - mu: for |d| >= 1/2 both bin edges lie on one side of mu and
+//   P = 1/2 exp(-(|d| - 1/2)/b) (1 - exp(-1/b));
+// otherwise P = 1 - 1/2 (exp(-(1/2 + d)/b) + exp(-(1/2 - d)/b)), formed with expm1 so
+// nothing cancels.  Derivatives of ln P:
+//   outer: d/dd = -sign(d)/b,  d/ds = ((|d| - 1/2) - 1/expm1(1/b)) / b
+//   inner: d/dd = (e1 - e2) / (2 b P),  d/ds = -(e1 (1/2 + d) + e2 (1/2 - d)) / (2 b P)
+__device__ __forceinline__ LapOut laplace_bits(float yh, float mu, float s) {
+  constexpr float kLogBMin = -4.60517018598809136f;  // ln 1e-2
+  constexpr float kLogBMax = 6.90775527898213705f;   // ln 1e3
+  constexpr float kInvLn2 = 1.44269504088896341f;
+  constexpr float kPMin = 1.52587890625e-05f;        // 2^-16
+  const float sc = fminf(fmaxf(s, kLogBMin), kLogBMax);
+  const float b = expf(sc);
+  const float ib = 1.0f / b;
+  const float d = yh - mu;
+  const float ad = fabsf(d);
+  float P, gd, gs;
+  if (ad >= 0.5f) {
+    P = 0.5f * expf(-(ad - 0.5f) * ib) * (-expm1f(-ib));
+    gd = -copysignf(ib, d);
+    gs = ((ad - 0.5f) - 1.0f / expm1f(ib)) * ib;
+  } else {
+    const float a1 = (0.5f + d) * ib, a2 = (0.5f - d) * ib;
+    const float e1 = expf(-a1), e2 = expf(-a2);
+    P = -0.5f * (expm1f(-a1) + expm1f(-a2));
+    const float iP = 1.0f / P;
+    gd = 0.5f * (e1 - e2) * ib * iP;
+    gs = -0.5f * (e1 * a1 + e2 * a2) * iP;
+  }
+  LapOut o;
+  if (!(P >= kPMin)) {
+    o.bits = 16.0f;
+    o.g_y = o.g_mu = o.g_s = 0.0f;
+    return o;
+  }
+  o.bits = -log2f(P);
+  o.g_y = -gd * kInvLn2;
+  o.g_mu = gd * kInvLn2;
+  o.g_s = (s >= kLogBMin && s <= kLogBMax) ? -gs * kInvLn2 : 0.0f;
+  return o;
+}
+
+template <int N>
+struct ArmBlocking {
+  static constexpr int RB = (N % 6 == 0) ? 6 : 4;  // weight-gradient block edge
+  static constexpr int NB = N / RB;                // blocks per matrix edge
+};
+
+template <int RB>
+__device__ __forceinline__ void load_row(float (&v)[RB], const float* p) {
+  if constexpr (RB % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < RB; k += 4) {
+      const float4 t = *reinterpret_cast<const float4*>(p + k);
+      v[k] = t.x; v[k + 1] = t.y; v[k + 2] = t.z; v[k + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < RB; k += 2) {
+      const float2 t = *reinterpret_cast<const float2*>(p + k);
+      v[k] = t.x; v[k + 1] = t.y;
+    }
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void store_row(float* p, const float (&v)[N]) {
+#pragma unroll
+  for (int k = 0; k < N; k += 4)
+    *reinterpret_cast<float4*>(p + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+}
+
+template <int N, int NL>
+struct ArmShape {
+  static constexpr int S = N + 4;               // smem row stride (conflict-free float4 rows)
+  static constexpr int LW = N * N + N;          // floats per LinR layer (W then b)
+  static constexpr int OW = NL * LW;            // W_out
+  static constexpr int OB = OW + 2 * N;         // b_out
+  static constexpr int NP = OB + 2;             // ARM parameters
+  static constexpr int T = kArmTile;
+  static constexpr int tile_floats = 2 * NL * T * S + T * S + 2 * T;
+  static constexpr int NBLK = NL * ArmBlocking<N>::NB * ArmBlocking<N>::NB;
+  static constexpr int G = T / NBLK;            // interleaved latent groups
+  static constexpr int NCH_B = NL * N / 4;      // bias chunks of 4
+  static constexpr int NCH = NCH_B + N / 4;     // + W_out column chunks (b_out rides on #0)
+  static constexpr int XPER = (NCH + NBLK - 1) / NBLK;
+  static constexpr int red_floats = G * NP;
+  static constexpr int smem_floats = tile_floats > red_floats ? tile_floats : red_floats;
+  static_assert(T % NBLK == 0, "tile must split evenly into weight blocks");
+};
+
+template <int N, int NL, bool BWD>
+__global__ void __launch_bounds__(kArmTile, 3) k_arm(ArmArgs a) {
+  using Sh = ArmShape<N, NL>;
+  constexpr int S = Sh::S, LW = Sh::LW, OW = Sh::OW, OB = Sh::OB, NP = Sh::NP, T = Sh::T;
+  constexpr int RB = ArmBlocking<N>::RB, NB = ArmBlocking<N>::NB;
+  constexpr int NBLK = Sh::NBLK, G = Sh::G, NCH_B = Sh::NCH_B, NCH = Sh::NCH;
+  constexpr int XPER = Sh::XPER;
+
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  float* s_in = sm;                    // [NL][T][S] input of LinR layer L
+  float* s_dz = s_in + NL * T * S;     // [NL][T][S] dz of LinR layer L
+  float* s_ho = s_dz + NL * T * S;     // [T][S]     input of the output layer
+  float* s_do = s_ho + T * S;          // [T][2]     (d bits/d mu, d bits/d s)
+
+  const int tid = threadIdx.x;
+  const int unit = tid % NBLK, grp = tid / NBLK;
+  const int uL = unit / (NB * NB), urb = (unit / NB) % NB, ucb = unit % NB;
+
+  float acc[RB][RB];
+  float xacc[XPER][10];
+  if constexpr (BWD) {
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+      for (int c = 0; c < RB; ++c) acc[r][c] = 0.f;
+#pragma unroll
+    for (int q = 0; q < XPER; ++q)
+#pragma unroll
+      for (int e = 0; e < 10; ++e) xacc[q][e] = 0.f;
+  }
+  float bits_acc = 0.f;
+
+  for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+    const int2 td = a.tiles[tile];
+    const int l = td.x;
+    const int w = a.g.w[l];
+    const int n_l = a.g.h[l] * w;
+    const int i = td.y + tid;
+    const bool valid = i < n_l;
+    const float* plane = a.yhat + a.g.off[l];
+    int r = 0, c = 0;
+    if (valid) { r = i / w; c = i - r * w; }
+
+    // context gather, zero outside the grid
+    float h[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int2 o = c_off[k];
+      const int rr = r + o.x, cc = c + o.y;
+      h[k] = (valid && rr >= 0 && cc >= 0 && cc < w) ? __ldg(plane + rr * w + cc) : 0.f;
+    }
+    const float yq = valid ? __ldg(plane + i) : 0.f;
+
+    // forward: h <- h + relu(W h + b), NL times
+    uint32_t mask[NL];
+#pragma unroll
+    for (int L = 0; L < NL; ++L) {
+      if constexpr (BWD) store_row<N>(s_in + (L * T + tid) * S, h);
+      float z[N];
+#pragma unroll
+      for (int o = 0; o < N; ++o) z[o] = c_arm[L * LW + N * N + o];
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+#pragma unroll
+        for (int o = 0; o < N; ++o) z[o] = fmaf(c_arm[L * LW + o * N + k], h[k], z[o]);
+      uint32_t mk = 0;
+#pragma unroll
+      for (int o = 0; o < N; ++o) {
+        mk |= (z[o] > 0.f ? 1u : 0u) << o;
+        h[o] += fmaxf(z[o], 0.f);
+      }
+      mask[L] = mk;
+    }
+    if constexpr (BWD) store_row<N>(s_ho + tid * S, h);
+    float mu = c_arm[OB], s = c_arm[OB + 1];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      mu = fmaf(c_arm[OW + k], h[k], mu);
+      s = fmaf(c_arm[OW + N + k], h[k], s);
+    }
+    LapOut lo = laplace_bits(yq, mu, s);
+    if (!valid) lo.bits = lo.g_y = lo.g_mu = lo.g_s = 0.f;
+    bits_acc += lo.bits;
+
+    if constexpr (BWD) {
+      reinterpret_cast<float2*>(s_do)[tid] = make_float2(lo.g_mu, lo.g_s);
+      float dh[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) dh[k] = lo.g_mu * c_arm[OW + k] + lo.g_s * c_arm[OW + N + k];
+#pragma unroll
+      for (int L = NL - 1; L >= 0; --L) {
+        float dz[N];
+#pragma unroll
+        for (int o = 0; o < N; ++o) dz[o] = ((mask[L] >> o) & 1u) ? dh[o] : 0.f;
+        store_row<N>(s_dz + (L * T + tid) * S, dz);
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+#pragma unroll
+          for (int o = 0; o < N; ++o) dh[k] = fmaf(c_arm[L * LW + o * N + k], dz[o], dh[k]);
+      }
+      if (valid) {
+        const long long q = a.g.off[l] + i;
+#pragma unroll
+        for (int k = 0; k < N; ++k) a.dctx[k * a.g.n_pad + q] = dh[k];
+        a.gself[q] = lo.g_y;
+      }
+      __syncthreads();
+
+      // weight gradients of the LinR layers: acc += sum_p dz_L[p][rows] (x) in_L[p][cols]
+      {
+        const float* A = s_dz + uL * T * S + urb * RB;
+        const float* B = s_in + uL * T * S + ucb * RB;
+        for (int p = grp; p < T; p += G) {
+          float av[RB], bv[RB];
+          load_row<RB>(av, A + p * S);
+          load_row<RB>(bv, B + p * S);
+#pragma unroll
+          for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+            for (int cc = 0; cc < RB; ++cc) acc[rr][cc] = fmaf(av[rr], bv[cc], acc[rr][cc]);
+        }
+      }
+      // biases and the output layer, in chunks of four columns
+#pragma unroll
+      for (int qi = 0; qi < XPER; ++qi) {
+        const int q = unit + qi * NBLK;
+        if (q < NCH_B) {
+          const int L = q / (N / 4), i0 = (q % (N / 4)) * 4;
+          const float* A = s_dz + L * T * S + i0;
+          for (int p = grp; p < T; p += G) {
+            const float4 t = *reinterpret_cast<const float4*>(A + p * S);
+            xacc[qi][0] += t.x; xacc[qi][1] += t.y; xacc[qi][2] += t.z; xacc[qi][3] += t.w;
+          }
+        } else if (q < NCH) {
+          const int j0 = (q - NCH_B) * 4;
+          for (int p = grp; p < T; p += G) {
+            const float4 t = *reinterpret_cast<const float4*>(s_ho + p * S + j0);
+            const float2 d = reinterpret_cast<const float2*>(s_do)[p];
+            xacc[qi][0] = fmaf(d.x, t.x, xacc[qi][0]); xacc[qi][1] = fmaf(d.x, t.y, xacc[qi][1]);
+            xacc[qi][2] = fmaf(d.x, t.z, xacc[qi][2]); xacc[qi][3] = fmaf(d.x, t.w, xacc[qi][3]);
+            xacc[qi][4] = fmaf(d.y, t.x, xacc[qi][4]); xacc[qi][5] = fmaf(d.y, t.y, xacc[qi][5]);
+            xacc[qi][6] = fmaf(d.y, t.z, xacc[qi][6]); xacc[qi][7] = fmaf(d.y, t.w, xacc[qi][7]);
+            xacc[qi][8] += d.x; xacc[qi][9] += d.y;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // rate partial of this CTA
+  {
+    float v = bits_acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __shared__ float s_bits[T / 32];
+    if ((tid & 31) == 0) s_bits[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+      float t = 0.f;
+#pragma unroll
+      for (int k = 0; k < T / 32; ++k) t += s_bits[k];
+      a.part_bits[blockIdx.x] = t;
+    }
+  }
+
+  if constexpr (BWD) {
+    // every (group, parameter) slot is written exactly once, then summed over groups
+    float* red = sm;
+    float* mine = red + grp * NP;
+#pragma unroll
+    for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+      for (int cc = 0; cc < RB; ++cc)
+        mine[uL * LW + (urb * RB + rr) * N + ucb * RB + cc] = acc[rr][cc];
+#pragma unroll
+    for (int qi = 0; qi < XPER; ++qi) {
+      const int q = unit + qi * NBLK;
+      if (q < NCH_B) {
+        const int L = q / (N / 4), i0 = (q % (N / 4)) * 4;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) mine[L * LW + N * N + i0 + e] = xacc[qi][e];
+      } else if (q < NCH) {
+        const int j0 = (q - NCH_B) * 4;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          mine[OW + j0 + e] = xacc[qi][e];
+          mine[OW + N + j0 + e] = xacc[qi][4 + e];
+        }
+        if (j0 == 0) { mine[OB] = xacc[qi][8]; mine[OB + 1] = xacc[qi][9]; }
+      }
+    }
+    __syncthreads();
+    for (int j = tid; j < NP; j += T) {
+      float t = 0.f;
+#pragma unroll
+      for (int g = 0; g < G; ++g) t += red[g * NP + j];
+      a.part_grad[(long long)blockIdx.x * NP + j] = t;
+    }
+  }
+}
+
+template <int N, int NL, bool BWD>
+static cudaError_t launch_t(const ArmArgs& a, int grid, cudaStream_t st) {
+  using Sh = ArmShape<N, NL>;
+  const size_t smem = BWD ? (size_t)Sh::smem_floats * sizeof(float) : 0;
+  k_arm<N, NL, BWD><<<grid, kArmTile, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int N, int NL>
+static cudaError_t prepare_t() {
+  return cudaFuncSetAttribute(k_arm<N, NL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(ArmShape<N, NL>::smem_floats * sizeof(float)));
+}
+
+
+template <int N, int NL>
+static size_t smem_t(bool bwd) {
+  return bwd ? (size_t)ArmShape<N, NL>::smem_floats * sizeof(float) : 0;
+}
+
+#define CC_ARM_DISPATCH(FN, ...)                                              \
+  switch (a.N * 10 + a.NL) {                                                  \
+    case 81: return FN<8, 1>(__VA_ARGS__);                                    \
+    case 82: return FN<8, 2>(__VA_ARGS__);                                    \
+    case 161: return FN<16, 1>(__VA_ARGS__);                                  \
+    case 162: return FN<16, 2>(__VA_ARGS__);                                  \
+    case 241: return FN<24, 1>(__VA_ARGS__);                                  \
+    case 242: return FN<24, 2>(__VA_ARGS__);                                  \
+    default: break;                                                           \
+  }
+
+template <int N, int NL>
+static cudaError_t launch_nl(bool bwd, const ArmArgs& k, int grid, cudaStream_t st) {
+  return bwd ? launch_t<N, NL, true>(k, grid, st) : launch_t<N, NL, false>(k, grid, st);
+}
+
+cudaError_t arm_launch(const Arch& a, bool backward, const float* yhat, const Geo& g,
+                       const int2* tiles, int n_tiles, int grid, float* dctx, float* gself,
+                       float* part_grad, float* part_bits, cudaStream_t st) {
+  ArmArgs k;
+  k.yhat = yhat; k.dctx = dctx; k.gself = gself; k.part_grad = part_grad;
+  k.part_bits = part_bits; k.tiles = tiles; k.n_tiles = n_tiles; k.g = g;
+  CC_ARM_DISPATCH(launch_nl, backward, k, grid, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t arm_prepare(const Arch& a) {
+  CC_ARM_DISPATCH(prepare_t);
+  return cudaErrorInvalidValue;
+}
+
+size_t arm_smem_bytes(const Arch& a, bool backward) {
+  CC_ARM_DISPATCH(smem_t, backward);
+  return 0;
+}
+
+int arm_blocks_per_sm(const Arch& a, bool backward) {
+  (void)a;
+  return backward ? 3 : 4;
+}
+
+cudaError_t arm_upload(const float* d_params, int n_arm, const int2* d_offsets, int N,
+                       cudaStream_t st) {
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_arm, d_params, (size_t)n_arm * sizeof(float), 0,
+                                          cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbolAsync(c_off, d_offsets, (size_t)N * sizeof(int2), 0,
+                                 cudaMemcpyDeviceToDevice, st);
+}
+
+}  // namespace cc

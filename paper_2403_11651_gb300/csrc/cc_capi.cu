@@ -1,0 +1,778 @@
+// C ABI of the library (declared in include/coolchic.h): context set-up, device memory
+// plan, the sequence of kernels of one iteration and its CUDA-graph capture.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "cc_internal.cuh"
+#include "../../include/coolchic.h"
+
+using namespace cc;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail_cuda(cudaError_t e, const char* what) {
+  snprintf(g_err, sizeof(g_err), "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+  return CC_ECUDA;
+}
+
+#define CK(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return fail_cuda(e_, #call);  \
+  } while (0)
+
+#define CKE(call)                                        \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return e_;                    \
+  } while (0)
+
+constexpr uint32_t kStateMagic = 0x31534343u;  // "CCS1"
+constexpr uint32_t kStateVersion = 1;
+
+struct StateHeader {
+  uint32_t magic, version;
+  int32_t H, W, n_lat, n_params, iter, pad;
+  uint64_t seed;
+  int32_t arch[8];
+};
+
+long long align32(long long v) { return (v + 31) & ~31ll; }
+
+// The N nearest causal neighbours (dy < 0, or dy = 0 and dx < 0), ties broken by smaller
+// |dy| then smaller dx, listed in raster order.
+std::vector<int2> causal_offsets(int n) {
+  struct Cand { int dy, dx; };
+  std::vector<Cand> c;
+  for (int dy = -6; dy <= 0; ++dy)
+    for (int dx = -6; dx <= 6; ++dx)
+      if (dy < 0 || dx < 0) c.push_back({dy, dx});
+  std::stable_sort(c.begin(), c.end(), [](const Cand& a, const Cand& b) {
+    const int da = a.dy * a.dy + a.dx * a.dx, db = b.dy * b.dy + b.dx * b.dx;
+    if (da != db) return da < db;
+    if (std::abs(a.dy) != std::abs(b.dy)) return std::abs(a.dy) < std::abs(b.dy);
+    return a.dx < b.dx;
+  });
+  c.resize(n);
+  std::sort(c.begin(), c.end(), [](const Cand& a, const Cand& b) {
+    return a.dy != b.dy ? a.dy < b.dy : a.dx < b.dx;
+  });
+  std::vector<int2> out;
+  for (auto& v : c) out.push_back(make_int2(v.dy, v.dx));
+  return out;
+}
+
+int validate(const cc_config* c) {
+  if (!c) return CC_EINVAL;
+  if (c->levels != kLevels) return CC_EINVAL;
+  if (c->arm_ctx != 8 && c->arm_ctx != 16 && c->arm_ctx != 24) return CC_EINVAL;
+  if (c->arm_layers != 1 && c->arm_layers != 2) return CC_EINVAL;
+  if (c->up_kernel != 4 && c->up_kernel != 8) return CC_EINVAL;
+  if (c->up_per_level != 0 && c->up_per_level != 1) return CC_EINVAL;
+  if (c->syn_hidden != 8 && c->syn_hidden != 16 && c->syn_hidden != 40) return CC_EINVAL;
+  if (c->syn_res3x3 != 1 && c->syn_res3x3 != 2) return CC_EINVAL;
+  if (!(c->lam >= 0.f) || !(c->lr > 0.f) || c->total_iters < 0) return CC_EINVAL;
+  if (!(c->ste_frac >= 0.f && c->ste_frac <= 1.f)) return CC_EINVAL;
+  return CC_OK;
+}
+
+Arch arch_of(const cc_config* c) {
+  Arch a;
+  a.N = c->arm_ctx; a.NL = c->arm_layers; a.K = c->up_kernel; a.per_level = c->up_per_level;
+  a.C = c->syn_hidden; a.NR = c->syn_res3x3;
+  return a;
+}
+
+Layout layout_of(const Arch& a) {
+  Layout l;
+  l.n_arm = a.NL * (a.N * a.N + a.N) + 2 * a.N + 2;
+  l.up0 = l.n_arm;
+  l.n_up = a.per_level ? kLevels - 1 : 1;
+  l.syn0 = l.up0 + l.n_up * a.K * a.K;
+  l.n_syn = 11 * a.C + 3 + a.NR * 84;
+  l.total = l.syn0 + l.n_syn;
+  return l;
+}
+
+Geo geo_of(int H, int W) {
+  Geo g;
+  g.H = H; g.W = W;
+  long long off = 0;
+  g.n_lat = 0;
+  for (int l = 0; l < kLevels; ++l) {
+    g.h[l] = (H + (1 << l) - 1) >> l;
+    g.w[l] = (W + (1 << l) - 1) >> l;
+    g.off[l] = off;
+    off = align32(off + (long long)g.h[l] * g.w[l]);
+    g.n_lat += g.h[l] * g.w[l];
+  }
+  g.n_pad = off;
+  return g;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return n;
+}
+
+}  // namespace
+
+struct cc_ctx {
+  cc_config cfg;
+  Arch arch;
+  Layout lay;
+  Geo geo;
+  int HW = 0;
+  int ste_start = 0;
+  int dev = 0;
+  cudaStream_t st = nullptr;
+  cudaStream_t cap = nullptr;
+  bool own_mem = false;
+  void* mem = nullptr;
+  size_t bytes = 0;
+  float *x, *y, *my, *vy, *yhat, *gsyn, *gself, *dctx, *noise;
+  float *params, *mp, *vp;
+  float *hbuf, *dhbuf, *dz;
+  float *part_arm, *part_bits, *part_d, *part_conv, *part_syn, *part_up, *part2;
+  float* grad_scratch;
+  uint8_t* img_u8;
+  int2 *tiles, *offs;
+  IterScalars* sc;
+  double* log;
+  UpPlan up;
+  std::vector<int2> h_tiles, h_offs;
+  int n_tiles = 0, grid_arm = 0, grid_syn = 0, slices = 16, n_virtual = 0;
+  SectionTable tab;
+  cudaGraphExec_t g1 = nullptr, g16 = nullptr;
+  int iter = 0;
+  int kernels_per_iter = 0;
+};
+
+namespace {
+
+// Lay out every buffer in one allocation; with base == nullptr only the size is computed.
+size_t plan(cc_ctx* c, char* base) {
+  size_t off = 0;
+  auto take = [&](size_t nbytes) -> char* {
+    char* p = base ? base + off : nullptr;
+    off = (off + nbytes + 255) & ~(size_t)255;
+    return p;
+  };
+  const Geo& g = c->geo;
+  const Arch& a = c->arch;
+  const size_t HW = (size_t)c->HW;
+  const size_t L = (size_t)g.n_pad * sizeof(float);
+  c->x = (float*)take(3 * HW * sizeof(float));
+  c->y = (float*)take(L);
+  c->my = (float*)take(L);
+  c->vy = (float*)take(L);
+  c->yhat = (float*)take(L);
+  c->gsyn = (float*)take(L);
+  c->gself = (float*)take(L);
+  c->noise = (float*)take(L);
+  c->dctx = (float*)take((size_t)a.N * L);
+  c->params = (float*)take((size_t)c->lay.total * sizeof(float));
+  c->mp = (float*)take((size_t)c->lay.total * sizeof(float));
+  c->vp = (float*)take((size_t)c->lay.total * sizeof(float));
+  c->hbuf = (float*)take((size_t)(a.NR + 1) * 3 * HW * sizeof(float));
+  c->dhbuf = (float*)take((size_t)(a.NR + 1) * 3 * HW * sizeof(float));
+  c->dz = (float*)take(3 * HW * sizeof(float));
+  c->part_arm = (float*)take((size_t)c->grid_arm * c->lay.n_arm * sizeof(float));
+  c->part_bits = (float*)take((size_t)c->grid_arm * sizeof(float));
+  c->part_d = (float*)take((size_t)c->grid_syn * sizeof(float));
+  c->part_conv = (float*)take((size_t)a.NR * c->grid_syn * 84 * sizeof(float));
+  c->part_syn = (float*)take((size_t)c->grid_syn * (11 * a.C + 3) * sizeof(float));
+  c->part_up = (float*)take((size_t)(kLevels - 1) * c->grid_syn * kLevels * a.K * a.K *
+                            sizeof(float));
+  c->part2 = (float*)take((size_t)c->slices * c->n_virtual * sizeof(float));
+  c->grad_scratch = (float*)take((size_t)(g.n_lat + c->lay.total) * sizeof(float));
+  c->img_u8 = (uint8_t*)take(3 * HW);
+  c->tiles = (int2*)take((size_t)c->n_tiles * sizeof(int2));
+  c->offs = (int2*)take(24 * sizeof(int2));
+  c->sc = (IterScalars*)take(sizeof(IterScalars));
+  c->log = (double*)take((size_t)kLogCap * 3 * sizeof(double));
+  for (int l = 1; l < kLevels; ++l)
+    for (int j = 0; j < l; ++j) {
+      const size_t n = (size_t)align32((long long)g.h[j] * g.w[j]) * sizeof(float);
+      c->up.plane[l][j] = (float*)take(n);
+      c->up.dplane[l][j] = (float*)take(n);
+    }
+  return off;
+}
+
+int setup(cc_ctx* c, const cc_config* cfg, int H, int W) {
+  int e = validate(cfg);
+  if (e) return e;
+  if (H < 1 || W < 1 || H > 16384 || W > 16384) return CC_EINVAL;
+  c->cfg = *cfg;
+  c->arch = arch_of(cfg);
+  c->lay = layout_of(c->arch);
+  c->geo = geo_of(H, W);
+  c->HW = H * W;
+  c->ste_start = (int)std::llround((double)cfg->total_iters * (1.0 - (double)cfg->ste_frac));
+  c->h_tiles.clear();
+  for (int l = 0; l < kLevels; ++l)
+    for (int s = 0; s < c->geo.h[l] * c->geo.w[l]; s += kArmTile) c->h_tiles.push_back(make_int2(l, s));
+  c->n_tiles = (int)c->h_tiles.size();
+  const int sms = sm_count();
+  if (sms <= 0) return fail_cuda(cudaErrorNoDevice, "cudaDeviceGetAttribute");
+  c->grid_arm = std::min(c->n_tiles, sms * arm_blocks_per_sm(c->arch, true));
+  c->grid_syn = std::max(1, std::min((c->HW + kPixTile - 1) / kPixTile, 2 * sms));
+  const int n1x1 = 11 * c->arch.C + 3;
+  const int vconv = c->lay.n_arm + n1x1;
+  const int vup = vconv + c->arch.NR * 84;
+  const int K2 = c->arch.K * c->arch.K;
+  c->n_virtual = vup + (kLevels - 1) * K2;
+  c->h_offs = causal_offsets(c->arch.N);
+  return CC_OK;
+}
+
+void build_sections(cc_ctx* c) {
+  SectionTable& t = c->tab;
+  const Arch& a = c->arch;
+  const int n1x1 = 11 * a.C + 3;
+  const int K2 = a.K * a.K;
+  int n = 0;
+  t.s[n++] = {c->part_arm, c->grid_arm, c->lay.n_arm, c->lay.n_arm, 0,
+              (float)((double)c->cfg.lam / (double)c->HW)};
+  t.s[n++] = {c->part_syn, c->grid_syn, n1x1, n1x1, c->lay.n_arm, 1.f};
+  for (int i = 0; i < a.NR; ++i)
+    t.s[n++] = {c->part_conv + (size_t)i * c->grid_syn * 84, c->grid_syn, 84, 84,
+                c->lay.n_arm + n1x1 + 84 * i, 1.f};
+  const int vup = c->lay.n_arm + n1x1 + 84 * a.NR;
+  for (int l = 1; l < kLevels; ++l)
+    t.s[n++] = {c->part_up + (size_t)l * K2, l * c->grid_syn, K2, kLevels * K2,
+                vup + (l - 1) * K2, 1.f};
+  t.n = n;
+}
+
+// One pass of the hot path.  qmode: quantisation mode of k_quantize.  backward: run the
+// backward kernels (and the update when apply).  grad_out: device buffer receiving dL/dy
+// then dL/dparams, or nullptr.
+cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bool apply,
+                         float* grad_out, bool advance, cudaEvent_t* ev = nullptr) {
+  const Arch& a = c->arch;
+  const size_t HW = (size_t)c->HW;
+  auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], s) : cudaSuccess; };
+  CKE(mark(0));
+  CKE(arm_upload(c->params, c->lay.n_arm, c->offs, a.N, s));
+  CKE(syn_upload(c->params, c->lay, a, s));
+  CKE(quantize_launch(c->geo, c->y, c->yhat, c->noise, qmode, c->sc, c->ste_start, c->cfg.seed,
+                      -1, s));
+  CKE(mark(1));
+  CKE(arm_launch(a, backward, c->yhat, c->geo, c->tiles, c->n_tiles, c->grid_arm, c->dctx,
+                 c->gself, c->part_arm, c->part_bits, s));
+  CKE(mark(2));
+  CKE(up_forward(a, c->geo, c->yhat, c->up, s));
+  CKE(mark(3));
+  CKE(syn_forward(a, c->geo, c->yhat, c->up, c->x, c->hbuf, c->dhbuf + (size_t)a.NR * 3 * HW,
+                  c->part_d, c->grid_syn, s));
+  CKE(mark(4));
+  if (backward) {
+    CKE(syn_backward(a, c->geo, c->yhat, c->up, c->hbuf, c->dhbuf, c->dz, c->gsyn, c->part_conv,
+                     c->part_syn, c->grid_syn, s));
+    CKE(mark(5));
+    CKE(up_backward(a, c->geo, c->yhat, c->up, c->gsyn, c->part_up, c->grid_syn, s));
+    CKE(mark(6));
+    CKE(reduce_sections(c->tab, c->part2, c->n_virtual, c->slices, s));
+    CKE(param_update(c->lay, a, c->part2, c->slices, c->params, c->mp, c->vp,
+                     grad_out ? grad_out + c->geo.n_lat : nullptr, apply, c->cfg.lr, c->sc, s));
+    CKE(latent_update(c->geo, a, c->offs, c->gsyn, c->gself, c->dctx,
+                      (float)((double)c->cfg.lam / (double)c->HW), c->y, c->my, c->vy, grad_out,
+                      apply, c->cfg.lr, c->sc, s));
+  }
+  CKE(finish_iteration(c->part_d, c->grid_syn, c->part_bits, c->grid_arm,
+                       1.0 / (3.0 * (double)HW), 1.0 / (double)HW, (double)c->cfg.lam, c->sc,
+                       c->log, advance, s));
+  return mark(7);
+}
+
+int build_graph(cc_ctx* c, int n, cudaGraphExec_t* out) {
+  CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t err = cudaSuccess;
+  for (int k = 0; k < n && err == cudaSuccess; ++k)
+    err = enqueue_pass(c, c->cap, 0, true, true, nullptr, true);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);
+  if (err != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail_cuda(err, "iteration capture");
+  }
+  if (e2 != cudaSuccess) return fail_cuda(e2, "cudaStreamEndCapture");
+  if (n == 1) {
+    size_t nn = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess) {
+      std::vector<cudaGraphNode_t> nodes(nn);
+      cudaGraphGetNodes(graph, nodes.data(), &nn);
+      int k = 0;
+      for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+      }
+      c->kernels_per_iter = k;
+    }
+  }
+  cudaError_t e3 = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e3 != cudaSuccess) return fail_cuda(e3, "cudaGraphInstantiate");
+  return CC_OK;
+}
+
+void default_params(const cc_ctx* c, std::vector<float>& p) {
+  // splitmix64 (Steele, Lea & Flood, OOPSLA 2014) keyed by the seed
+  uint64_t s = c->cfg.seed ^ 0x2545F4914F6CDD1Dull;
+  auto next = [&]() {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  auto uni = [&](int fan_in) {
+    const double u = (double)(next() >> 11) * (1.0 / 9007199254740992.0);
+    return (float)((2.0 * u - 1.0) / std::sqrt((double)fan_in));
+  };
+  const Arch& a = c->arch;
+  const Layout& L = c->lay;
+  p.assign(L.total, 0.f);
+  int k = 0;
+  for (int i = 0; i < a.NL; ++i) {
+    for (int j = 0; j < a.N * a.N; ++j) p[k++] = uni(a.N);
+    k += a.N;
+  }
+  for (int j = 0; j < 2 * a.N; ++j) p[k++] = uni(a.N);
+  k += 2;
+  // upsampling: 2x resampling filter (Keys cubic, a = -0.75, for k = 8; linear for k = 4)
+  auto keys = [](double x) {
+    const double A = -0.75;
+    x = std::fabs(x);
+    if (x <= 1) return (A + 2) * x * x * x - (A + 3) * x * x + 1;
+    if (x < 2) return A * x * x * x - 5 * A * x * x + 8 * A * x - 4 * A;
+    return 0.0;
+  };
+  std::vector<double> f1;
+  if (a.K == 8) {
+    for (double d : {1.75, 1.25, 0.75, 0.25, 0.25, 0.75, 1.25, 1.75}) f1.push_back(keys(d));
+  } else {
+    f1 = {0.25, 0.75, 0.75, 0.25};
+  }
+  for (int f = 0; f < L.n_up; ++f)
+    for (int u = 0; u < a.K; ++u)
+      for (int v = 0; v < a.K; ++v) p[k++] = (float)(f1[u] * f1[v]);
+  for (int j = 0; j < a.C * kLevels; ++j) p[k++] = uni(kLevels);
+  k += a.C;
+  for (int j = 0; j < 3 * a.C; ++j) p[k++] = uni(a.C);
+  k += 3;
+  for (int i = 0; i < a.NR; ++i) {
+    for (int j = 0; j < 81; ++j) p[k++] = uni(27);
+    k += 3;
+  }
+}
+
+int init_common(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
+                const float* init_params, void* stream, void* ws, size_t ws_bytes, cc_ctx** out) {
+  if (!out || !rgb_hwc) return CC_EINVAL;
+  *out = nullptr;
+  cc_ctx* c = new cc_ctx();
+  int e = setup(c, cfg, H, W);
+  if (e) { delete c; return e; }
+  cudaGetDevice(&c->dev);
+  c->st = (cudaStream_t)stream;
+  const size_t need = plan(c, nullptr);
+  if (ws) {
+    if (ws_bytes < need) { delete c; return CC_ENOMEM; }
+    c->mem = ws;
+    c->own_mem = false;
+  } else {
+    cudaError_t ce = cudaMalloc(&c->mem, need);
+    if (ce != cudaSuccess) { delete c; fail_cuda(ce, "cudaMalloc"); return CC_ENOMEM; }
+    c->own_mem = true;
+  }
+  c->bytes = need;
+  plan(c, (char*)c->mem);
+  build_sections(c);
+  auto bail = [&](int code) { cc_free(c); return code; };
+  cudaError_t ce = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+  if (ce != cudaSuccess) return bail(fail_cuda(ce, "cudaStreamCreate"));
+  if ((ce = arm_prepare(c->arch)) != cudaSuccess) return bail(fail_cuda(ce, "arm_prepare"));
+  if ((ce = syn_prepare(c->arch)) != cudaSuccess) return bail(fail_cuda(ce, "syn_prepare"));
+  if ((ce = cudaMemsetAsync(c->mem, 0, need, c->st)) != cudaSuccess)
+    return bail(fail_cuda(ce, "cudaMemsetAsync"));
+  if ((ce = cudaMemcpyAsync(c->img_u8, rgb_hwc, (size_t)3 * c->HW, cudaMemcpyDefault, c->st)))
+    return bail(fail_cuda(ce, "image copy"));
+  if ((ce = image_to_planar(c->img_u8, c->x, H, W, c->st))) return bail(fail_cuda(ce, "image"));
+  std::vector<float> hp;
+  const float* src = init_params;
+  if (!src) {
+    default_params(c, hp);
+    src = hp.data();
+  }
+  if ((ce = cudaMemcpyAsync(c->params, src, (size_t)c->lay.total * sizeof(float),
+                            cudaMemcpyDefault, c->st)))
+    return bail(fail_cuda(ce, "params copy"));
+  if ((ce = cudaMemcpyAsync(c->tiles, c->h_tiles.data(), c->h_tiles.size() * sizeof(int2),
+                            cudaMemcpyHostToDevice, c->st)))
+    return bail(fail_cuda(ce, "tiles copy"));
+  if ((ce = cudaMemcpyAsync(c->offs, c->h_offs.data(), c->h_offs.size() * sizeof(int2),
+                            cudaMemcpyHostToDevice, c->st)))
+    return bail(fail_cuda(ce, "offsets copy"));
+  if ((ce = cudaStreamSynchronize(c->st))) return bail(fail_cuda(ce, "init sync"));
+  *out = c;
+  return CC_OK;
+}
+
+int sync_copy_scalars(cc_ctx* c, IterScalars* h) {
+  CK(cudaMemcpyAsync(h, c->sc, sizeof(IterScalars), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return CC_OK;
+}
+
+// latent-shaped device buffer <-> flat latent order at `flat` (host or device)
+int copy_latents(cc_ctx* c, float* dev, float* flat, bool to_flat) {
+  long long fo = 0;
+  for (int l = 0; l < kLevels; ++l) {
+    const size_t n = (size_t)c->geo.h[l] * c->geo.w[l];
+    if (to_flat)
+      CK(cudaMemcpyAsync(flat + fo, dev + c->geo.off[l], n * sizeof(float), cudaMemcpyDefault, c->st));
+    else
+      CK(cudaMemcpyAsync(dev + c->geo.off[l], flat + fo, n * sizeof(float), cudaMemcpyDefault, c->st));
+    fo += (long long)n;
+  }
+  return CC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cc_param_count(const cc_config* cfg, int* n_params) {
+  if (!n_params) return CC_EINVAL;
+  int e = validate(cfg);
+  if (e) return e;
+  *n_params = layout_of(arch_of(cfg)).total;
+  return CC_OK;
+}
+
+int cc_latent_count(const cc_config* cfg, int H, int W, int* n_latents) {
+  if (!n_latents || H < 1 || W < 1) return CC_EINVAL;
+  int e = validate(cfg);
+  if (e) return e;
+  *n_latents = geo_of(H, W).n_lat;
+  return CC_OK;
+}
+
+int cc_workspace_size(const cc_config* cfg, int H, int W, size_t* bytes) {
+  if (!bytes) return CC_EINVAL;
+  cc_ctx c;
+  int e = setup(&c, cfg, H, W);
+  if (e) return e;
+  *bytes = plan(&c, nullptr);
+  return CC_OK;
+}
+
+int cc_init_image(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
+                  const float* init_params, void* cuda_stream, cc_ctx** out) {
+  return init_common(cfg, rgb_hwc, H, W, init_params, cuda_stream, nullptr, 0, out);
+}
+
+int cc_init_image_ws(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
+                     const float* init_params, void* cuda_stream, void* device_workspace,
+                     size_t ws_bytes, cc_ctx** out) {
+  if (!device_workspace) return CC_EINVAL;
+  return init_common(cfg, rgb_hwc, H, W, init_params, cuda_stream, device_workspace, ws_bytes,
+                     out);
+}
+
+int cc_set_image(cc_ctx* c, const uint8_t* rgb_hwc) {
+  if (!c || !rgb_hwc) return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  CK(cudaMemcpyAsync(c->img_u8, rgb_hwc, (size_t)3 * c->HW, cudaMemcpyDefault, c->st));
+  CK(image_to_planar(c->img_u8, c->x, c->geo.H, c->geo.W, c->st));
+  return CC_OK;
+}
+
+int cc_encode_iters(cc_ctx* c, int n_iters) {
+  if (!c || n_iters < 0) return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  if (!c->g1) {
+    int e = build_graph(c, 1, &c->g1);
+    if (e) return e;
+  }
+  if (n_iters >= 16 && !c->g16) {
+    int e = build_graph(c, 16, &c->g16);
+    if (e) return e;
+  }
+  int left = n_iters;
+  while (left >= 16) {
+    CK(cudaGraphLaunch(c->g16, c->st));
+    left -= 16;
+  }
+  while (left > 0) {
+    CK(cudaGraphLaunch(c->g1, c->st));
+    --left;
+  }
+  c->iter += n_iters;
+  return CC_OK;
+}
+
+int cc_rd_cost(cc_ctx* c, int hard_round, double* D, double* R_bpp, double* cost) {
+  if (!c) return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  CK(enqueue_pass(c, c->st, hard_round ? 1 : 3, false, false, nullptr, false));
+  IterScalars h;
+  int e = sync_copy_scalars(c, &h);
+  if (e) return e;
+  if (D) *D = h.D;
+  if (R_bpp) *R_bpp = h.R;
+  if (cost) *cost = h.loss;
+  return std::isfinite(h.loss) ? CC_OK : CC_ENONFINITE;
+}
+
+int cc_decode(cc_ctx* c, float* rgb_out_hwc) {
+  if (!c || !rgb_out_hwc) return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  const Arch& a = c->arch;
+  const size_t HW = (size_t)c->HW;
+  CK(syn_upload(c->params, c->lay, a, c->st));
+  CK(quantize_launch(c->geo, c->y, c->yhat, c->noise, 1, c->sc, c->ste_start, c->cfg.seed, -1,
+                     c->st));
+  CK(up_forward(a, c->geo, c->yhat, c->up, c->st));
+  CK(syn_forward(a, c->geo, c->yhat, c->up, c->x, c->hbuf, c->dhbuf + (size_t)a.NR * 3 * HW,
+                 c->part_d, c->grid_syn, c->st));
+  CK(syn_decode(a, c->geo, c->hbuf + (size_t)a.NR * 3 * HW, c->dz, c->st));
+  CK(cudaMemcpyAsync(rgb_out_hwc, c->dz, 3 * HW * sizeof(float), cudaMemcpyDefault, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return CC_OK;
+}
+
+int cc_forward_backward(cc_ctx* c, const float* noise_override, int hard, float* grads_out,
+                        double* D, double* R_bpp) {
+  if (!c || hard < -1 || hard > 1) return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  int qmode = 0;
+  if (hard == 1) {
+    qmode = 1;
+  } else if (noise_override) {
+    int e = copy_latents(c, c->noise, const_cast<float*>(noise_override), false);
+    if (e) return e;
+    qmode = 2;
+  } else if (hard == 0) {
+    qmode = 3;
+  }
+  CK(enqueue_pass(c, c->st, qmode, true, false, c->grad_scratch, false));
+  if (grads_out)
+    CK(cudaMemcpyAsync(grads_out, c->grad_scratch,
+                       (size_t)(c->geo.n_lat + c->lay.total) * sizeof(float), cudaMemcpyDefault,
+                       c->st));
+  IterScalars h;
+  int e = sync_copy_scalars(c, &h);
+  if (e) return e;
+  if (D) *D = h.D;
+  if (R_bpp) *R_bpp = h.R;
+  return std::isfinite(h.loss) ? CC_OK : CC_ENONFINITE;
+}
+
+int cc_get_grads(cc_ctx* c, const float* noise_override, float* grads_out) {
+  return cc_forward_backward(c, noise_override, -1, grads_out, nullptr, nullptr);
+}
+
+int cc_get_losses(cc_ctx* c, int first, int count, double* out) {
+  if (!c || !out || first < 0 || count < 0 || first + count > c->iter ||
+      first < c->iter - kLogCap)
+    return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  std::vector<double> all((size_t)kLogCap * 3);
+  CK(cudaMemcpyAsync(all.data(), c->log, all.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                     c->st));
+  CK(cudaStreamSynchronize(c->st));
+  std::vector<double> pick((size_t)count * 3);
+  for (int k = 0; k < count; ++k)
+    for (int j = 0; j < 3; ++j) pick[k * 3 + j] = all[((first + k) % kLogCap) * 3 + j];
+  CK(cudaMemcpy(out, pick.data(), pick.size() * sizeof(double), cudaMemcpyDefault));
+  for (double v : pick)
+    if (!std::isfinite(v)) return CC_ENONFINITE;
+  return CC_OK;
+}
+
+int cc_set_latents(cc_ctx* c, const float* y_flat) {
+  if (!c || !y_flat) return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  return copy_latents(c, c->y, const_cast<float*>(y_flat), false);
+}
+
+int cc_get_latents(cc_ctx* c, float* y_flat) {
+  if (!c || !y_flat) return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  int e = copy_latents(c, c->y, y_flat, true);
+  if (e) return e;
+  CK(cudaStreamSynchronize(c->st));
+  return CC_OK;
+}
+
+int cc_set_params(cc_ctx* c, const float* params) {
+  if (!c || !params) return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  CK(cudaMemcpyAsync(c->params, params, (size_t)c->lay.total * sizeof(float), cudaMemcpyDefault,
+                     c->st));
+  return CC_OK;
+}
+
+int cc_get_params(cc_ctx* c, float* params) {
+  if (!c || !params) return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  CK(cudaMemcpyAsync(params, c->params, (size_t)c->lay.total * sizeof(float), cudaMemcpyDefault,
+                     c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return CC_OK;
+}
+
+int cc_profile_phases(cc_ctx* c, int reps, float* ms_out) {
+  if (!c || !ms_out || reps < 1) return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  cudaEvent_t ev[8];
+  for (int k = 0; k < 8; ++k) CK(cudaEventCreate(&ev[k]));
+  double acc[CC_N_PHASES] = {0};
+  int rc = CC_OK;
+  for (int r = 0; r < reps && rc == CC_OK; ++r) {
+    cudaError_t e = enqueue_pass(c, c->st, 0, true, true, nullptr, true, ev);
+    if (e != cudaSuccess) { rc = fail_cuda(e, "profiled pass"); break; }
+    if ((e = cudaEventSynchronize(ev[7])) != cudaSuccess) { rc = fail_cuda(e, "event sync"); break; }
+    for (int k = 0; k < CC_N_PHASES; ++k) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      acc[k] += ms;
+    }
+    c->iter += 1;
+  }
+  for (int k = 0; k < 8; ++k) cudaEventDestroy(ev[k]);
+  if (rc) return rc;
+  for (int k = 0; k < CC_N_PHASES; ++k) ms_out[k] = (float)(acc[k] / reps);
+  return CC_OK;
+}
+
+int cc_graph_kernel_count(cc_ctx* c, int* n_kernels) {
+  if (!c || !n_kernels) return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  if (!c->g1) {
+    int e = build_graph(c, 1, &c->g1);
+    if (e) return e;
+  }
+  *n_kernels = c->kernels_per_iter;
+  return CC_OK;
+}
+
+int cc_iteration(cc_ctx* c, int* iter) {
+  if (!c || !iter) return CC_EINVAL;
+  *iter = c->iter;
+  return CC_OK;
+}
+
+int cc_noise(cc_ctx* c, int iter, float* out) {
+  if (!c || !out || iter < 0) return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  CK(quantize_launch(c->geo, c->y, c->yhat, c->noise, 4, c->sc, c->ste_start, c->cfg.seed, iter,
+                     c->st));
+  int e = copy_latents(c, c->yhat, out, true);
+  if (e) return e;
+  CK(cudaStreamSynchronize(c->st));
+  return CC_OK;
+}
+
+int cc_get_state(cc_ctx* c, void* buf, size_t* nbytes) {
+  if (!c || !nbytes) return CC_EINVAL;
+  const size_t nl = (size_t)c->geo.n_lat, np = (size_t)c->lay.total;
+  const size_t need = sizeof(StateHeader) + (3 * nl + 3 * np) * sizeof(float);
+  if (!buf) {
+    *nbytes = need;
+    return CC_OK;
+  }
+  if (*nbytes < need) return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  StateHeader hd{};
+  hd.magic = kStateMagic; hd.version = kStateVersion;
+  hd.H = c->geo.H; hd.W = c->geo.W; hd.n_lat = (int)nl; hd.n_params = (int)np;
+  hd.iter = c->iter; hd.seed = c->cfg.seed;
+  const int ar[8] = {c->arch.N, c->arch.NL, c->arch.K, c->arch.per_level, c->arch.C, c->arch.NR,
+                     kLevels, 0};
+  memcpy(hd.arch, ar, sizeof(ar));
+  char* p = (char*)buf;
+  memcpy(p, &hd, sizeof(hd));
+  float* f = (float*)(p + sizeof(hd));
+  int e;
+  if ((e = copy_latents(c, c->y, f, true))) return e;
+  CK(cudaMemcpyAsync(f + nl, c->params, np * sizeof(float), cudaMemcpyDeviceToHost, c->st));
+  if ((e = copy_latents(c, c->my, f + nl + np, true))) return e;
+  if ((e = copy_latents(c, c->vy, f + 2 * nl + np, true))) return e;
+  CK(cudaMemcpyAsync(f + 3 * nl + np, c->mp, np * sizeof(float), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(f + 3 * nl + 2 * np, c->vp, np * sizeof(float), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  *nbytes = need;
+  return CC_OK;
+}
+
+int cc_set_state(cc_ctx* c, const void* buf, size_t nbytes) {
+  if (!c || !buf || nbytes < sizeof(StateHeader)) return CC_EINVAL;
+  StateHeader hd;
+  memcpy(&hd, buf, sizeof(hd));
+  const size_t nl = (size_t)c->geo.n_lat, np = (size_t)c->lay.total;
+  const size_t need = sizeof(StateHeader) + (3 * nl + 3 * np) * sizeof(float);
+  const int ar[8] = {c->arch.N, c->arch.NL, c->arch.K, c->arch.per_level, c->arch.C, c->arch.NR,
+                     kLevels, 0};
+  if (hd.magic != kStateMagic || hd.version != kStateVersion || nbytes != need ||
+      hd.H != c->geo.H || hd.W != c->geo.W || hd.n_lat != (int)nl || hd.n_params != (int)np ||
+      memcmp(hd.arch, ar, sizeof(ar)) != 0 || hd.iter < 0)
+    return CC_ESTATE;
+  CK(cudaSetDevice(c->dev));
+  // the blob may be pageable host memory: stage through a host copy with a lifetime
+  std::vector<float> f((3 * nl + 3 * np));
+  memcpy(f.data(), (const char*)buf + sizeof(hd), f.size() * sizeof(float));
+  int e;
+  if ((e = copy_latents(c, c->y, f.data(), false))) return e;
+  CK(cudaMemcpyAsync(c->params, f.data() + nl, np * sizeof(float), cudaMemcpyHostToDevice, c->st));
+  if ((e = copy_latents(c, c->my, f.data() + nl + np, false))) return e;
+  if ((e = copy_latents(c, c->vy, f.data() + 2 * nl + np, false))) return e;
+  CK(cudaMemcpyAsync(c->mp, f.data() + 3 * nl + np, np * sizeof(float), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->vp, f.data() + 3 * nl + 2 * np, np * sizeof(float), cudaMemcpyHostToDevice,
+                     c->st));
+  IterScalars sc{};
+  sc.t = hd.iter;
+  CK(cudaMemcpyAsync(c->sc, &sc, sizeof(sc), cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  c->iter = hd.iter;
+  return CC_OK;
+}
+
+void cc_free(cc_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->dev);
+  if (c->st) cudaStreamSynchronize(c->st);
+  if (c->g1) cudaGraphExecDestroy(c->g1);
+  if (c->g16) cudaGraphExecDestroy(c->g16);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->own_mem && c->mem) cudaFree(c->mem);
+  delete c;
+}
+
+const char* cc_strerror(int code) {
+  switch (code) {
+    case CC_OK: return "ok";
+    case CC_EINVAL: return "invalid argument or unsupported configuration";
+    case CC_ENOMEM: return "out of device memory or workspace too small";
+    case CC_ECUDA: return "CUDA runtime error";
+    case CC_ETIMEOUT: return "bounded device wait timed out";
+    case CC_ENONFINITE: return "non-finite loss";
+    case CC_ESTATE: return "state blob does not match this context";
+    default: return "unknown error";
+  }
+}
+
+const char* cc_last_cuda_error(void) { return g_err; }
+
+}  // extern "C"

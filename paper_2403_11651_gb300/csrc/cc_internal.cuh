@@ -1,0 +1,116 @@
+// Internal declarations shared by the translation units of the Cool-chic library.
+// Everything here is host/device plumbing; the arithmetic lives in the .cu files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+namespace cc {
+
+constexpr int kLevels = 7;        // L of Sec. II "Decoding" item i (fixed by Table 1 "7-C")
+constexpr int kArmTile = 128;     // latents per ARM tile (= threads per ARM block)
+constexpr int kPixTile = 256;     // pixels per synthesis block
+constexpr int kLogCap = 4096;     // per-iteration loss log entries kept on the device
+
+// Latent pyramid geometry.  Every latent-shaped buffer holds the L planes back to back,
+// each plane row-major with row stride w_l, starting at a 32-float aligned offset.
+struct Geo {
+  int H, W;
+  int h[kLevels], w[kLevels];
+  long long off[kLevels];
+  long long n_pad;   // floats in a latent-shaped buffer
+  int n_lat;         // sum_l h_l w_l
+};
+
+// Architecture (Table 1 notation) as the kernels see it.
+struct Arch {
+  int N;        // ARM context size and width
+  int NL;       // N-N-LinR layers
+  int K;        // upsampling kernel
+  int per_level;
+  int C;        // synthesis hidden width
+  int NR;       // 3x3 residual layers
+};
+
+// Offsets of the flat parameter vector (same order as include/coolchic.h).
+struct Layout {
+  int n_arm;          // [0, n_arm): ARM
+  int up0, n_up;      // [up0, up0 + n_up * K*K): upsampling filters
+  int syn0, n_syn;    // [syn0, syn0 + n_syn): synthesis
+  int total;
+};
+
+// A block of per-CTA partial sums of some parameter gradients: rows x cols floats,
+// row stride `stride`; column j adds into virtual gradient slot col0 + j, times scale.
+struct Section {
+  const float* part;
+  int rows, cols, stride, col0;
+  float scale;
+};
+constexpr int kMaxSections = 12;
+struct SectionTable {
+  Section s[kMaxSections];
+  int n;
+};
+
+// Scalars of the current iteration, written on the device.
+struct IterScalars {
+  int t;            // index of the current iteration (0-based)
+  int pad;
+  double D, R, loss;
+};
+
+// ---- launchers (each returns the cudaError_t of its launch) ----
+// ARM (cc_arm.cu)
+cudaError_t arm_upload(const float* d_params, int n_arm, const int2* d_offsets, int N,
+                       cudaStream_t st);
+cudaError_t arm_launch(const Arch& a, bool backward, const float* yhat, const Geo& g,
+                       const int2* tiles, int n_tiles, int grid, float* dctx, float* gself,
+                       float* part_grad, float* part_bits, cudaStream_t st);
+int arm_blocks_per_sm(const Arch& a, bool backward);
+cudaError_t arm_prepare(const Arch& a);   // kernel attributes; call once before capture
+size_t arm_smem_bytes(const Arch& a, bool backward);
+
+// synthesis + upsampling (cc_syn.cu)
+struct UpPlan {
+  // planes of level l at resolution j (j < l); j == l is the latent plane itself
+  float* plane[kLevels][kLevels];
+  float* dplane[kLevels][kLevels];
+};
+cudaError_t syn_upload(const float* d_params, const Layout& lay, const Arch& a,
+                       cudaStream_t st);
+cudaError_t up_forward(const Arch& a, const Geo& g, const float* yhat, const UpPlan& up,
+                       cudaStream_t st);
+cudaError_t up_backward(const Arch& a, const Geo& g, const float* yhat, const UpPlan& up,
+                        float* gsyn, float* part_up, int grid, cudaStream_t st);
+cudaError_t syn_forward(const Arch& a, const Geo& g, const float* yhat, const UpPlan& up,
+                        const float* x, float* hbuf, float* dxhat, float* part_d, int grid,
+                        cudaStream_t st);
+cudaError_t syn_backward(const Arch& a, const Geo& g, const float* yhat, const UpPlan& up,
+                         float* hbuf, float* dhbuf, float* dz, float* gsyn,
+                         float* part_conv, float* part_syn, int grid, cudaStream_t st);
+cudaError_t syn_decode(const Arch& a, const Geo& g, const float* hbuf_last, float* out_hwc,
+                       cudaStream_t st);
+int syn1x1_partial_cols(const Arch& a);
+cudaError_t syn_prepare(const Arch& a);   // kernel attributes; call once before capture
+
+// iteration bookkeeping (cc_iter.cu)
+cudaError_t quantize_launch(const Geo& g, const float* y, float* yhat, const float* noise,
+                            int mode, const IterScalars* sc, int ste_start, uint64_t seed,
+                            int iter_override, cudaStream_t st);
+cudaError_t reduce_sections(const SectionTable& tab, float* part2, int n_virtual, int slices,
+                            cudaStream_t st);
+cudaError_t param_update(const Layout& lay, const Arch& a, const float* part2, int slices,
+                         float* params, float* m, float* v, float* grad_out, bool apply,
+                         float lr, const IterScalars* sc, cudaStream_t st);
+cudaError_t latent_update(const Geo& g, const Arch& a, const int2* d_offsets,
+                          const float* gsyn, const float* gself, const float* dctx,
+                          float rate_scale, float* y, float* m, float* v, float* grad_out,
+                          bool apply, float lr, const IterScalars* sc, cudaStream_t st);
+cudaError_t finish_iteration(const float* part_d, int nd, const float* part_bits, int nb,
+                             double d_scale, double r_scale, double lam, IterScalars* sc,
+                             double* log, bool advance, cudaStream_t st);
+cudaError_t image_to_planar(const uint8_t* rgb_hwc, float* x, int H, int W, cudaStream_t st);
+
+}  // namespace cc

@@ -1,0 +1,288 @@
+// Quantisation proxy, gradient assembly and Adam (Sec. II "Encoding"; Adam of Kingma & Ba
+// as used in Sec. IV-B), plus the deterministic reductions of the per-CTA partial sums.
+#include "cc_internal.cuh"
+
+namespace cc {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, Sec. 3.3): ten rounds of
+//   (x0, x1, x2, x3) <- (hi(M1 x2) ^ x1 ^ k0, lo(M1 x2), hi(M0 x0) ^ x3 ^ k1, lo(M0 x0))
+// with the key bumped by the Weyl constants after each round.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint2 k) {
+  constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(M0, x.x), lo0 = M0 * x.x;
+    const uint32_t hi1 = __umulhi(M1, x.z), lo1 = M1 * x.z;
+    x = make_uint4(hi1 ^ x.y ^ k.x, lo1, hi0 ^ x.w ^ k.y, lo0);
+    k.x += W0;
+    k.y += W1;
+  }
+  return x;
+}
+
+// Modes: 0 follow the schedule, 1 rint, 2 y + given noise, 3 y + Philox noise,
+//        4 write the Philox noise itself.
+// Noise of latent i of level l at iteration t: word (i mod 4) of
+// Philox4x32-10(counter (i div 4, l, t, 0), key (seed lo, seed hi)), u = (w >> 8) 2^-24 - 1/2.
+__global__ void __launch_bounds__(256) k_quantize(Geo g, const float* __restrict__ y,
+                                                  float* __restrict__ yhat,
+                                                  const float* __restrict__ noise, int mode,
+                                                  const IterScalars* sc, int ste_start,
+                                                  uint2 key, int iter_override) {
+  const int l = blockIdx.y;
+  const int n = g.h[l] * g.w[l];
+  const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (i0 >= n) return;
+  const int t = iter_override >= 0 ? iter_override : sc->t;
+  int m = mode;
+  if (m == 0) m = t >= ste_start ? 1 : 3;
+  const long long base = g.off[l];
+  uint4 r = make_uint4(0, 0, 0, 0);
+  if (m >= 3) r = philox4x32_10(make_uint4((uint32_t)(i0 >> 2), (uint32_t)l, (uint32_t)t, 0u), key);
+  const uint32_t words[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int i = i0 + e;
+    if (i >= n) break;
+    const float yv = y[base + i];
+    float out;
+    if (m == 1) {
+      out = rintf(yv);
+    } else if (m == 2) {
+      out = yv + noise[base + i];
+    } else {
+      const float u = (float)(words[e] >> 8) * 5.9604644775390625e-08f - 0.5f;
+      out = m == 4 ? u : yv + u;
+    }
+    yhat[base + i] = out;
+  }
+}
+
+cudaError_t quantize_launch(const Geo& g, const float* y, float* yhat, const float* noise,
+                            int mode, const IterScalars* sc, int ste_start, uint64_t seed,
+                            int iter_override, cudaStream_t st) {
+  int maxn = 0;
+  for (int l = 0; l < kLevels; ++l) maxn = g.h[l] * g.w[l] > maxn ? g.h[l] * g.w[l] : maxn;
+  const int groups = (maxn + 3) / 4;
+  dim3 grid((groups + 255) / 256, kLevels);
+  const uint2 key = make_uint2((uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32));
+  k_quantize<<<grid, 256, 0, st>>>(g, y, yhat, noise, mode, sc, ste_start, key, iter_override);
+  return cudaGetLastError();
+}
+
+// part2[slice][col0 + j] = scale * sum over the slice's rows of part[row][j], rows summed
+// in a fixed tree (8 interleaved sequential sums, then those 8 in order).
+__global__ void __launch_bounds__(256) k_reduce_sections(SectionTable tab, float* part2,
+                                                         int n_virtual) {
+  const Section s = tab.s[blockIdx.z];
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  const int slices = gridDim.y, slice = blockIdx.y;
+  const int rps = (s.rows + slices - 1) / slices;
+  const int r0 = slice * rps;
+  const int r1 = min(s.rows, r0 + rps);
+  float acc = 0.f;
+  if (j < s.cols)
+    for (int r = r0 + (int)threadIdx.y; r < r1; r += 8) acc += s.part[(long long)r * s.stride + j];
+  __shared__ float sm[8][33];
+  sm[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && j < s.cols) {
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += sm[k][threadIdx.x];
+    part2[(long long)slice * n_virtual + s.col0 + j] = t * s.scale;
+  }
+}
+
+cudaError_t reduce_sections(const SectionTable& tab, float* part2, int n_virtual, int slices,
+                            cudaStream_t st) {
+  int maxc = 0;
+  for (int i = 0; i < tab.n; ++i) maxc = tab.s[i].cols > maxc ? tab.s[i].cols : maxc;
+  dim3 grid((maxc + 31) / 32, slices, tab.n);
+  k_reduce_sections<<<grid, dim3(32, 8), 0, st>>>(tab, part2, n_virtual);
+  return cudaGetLastError();
+}
+
+struct AdamStep {
+  float lr, inv_bc1, inv_sqrt_bc2;
+};
+
+__device__ __forceinline__ AdamStep adam_step(int t, float lr) {
+  // bias corrections of step t + 1, in double
+  const double s = (double)(t + 1);
+  AdamStep a;
+  a.lr = lr;
+  a.inv_bc1 = (float)(1.0 / (1.0 - pow(0.9, s)));
+  a.inv_sqrt_bc2 = (float)(1.0 / sqrt(1.0 - pow(0.999, s)));
+  return a;
+}
+
+__device__ __forceinline__ void adam_apply(float& p, float& m, float& v, float g,
+                                           const AdamStep& a) {
+  m = 0.9f * m + 0.1f * g;
+  v = 0.999f * v + 0.001f * g * g;
+  p -= a.lr * (m * a.inv_bc1) / (sqrtf(v) * a.inv_sqrt_bc2 + 1e-8f);
+}
+
+struct VirtualMap {
+  int n_arm, up0, syn0, n1x1, nconv, K2, n_up, per_level;
+  int vsyn, vconv, vup, n_virtual;
+};
+
+__global__ void __launch_bounds__(128) k_param_update(VirtualMap vm, const float* part2,
+                                                      int slices, float* params, float* m,
+                                                      float* v, float* grad_out, int apply,
+                                                      float lr, const IterScalars* sc,
+                                                      int total, AdamStep* step_out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const AdamStep st = adam_step(sc->t, lr);
+  if (j == 0 && step_out) *step_out = st;
+  if (j >= total) return;
+  int vs[kLevels - 1];
+  int nv = 1;
+  if (j < vm.n_arm) {
+    vs[0] = j;
+  } else if (j < vm.up0 + vm.n_up * vm.K2) {
+    const int fi = (j - vm.up0) / vm.K2, u = (j - vm.up0) % vm.K2;
+    if (vm.per_level) {
+      vs[0] = vm.vup + fi * vm.K2 + u;
+    } else {
+      nv = kLevels - 1;
+      for (int l = 0; l < kLevels - 1; ++l) vs[l] = vm.vup + l * vm.K2 + u;
+    }
+  } else if (j < vm.syn0 + vm.n1x1) {
+    vs[0] = vm.vsyn + (j - vm.syn0);
+  } else {
+    vs[0] = vm.vconv + (j - vm.syn0 - vm.n1x1);
+  }
+  float g = 0.f;
+  for (int k = 0; k < nv; ++k) {
+    float t = 0.f;
+    for (int s = 0; s < slices; ++s) t += part2[(long long)s * vm.n_virtual + vs[k]];
+    g += t;
+  }
+  if (grad_out) grad_out[j] = g;
+  if (apply) adam_apply(params[j], m[j], v[j], g, st);
+}
+
+cudaError_t param_update(const Layout& lay, const Arch& a, const float* part2, int slices,
+                         float* params, float* m, float* v, float* grad_out, bool apply,
+                         float lr, const IterScalars* sc, cudaStream_t st) {
+  VirtualMap vm;
+  vm.n_arm = lay.n_arm; vm.up0 = lay.up0; vm.syn0 = lay.syn0;
+  vm.n1x1 = 11 * a.C + 3; vm.nconv = a.NR * 84; vm.K2 = a.K * a.K; vm.n_up = lay.n_up;
+  vm.per_level = a.per_level;
+  vm.vsyn = lay.n_arm; vm.vconv = vm.vsyn + vm.n1x1; vm.vup = vm.vconv + vm.nconv;
+  vm.n_virtual = vm.vup + (kLevels - 1) * vm.K2;
+  k_param_update<<<(lay.total + 127) / 128, 128, 0, st>>>(vm, part2, slices, params, m, v,
+                                                          grad_out, apply ? 1 : 0, lr, sc,
+                                                          lay.total, nullptr);
+  return cudaGetLastError();
+}
+
+// Gradient of a latent: the synthesis path, plus lambda/(HW) times the rate terms in
+// which it appears, as the coded symbol (gself) and in the context of every latent p
+// whose causal neighbourhood contains it (dctx of p at the matching slot).
+__global__ void __launch_bounds__(256) k_latent_update(Geo g, const int2* __restrict__ offs,
+                                                       int N, const float* __restrict__ gsyn,
+                                                       const float* __restrict__ gself,
+                                                       const float* __restrict__ dctx,
+                                                       float rate_scale, float* y, float* m,
+                                                       float* v, float* grad_out, int apply,
+                                                       float lr, const IterScalars* sc) {
+  const int l = blockIdx.y;
+  const int w = g.w[l], h = g.h[l];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= h * w) return;
+  const int r = i / w, c = i - r * w;
+  const long long q = g.off[l] + i;
+  float gr = __ldg(gself + q);
+  for (int k = 0; k < N; ++k) {
+    const int2 o = __ldg(offs + k);
+    const int pr = r - o.x, pc = c - o.y;
+    if (pr < h && pc >= 0 && pc < w)
+      gr += __ldg(dctx + (long long)k * g.n_pad + g.off[l] + pr * w + pc);
+  }
+  const float gt = __ldg(gsyn + q) + rate_scale * gr;
+  if (grad_out) {
+    long long fo = 0;
+    for (int k = 0; k < l; ++k) fo += (long long)g.h[k] * g.w[k];
+    grad_out[fo + i] = gt;
+  }
+  if (apply) {
+    const AdamStep st = adam_step(sc->t, lr);
+    float yv = y[q], mv = m[q], vv = v[q];
+    adam_apply(yv, mv, vv, gt, st);
+    y[q] = yv; m[q] = mv; v[q] = vv;
+  }
+}
+
+cudaError_t latent_update(const Geo& g, const Arch& a, const int2* d_offsets,
+                          const float* gsyn, const float* gself, const float* dctx,
+                          float rate_scale, float* y, float* m, float* v, float* grad_out,
+                          bool apply, float lr, const IterScalars* sc, cudaStream_t st) {
+  int maxn = 0;
+  for (int l = 0; l < kLevels; ++l) maxn = g.h[l] * g.w[l] > maxn ? g.h[l] * g.w[l] : maxn;
+  dim3 grid((maxn + 255) / 256, kLevels);
+  k_latent_update<<<grid, 256, 0, st>>>(g, d_offsets, a.N, gsyn, gself, dctx, rate_scale, y,
+                                        m, v, grad_out, apply ? 1 : 0, lr, sc);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_finish(const float* part_d, int nd,
+                                                const float* part_bits, int nb, double d_scale,
+                                                double r_scale, double lam, IterScalars* sc,
+                                                double* log, int advance) {
+  __shared__ double sd[256], sb[256];
+  double a = 0.0, b = 0.0;
+  for (int k = threadIdx.x; k < nd; k += 256) a += (double)part_d[k];
+  for (int k = threadIdx.x; k < nb; k += 256) b += (double)part_bits[k];
+  sd[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      sd[threadIdx.x] += sd[threadIdx.x + s];
+      sb[threadIdx.x] += sb[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double D = sd[0] * d_scale, R = sb[0] * r_scale;
+    sc->D = D;
+    sc->R = R;
+    sc->loss = D + lam * R;
+    const int t = sc->t;
+    double* e = log + 3 * (long long)(t % kLogCap);
+    e[0] = D;
+    e[1] = R;
+    e[2] = D + lam * R;
+    if (advance) sc->t = t + 1;
+  }
+}
+
+cudaError_t finish_iteration(const float* part_d, int nd, const float* part_bits, int nb,
+                             double d_scale, double r_scale, double lam, IterScalars* sc,
+                             double* log, bool advance, cudaStream_t st) {
+  k_finish<<<1, 256, 0, st>>>(part_d, nd, part_bits, nb, d_scale, r_scale, lam, sc, log,
+                              advance ? 1 : 0);
+  return cudaGetLastError();
+}
+
+__global__ void k_image_to_planar(const uint8_t* __restrict__ rgb, float* __restrict__ x,
+                                  int HW) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) x[c * HW + p] = (float)rgb[p * 3 + c] / 255.0f;
+  }
+}
+
+cudaError_t image_to_planar(const uint8_t* rgb_hwc, float* x, int H, int W, cudaStream_t st) {
+  const int HW = H * W;
+  const int blocks = (HW + 255) / 256 < 4096 ? (HW + 255) / 256 : 4096;
+  k_image_to_planar<<<blocks, 256, 0, st>>>(rgb_hwc, x, HW);
+  return cudaGetLastError();
+}
+
+}  // namespace cc

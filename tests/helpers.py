@@ -1,0 +1,93 @@
+"""Shared set-up for the parity tests: the same seeded inputs handed to the CUDA library
+(through its C ABI binding) and to the FP64 oracle."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from oracle import coolchic as oc
+from paper_2403_11651_gb300 import coolchic as cc
+from paper_2403_11651_gb300 import synthetic as syn
+
+ARCHS = {
+    # name: (arm_ctx, arm_layers, up_kernel, up_per_level, syn_hidden, syn_res3x3)
+    "c1": (8, 2, 8, 1, 8, 2),
+    "c2": (24, 2, 8, 1, 40, 2),
+    "t300": (8, 1, 4, 0, 8, 1),
+    "t1079": (16, 2, 4, 0, 16, 2),
+}
+
+
+def config_dict(arch: str, lam=1e-3, lr=1e-2, total_iters=100, ste_frac=0.0):
+    n, nl, k, pl, c, nr = ARCHS[arch]
+    return dict(levels=7, arm_ctx=n, arm_layers=nl, up_kernel=k, up_per_level=bool(pl),
+                syn_hidden=c, syn_res3x3=nr, lam=lam, lr=lr, total_iters=total_iters,
+                ste_frac=ste_frac)
+
+
+def oracle_arch(d: dict) -> oc.Arch:
+    return oc.Arch(levels=7, arm_ctx=d["arm_ctx"], arm_layers=d["arm_layers"],
+                   up_kernel=d["up_kernel"], up_per_level=bool(d["up_per_level"]),
+                   syn_hidden=d["syn_hidden"], syn_res3x3=d["syn_res3x3"])
+
+
+class Pair:
+    """A CUDA context and an oracle encoder built from identical inputs."""
+
+    def __init__(self, d: dict, H: int, W: int, seed: int = 0, random_state: bool = False,
+                 state_scale: float = 1.5):
+        self.d, self.H, self.W, self.seed = d, H, W, seed
+        self.cfg = cc.make_config(d, seed=seed)
+        self.rgb = syn.synthetic_image(H, W, seed)
+        self.init = syn.initial_parameters(syn.ArchSizes.from_config(d), seed)
+        rng = np.random.default_rng(seed + 1000)
+        if random_state:
+            for k in self.init:   # non-zero biases so every gradient term is exercised
+                if ".b" in k:
+                    self.init[k] = rng.uniform(-0.1, 0.1, self.init[k].shape).astype(np.float32)
+        self.flat_init = cc.flatten_params(self.init, self.cfg)
+        self.n_params = cc.cc_param_count(self.cfg)
+        self.n_lat = cc.cc_latent_count(self.cfg, H, W)
+        self.ctx = cc.cc_init_image(self.cfg, self.rgb, H, W, self.flat_init)
+        self.oracle = oc.OracleEncoder(
+            self.rgb, oracle_arch(d),
+            oc.Train(lam=d["lam"], lr=d["lr"], total_iters=d["total_iters"],
+                     ste_frac=d["ste_frac"], seed=seed), self.init)
+        if random_state:
+            y = [rng.normal(0, state_scale, s).astype(np.float32) for s in cc.level_shapes(H, W)]
+            self.set_latents(y)
+
+    def set_latents(self, levels):
+        flat = np.concatenate([np.asarray(a, np.float32).ravel() for a in levels])
+        cc.cc_set_latents(self.ctx, flat)
+        self.oracle.set_latents([a.astype(np.float64) for a in levels])
+
+    def gpu_grads(self, noise_levels=None, hard=-1):
+        noise = None
+        if noise_levels is not None:
+            noise = np.concatenate([np.asarray(a, np.float32).ravel() for a in noise_levels])
+        g, D, R = cc.cc_forward_backward(self.ctx, self.n_lat + self.n_params, noise, hard)
+        return (cc.split_latents(g[:self.n_lat], self.H, self.W),
+                cc.unflatten_params(g[self.n_lat:], self.cfg), D, R)
+
+    def oracle_grads(self, noise_levels=None, hard=False):
+        u = None
+        if noise_levels is not None:
+            u = [torch.tensor(np.asarray(a, np.float64)) for a in noise_levels]
+        loss, D, R, grads = self.oracle.loss_and_grads(u_levels=u, hard=hard)
+        gy = [g.numpy() for g in grads[:7]]
+        gp = {n: g.numpy() for n, g in zip(self.oracle.names, grads[7:])}
+        return gy, gp, D, R
+
+    def close(self):
+        cc.cc_free(self.ctx)
+        self.ctx = None
+
+
+def assert_group_close(got, ref, rtol, name=""):
+    """max |got - ref| <= rtol * max |ref| over the group (scale-relative)."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    scale = float(np.max(np.abs(ref))) if ref.size else 0.0
+    err = float(np.max(np.abs(got - ref))) if ref.size else 0.0
+    assert err <= rtol * max(scale, 1e-30), f"{name}: max err {err:.3e} vs scale {scale:.3e}"

@@ -1,0 +1,106 @@
+"""C ABI checks that need no GPU: the library builds for sm_103a, loads, exports every
+entry point include/coolchic.h declares, and its host-side logic (parameter layout, latent
+counts, configuration validation) matches the paper and the binding."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import coolchic as oc
+from paper_2403_11651_gb300 import coolchic as cc
+from paper_2403_11651_gb300 import synthetic as syn
+
+from .helpers import config_dict
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    with open(os.path.join(ROOT, "include", "coolchic.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(cc_\w+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return cc.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_symbols()
+    assert len(names) >= 20
+    raw = ctypes.CDLL(cc.library_path())
+    for n in names:
+        assert hasattr(raw, n), n
+    assert set(names) == set(cc.EXPORTED)
+
+
+def test_param_count_reproduces_table1(lib, golden_dir):
+    import json
+    with open(os.path.join(golden_dir, "table1_fig5.json")) as f:
+        rows = json.load(f)["table1"]
+    for r in rows:
+        d = dict(levels=7, arm_ctx=r["arm_ctx"], arm_layers=r["arm_layers"],
+                 up_kernel=r["up_kernel"], up_per_level=False, syn_hidden=r["syn_hidden"],
+                 syn_res3x3=r["syn_res3x3"], lam=1e-3, lr=1e-2, total_iters=10, ste_frac=0.0)
+        assert cc.cc_param_count(cc.make_config(d)) == r["params"]
+    assert cc.cc_param_count(cc.make_config(config_dict("c2"))) == 1925 - 64 + 6 * 64
+
+
+@pytest.mark.parametrize("H,W", [(512, 768), (256, 256), (67, 45), (1, 1), (2048, 2048)])
+def test_latent_count(lib, H, W):
+    n = cc.cc_latent_count(cc.make_config(config_dict("c2")), H, W)
+    assert n == sum(h * w for h, w in oc.level_shapes(H, W))
+    if (H, W) == (512, 768):
+        assert n == 524256
+
+
+@pytest.mark.parametrize("field,value", [("levels", 6), ("arm_ctx", 12), ("arm_layers", 3),
+                                         ("up_kernel", 6), ("syn_hidden", 32),
+                                         ("syn_res3x3", 0), ("ste_frac", 1.5), ("lr", 0.0),
+                                         ("total_iters", -1)])
+def test_invalid_config_rejected(lib, field, value):
+    cfg = cc.make_config(config_dict("c2"))
+    setattr(cfg, field, value)
+    with pytest.raises(cc.CCError) as e:
+        cc.cc_param_count(cfg)
+    assert e.value.code == cc.CC_EINVAL
+
+
+def test_bad_sizes_rejected(lib):
+    cfg = cc.make_config(config_dict("c1"))
+    for H, W in [(0, 4), (4, 0), (-3, 5)]:
+        with pytest.raises(cc.CCError) as e:
+            cc.cc_latent_count(cfg, H, W)
+        assert e.value.code == cc.CC_EINVAL
+
+
+def test_strerror(lib):
+    assert cc.cc_strerror(0) == "ok"
+    for code in (-1, -2, -3, -4, -5, -6):
+        assert cc.cc_strerror(code) != "unknown error"
+    assert cc.cc_strerror(-99) == "unknown error"
+
+
+@pytest.mark.parametrize("arch", ["c1", "c2", "t300", "t1079"])
+def test_binding_layout_matches_oracle_order(arch):
+    d = config_dict(arch)
+    cfg = cc.make_config(d)
+    a = oc.Arch(arm_ctx=d["arm_ctx"], arm_layers=d["arm_layers"], up_kernel=d["up_kernel"],
+                up_per_level=d["up_per_level"], syn_hidden=d["syn_hidden"],
+                syn_res3x3=d["syn_res3x3"])
+    assert cc.param_layout(cfg) == [(n, tuple(s)) for n, s in oc.param_shapes(a)]
+    init = syn.initial_parameters(syn.ArchSizes.from_config(d), 3)
+    flat = cc.flatten_params(init, cfg)
+    back = cc.unflatten_params(flat, cfg)
+    for k in init:
+        assert np.array_equal(back[k], init[k])
+
+
+def test_config_files_load():
+    for name in ("c1", "c2", "c5"):
+        d = cc.load_config(name)
+        cfg = cc.make_config(d)
+        assert cfg.levels == 7 and cfg.total_iters == d["total_iters"]
