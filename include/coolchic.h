@@ -20,6 +20,9 @@
  *     (or, for asynchronous calls, before any later call on the same context);
  *   - the context owns its device memory (or borrows a caller workspace) until cc_free;
  *   - all GPU work of a context is issued on the stream given to cc_init_image;
+ *   - the contexts of one device share its constant-memory weight banks (every pass loads
+ *     its own weights first): passes of two contexts must not overlap in time, so issue
+ *     them on one stream or synchronise between them;
  *   - the images are 8-bit RGB, row-major, channels last (H x W x 3); the library uses
  *     x = v / 255 in float32.
  *

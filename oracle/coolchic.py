@@ -311,6 +311,50 @@ def forward(x, y_levels, P, arch: Arch, lam: float, u_levels=None, hard=False):
     return D + lam * R, D, R, xhat, yhat
 
 
+@torch.no_grad()
+def decision_margins(x, y_levels, P, arch: Arch, u_levels=None, hard=False):
+    """Distance of every discrete decision of the forward pass to its tie.
+
+    Where a decision sits within rounding error of its tie (a ReLU pre-activation near 0,
+    a bin probability near the 2^-16 floor, a log-scale near a clamp bound), an FP32
+    evaluation may legitimately take the other side, and the two one-sided derivatives
+    differ.  Returns (arm, syn): per latent of each level, the smallest of |z| over the
+    ARM's LinR pre-activations, |log2 P + 16| and the distance of s to its clamp bounds;
+    per pixel, the smallest |pre-activation| of the synthesis ReLUs.
+    """
+    H, W = x.shape[1], x.shape[2]
+    shapes = level_shapes(H, W, arch.levels)
+    yhat = [torch.round(y) if hard else y + u for y, u in
+            zip(y_levels, u_levels if u_levels is not None else [None] * arch.levels)]
+    offs = causal_offsets(arch.arm_ctx)
+    arm = []
+    for yl in yhat:
+        h = arm_context(yl, offs)
+        m = torch.full(yl.shape, float("inf"), dtype=DT)
+        for i in range(arch.arm_layers):
+            z = h @ P[f"arm.w{i}"].T + P[f"arm.b{i}"]
+            m = torch.minimum(m, torch.min(torch.abs(z), -1).values)
+            h = h + torch.relu(z)
+        out = h @ P["arm.wout"].T + P["arm.bout"]
+        mu, sc = out[..., 0], out[..., 1]
+        pm = laplace_bin_mass(yl, mu, sc)
+        m = torch.minimum(m, torch.abs(torch.log2(torch.clamp(pm, min=1e-300)) + 16.0))
+        m = torch.minimum(m, torch.minimum(torch.abs(sc - LOG_B_MIN), torch.abs(sc - LOG_B_MAX)))
+        arm.append(m.numpy())
+    feat = upsample_all(yhat, P, arch, shapes)
+    z = torch.einsum("ck,khw->chw", P["syn.wa"], feat) + P["syn.ba"][:, None, None]
+    syn = torch.min(torch.abs(z), 0).values
+    h = torch.relu(z)
+    z = torch.einsum("ck,khw->chw", P["syn.wb"], h) + P["syn.bb"][:, None, None]
+    syn = torch.minimum(syn, torch.min(torch.abs(z), 0).values)
+    h = torch.relu(z)
+    for i in range(arch.syn_res3x3 - 1):
+        z = conv3x3_replicate(h, P[f"syn.w3_{i}"], P[f"syn.b3_{i}"])
+        syn = torch.minimum(syn, torch.min(torch.abs(z), 0).values)
+        h = h + torch.relu(z)
+    return arm, syn.numpy()
+
+
 def image_to_planar(rgb_hwc_u8: np.ndarray) -> torch.Tensor:
     """uint8 H x W x 3 -> float64 [3, H, W] with x = v / 255."""
     return torch.tensor(np.transpose(rgb_hwc_u8, (2, 0, 1)).astype(np.float64) / 255.0, dtype=DT)

@@ -20,10 +20,13 @@ namespace cc {
 constexpr int kMaxN = 24;
 constexpr int kMaxArmParams = 2 * (kMaxN * kMaxN + kMaxN) + 2 * kMaxN + 2;
 __constant__ float c_arm[kMaxArmParams];
+// A second copy of the weights, read by the backward pass only: with a single bank the
+// compiler keeps every weight used by both passes in a register between its two uses.
+__constant__ float c_armb[kMaxArmParams];
 __constant__ int2 c_off[kMaxN];  // (dy, dx) of each context slot, raster order
 
 struct ArmArgs {
-  const float* yhat;
+  const float* yhat;   // zero-bordered copy (Geo::poff, Geo::pw)
   float* dctx;       // [N][n_pad]: d bits(p) / d context slot k of p
   float* gself;      // [n_pad]:    d bits(p) / d yhat(p)
   float* part_grad;  // [gridDim.x][n_arm]: per-CTA d bits / d psi
@@ -169,19 +172,23 @@ __global__ void __launch_bounds__(kArmTile, 3) k_arm(ArmArgs a) {
     const int n_l = a.g.h[l] * w;
     const int i = td.y + tid;
     const bool valid = i < n_l;
-    const float* plane = a.yhat + a.g.off[l];
+    // zero-bordered plane: every causal neighbour is inside the allocation, outside the
+    // grid it reads the zero border
+    const int pw = a.g.pw[l];
     int r = 0, c = 0;
     if (valid) { r = i / w; c = i - r * w; }
-
-    // context gather, zero outside the grid
+    const float* ctr = a.yhat + a.g.poff[l] + (long long)(r + kCtxPad) * pw + c + kCtxPad;
     float h[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       const int2 o = c_off[k];
-      const int rr = r + o.x, cc = c + o.y;
-      h[k] = (valid && rr >= 0 && cc >= 0 && cc < w) ? __ldg(plane + rr * w + cc) : 0.f;
+      h[k] = __ldg(ctr + o.x * pw + o.y);
     }
-    const float yq = valid ? __ldg(plane + i) : 0.f;
+    const float yq = __ldg(ctr);
+    if (!valid) {
+#pragma unroll
+      for (int k = 0; k < N; ++k) h[k] = 0.f;
+    }
 
     // forward: h <- h + relu(W h + b), NL times
     uint32_t mask[NL];
@@ -218,7 +225,7 @@ __global__ void __launch_bounds__(kArmTile, 3) k_arm(ArmArgs a) {
       reinterpret_cast<float2*>(s_do)[tid] = make_float2(lo.g_mu, lo.g_s);
       float dh[N];
 #pragma unroll
-      for (int k = 0; k < N; ++k) dh[k] = lo.g_mu * c_arm[OW + k] + lo.g_s * c_arm[OW + N + k];
+      for (int k = 0; k < N; ++k) dh[k] = lo.g_mu * c_armb[OW + k] + lo.g_s * c_armb[OW + N + k];
 #pragma unroll
       for (int L = NL - 1; L >= 0; --L) {
         float dz[N];
@@ -228,7 +235,7 @@ __global__ void __launch_bounds__(kArmTile, 3) k_arm(ArmArgs a) {
 #pragma unroll
         for (int k = 0; k < N; ++k)
 #pragma unroll
-          for (int o = 0; o < N; ++o) dh[k] = fmaf(c_arm[L * LW + o * N + k], dz[o], dh[k]);
+          for (int o = 0; o < N; ++o) dh[k] = fmaf(c_armb[L * LW + o * N + k], dz[o], dh[k]);
       }
       if (valid) {
         const long long q = a.g.off[l] + i;
@@ -397,6 +404,9 @@ cudaError_t arm_upload(const float* d_params, int n_arm, const int2* d_offsets, 
                        cudaStream_t st) {
   cudaError_t e = cudaMemcpyToSymbolAsync(c_arm, d_params, (size_t)n_arm * sizeof(float), 0,
                                           cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbolAsync(c_armb, d_params, (size_t)n_arm * sizeof(float), 0,
+                              cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
   return cudaMemcpyToSymbolAsync(c_off, d_offsets, (size_t)N * sizeof(int2), 0,
                                  cudaMemcpyDeviceToDevice, st);

@@ -112,6 +112,13 @@ Geo geo_of(int H, int W) {
     g.n_lat += g.h[l] * g.w[l];
   }
   g.n_pad = off;
+  off = 0;
+  for (int l = 0; l < kLevels; ++l) {
+    g.pw[l] = g.w[l] + 2 * kCtxPad;
+    g.poff[l] = off;
+    off = align32(off + (long long)(g.h[l] + kCtxPad) * g.pw[l]);
+  }
+  g.n_bord = off;
   return g;
 }
 
@@ -137,7 +144,7 @@ struct cc_ctx {
   bool own_mem = false;
   void* mem = nullptr;
   size_t bytes = 0;
-  float *x, *y, *my, *vy, *yhat, *gsyn, *gself, *dctx, *noise;
+  float *x, *y, *my, *vy, *yhat, *yhat_bord, *gsyn, *gself, *dctx, *noise;
   float *params, *mp, *vp;
   float *hbuf, *dhbuf, *dz;
   float *part_arm, *part_bits, *part_d, *part_conv, *part_syn, *part_up, *part2;
@@ -174,6 +181,7 @@ size_t plan(cc_ctx* c, char* base) {
   c->my = (float*)take(L);
   c->vy = (float*)take(L);
   c->yhat = (float*)take(L);
+  c->yhat_bord = (float*)take((size_t)g.n_bord * sizeof(float));
   c->gsyn = (float*)take(L);
   c->gself = (float*)take(L);
   c->noise = (float*)take(L);
@@ -264,10 +272,10 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
   CKE(mark(0));
   CKE(arm_upload(c->params, c->lay.n_arm, c->offs, a.N, s));
   CKE(syn_upload(c->params, c->lay, a, s));
-  CKE(quantize_launch(c->geo, c->y, c->yhat, c->noise, qmode, c->sc, c->ste_start, c->cfg.seed,
+  CKE(quantize_launch(c->geo, c->y, c->yhat, c->yhat_bord, c->noise, qmode, c->sc, c->ste_start, c->cfg.seed,
                       -1, s));
   CKE(mark(1));
-  CKE(arm_launch(a, backward, c->yhat, c->geo, c->tiles, c->n_tiles, c->grid_arm, c->dctx,
+  CKE(arm_launch(a, backward, c->yhat_bord, c->geo, c->tiles, c->n_tiles, c->grid_arm, c->dctx,
                  c->gself, c->part_arm, c->part_bits, s));
   CKE(mark(2));
   CKE(up_forward(a, c->geo, c->yhat, c->up, s));
@@ -541,7 +549,7 @@ int cc_decode(cc_ctx* c, float* rgb_out_hwc) {
   const Arch& a = c->arch;
   const size_t HW = (size_t)c->HW;
   CK(syn_upload(c->params, c->lay, a, c->st));
-  CK(quantize_launch(c->geo, c->y, c->yhat, c->noise, 1, c->sc, c->ste_start, c->cfg.seed, -1,
+  CK(quantize_launch(c->geo, c->y, c->yhat, c->yhat_bord, c->noise, 1, c->sc, c->ste_start, c->cfg.seed, -1,
                      c->st));
   CK(up_forward(a, c->geo, c->yhat, c->up, c->st));
   CK(syn_forward(a, c->geo, c->yhat, c->up, c->x, c->hbuf, c->dhbuf + (size_t)a.NR * 3 * HW,
@@ -677,7 +685,7 @@ int cc_iteration(cc_ctx* c, int* iter) {
 int cc_noise(cc_ctx* c, int iter, float* out) {
   if (!c || !out || iter < 0) return CC_EINVAL;
   CK(cudaSetDevice(c->dev));
-  CK(quantize_launch(c->geo, c->y, c->yhat, c->noise, 4, c->sc, c->ste_start, c->cfg.seed, iter,
+  CK(quantize_launch(c->geo, c->y, c->yhat, c->yhat_bord, c->noise, 4, c->sc, c->ste_start, c->cfg.seed, iter,
                      c->st));
   int e = copy_latents(c, c->yhat, out, true);
   if (e) return e;

@@ -21,7 +21,13 @@ struct Geo {
   long long off[kLevels];
   long long n_pad;   // floats in a latent-shaped buffer
   int n_lat;         // sum_l h_l w_l
+  // zero-bordered copy of y_hat for the context gather: kCtxPad rows above and kCtxPad
+  // columns on each side of every plane, row stride pw[l] = w[l] + 2 kCtxPad
+  long long poff[kLevels];
+  int pw[kLevels];
+  long long n_bord;
 };
+constexpr int kCtxPad = 4;        // reach of the largest causal context (N = 24)
 
 // Architecture (Table 1 notation) as the kernels see it.
 struct Arch {
@@ -56,7 +62,9 @@ struct SectionTable {
 
 // Scalars of the current iteration, written on the device.
 struct IterScalars {
-  int t;            // index of the current iteration (0-based)
+  int t;              // index of the current iteration (0-based)
+  float inv_bc1;      // Adam 1 / (1 - beta1^(t+1)) of the current update
+  float inv_sqrt_bc2; // Adam 1 / sqrt(1 - beta2^(t+1))
   int pad;
   double D, R, loss;
 };
@@ -96,9 +104,9 @@ int syn1x1_partial_cols(const Arch& a);
 cudaError_t syn_prepare(const Arch& a);   // kernel attributes; call once before capture
 
 // iteration bookkeeping (cc_iter.cu)
-cudaError_t quantize_launch(const Geo& g, const float* y, float* yhat, const float* noise,
-                            int mode, const IterScalars* sc, int ste_start, uint64_t seed,
-                            int iter_override, cudaStream_t st);
+cudaError_t quantize_launch(const Geo& g, const float* y, float* yhat, float* yhat_bord,
+                            const float* noise, int mode, const IterScalars* sc, int ste_start,
+                            uint64_t seed, int iter_override, cudaStream_t st);
 cudaError_t reduce_sections(const SectionTable& tab, float* part2, int n_virtual, int slices,
                             cudaStream_t st);
 cudaError_t param_update(const Layout& lay, const Arch& a, const float* part2, int slices,

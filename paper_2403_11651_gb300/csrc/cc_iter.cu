@@ -27,6 +27,7 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint2 k) {
 // Philox4x32-10(counter (i div 4, l, t, 0), key (seed lo, seed hi)), u = (w >> 8) 2^-24 - 1/2.
 __global__ void __launch_bounds__(256) k_quantize(Geo g, const float* __restrict__ y,
                                                   float* __restrict__ yhat,
+                                                  float* __restrict__ yhat_bord,
                                                   const float* __restrict__ noise, int mode,
                                                   const IterScalars* sc, int ste_start,
                                                   uint2 key, int iter_override) {
@@ -56,18 +57,23 @@ __global__ void __launch_bounds__(256) k_quantize(Geo g, const float* __restrict
       out = m == 4 ? u : yv + u;
     }
     yhat[base + i] = out;
+    if (yhat_bord) {
+      const int r = i / g.w[l], c = i - r * g.w[l];
+      yhat_bord[g.poff[l] + (long long)(r + kCtxPad) * g.pw[l] + c + kCtxPad] = out;
+    }
   }
 }
 
-cudaError_t quantize_launch(const Geo& g, const float* y, float* yhat, const float* noise,
-                            int mode, const IterScalars* sc, int ste_start, uint64_t seed,
-                            int iter_override, cudaStream_t st) {
+cudaError_t quantize_launch(const Geo& g, const float* y, float* yhat, float* yhat_bord,
+                            const float* noise, int mode, const IterScalars* sc, int ste_start,
+                            uint64_t seed, int iter_override, cudaStream_t st) {
   int maxn = 0;
   for (int l = 0; l < kLevels; ++l) maxn = g.h[l] * g.w[l] > maxn ? g.h[l] * g.w[l] : maxn;
   const int groups = (maxn + 3) / 4;
   dim3 grid((groups + 255) / 256, kLevels);
   const uint2 key = make_uint2((uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32));
-  k_quantize<<<grid, 256, 0, st>>>(g, y, yhat, noise, mode, sc, ste_start, key, iter_override);
+  k_quantize<<<grid, 256, 0, st>>>(g, y, yhat, yhat_bord, noise, mode, sc, ste_start, key,
+                                   iter_override);
   return cudaGetLastError();
 }
 
@@ -130,14 +136,23 @@ struct VirtualMap {
   int vsyn, vconv, vup, n_virtual;
 };
 
+// Also publishes the Adam bias corrections of this iteration in IterScalars (block 0),
+// for the latent update that runs next on the stream.
 __global__ void __launch_bounds__(128) k_param_update(VirtualMap vm, const float* part2,
                                                       int slices, float* params, float* m,
                                                       float* v, float* grad_out, int apply,
-                                                      float lr, const IterScalars* sc,
-                                                      int total, AdamStep* step_out) {
+                                                      float lr, IterScalars* sc, int total) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const AdamStep st = adam_step(sc->t, lr);
-  if (j == 0 && step_out) *step_out = st;
+  __shared__ AdamStep s_st;
+  if (threadIdx.x == 0) {
+    s_st = adam_step(sc->t, lr);
+    if (blockIdx.x == 0) {
+      sc->inv_bc1 = s_st.inv_bc1;
+      sc->inv_sqrt_bc2 = s_st.inv_sqrt_bc2;
+    }
+  }
+  __syncthreads();
+  const AdamStep st = s_st;
   if (j >= total) return;
   int vs[kLevels - 1];
   int nv = 1;
@@ -176,8 +191,8 @@ cudaError_t param_update(const Layout& lay, const Arch& a, const float* part2, i
   vm.vsyn = lay.n_arm; vm.vconv = vm.vsyn + vm.n1x1; vm.vup = vm.vconv + vm.nconv;
   vm.n_virtual = vm.vup + (kLevels - 1) * vm.K2;
   k_param_update<<<(lay.total + 127) / 128, 128, 0, st>>>(vm, part2, slices, params, m, v,
-                                                          grad_out, apply ? 1 : 0, lr, sc,
-                                                          lay.total, nullptr);
+                                                          grad_out, apply ? 1 : 0, lr,
+                                                          const_cast<IterScalars*>(sc), lay.total);
   return cudaGetLastError();
 }
 
@@ -211,7 +226,10 @@ __global__ void __launch_bounds__(256) k_latent_update(Geo g, const int2* __rest
     grad_out[fo + i] = gt;
   }
   if (apply) {
-    const AdamStep st = adam_step(sc->t, lr);
+    AdamStep st;
+    st.lr = lr;
+    st.inv_bc1 = sc->inv_bc1;
+    st.inv_sqrt_bc2 = sc->inv_sqrt_bc2;
     float yv = y[q], mv = m[q], vv = v[q];
     adam_apply(yv, mv, vv, gt, st);
     y[q] = yv; m[q] = mv; v[q] = vv;

@@ -20,6 +20,10 @@ constexpr int kMaxC = 40;
 constexpr int k3x3 = 84;                  // floats per 3x3 layer (W 3x3x3x3, b 3)
 constexpr int kSyn1x1Base = 2 * k3x3;     // 1x1 layers follow two reserved 3x3 slots
 __constant__ float c_syn[kSyn1x1Base + 11 * kMaxC + 3];
+// A second copy of the bank, read by backward passes only.  With one bank the compiler
+// keeps every weight used by both a forward and a backward loop in a register between the
+// two uses (hundreds of live values); with two, each use is a plain constant operand.
+__constant__ float c_synb[kSyn1x1Base + 11 * kMaxC + 3];
 __constant__ float c_up[(kLevels - 1) * 64];
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
@@ -48,31 +52,56 @@ struct UpFwdArgs {
   int sh, sw, dh, dw;
 };
 
+// One thread per 2x2 output quad (2t + py, 2s + px): along each axis output 2t + p reads
+// the inputs t + d, d in [p - K/4, p + K/4 - 1], with tap u = p - 2d + K/2 - 1, so the
+// quad needs a (K/2 + 1)^2 input patch and every tap index is a compile-time constant.
 template <int K>
 __global__ void __launch_bounds__(256) k_up_fwd(UpFwdArgs a) {
   constexpr int c = K / 2 - 1;
+  constexpr int R = K / 4;          // patch rows t - R .. t + R
+  constexpr int P = 2 * R + 1;
   const int li = blockIdx.y;
   const float* __restrict__ src = a.src[li];
   float* __restrict__ dst = a.dst[li];
-  const float* f = c_up + a.fidx[li] * K * K;
-  const int n = a.dh * a.dw;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const int oy = p / a.dw, ox = p - oy * a.dw;
-    const int uy0 = (oy + c) & 1, ux0 = (ox + c) & 1;
-    int ix[K / 2];
+  float f[K * K];
+  const int fb = a.fidx[li] * K * K;
 #pragma unroll
-    for (int t = 0; t < K / 2; ++t) ix[t] = clampi((ox + c - ux0 - 2 * t) >> 1, 0, a.sw - 1);
-    float acc = 0.f;
+  for (int u = 0; u < K * K; ++u) f[u] = c_up[fb + u];
+  const int qh = (a.dh + 1) >> 1, qw = (a.dw + 1) >> 1;
+  const int n = qh * qw;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const int t = q / qw, sx = q - t * qw;
+    int col[P];
 #pragma unroll
-    for (int ty = 0; ty < K / 2; ++ty) {
-      const int uy = uy0 + 2 * ty;
-      const int iy = clampi((oy + c - uy) >> 1, 0, a.sh - 1);
-      const float* row = src + iy * a.sw;
+    for (int d = 0; d < P; ++d) col[d] = clampi(sx - R + d, 0, a.sw - 1);
+    float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll
-      for (int tx = 0; tx < K / 2; ++tx)
-        acc = fmaf(f[uy * K + ux0 + 2 * tx], __ldg(row + ix[tx]), acc);
+    for (int dy = 0; dy < P; ++dy) {
+      const float* row = src + clampi(t - R + dy, 0, a.sh - 1) * a.sw;
+      float v[P];
+#pragma unroll
+      for (int d = 0; d < P; ++d) v[d] = __ldg(row + col[d]);
+#pragma unroll
+      for (int py = 0; py < 2; ++py) {
+        const int uy = py - 2 * (dy - R) + c;
+        if (uy < 0 || uy >= K) continue;   // compile-time
+#pragma unroll
+        for (int px = 0; px < 2; ++px)
+#pragma unroll
+          for (int dx = 0; dx < P; ++dx) {
+            const int ux = px - 2 * (dx - R) + c;
+            if (ux < 0 || ux >= K) continue;   // compile-time
+            acc[py][px] = fmaf(f[uy * K + ux], v[dx], acc[py][px]);
+          }
+      }
     }
-    dst[p] = acc;
+#pragma unroll
+    for (int py = 0; py < 2; ++py)
+#pragma unroll
+      for (int px = 0; px < 2; ++px) {
+        const int oy = 2 * t + py, ox = 2 * sx + px;
+        if (oy < a.dh && ox < a.dw) dst[oy * a.dw + ox] = acc[py][px];
+      }
   }
 }
 
@@ -89,6 +118,7 @@ struct UpBwdArgs {
 // Adjoint of one step.  Thread per input position i: it gathers every output that read
 // i, directly or through the clamp (virtual positions beyond the border fold onto the
 // edge), giving dL/d in[i] = sum f[u] dout[o] and the filter gradient in[i] * dout[o].
+// Inputs whose 8 x 8 output window lies inside the plane take a branch-free path.
 template <int K>
 __global__ void __launch_bounds__(256) k_up_bwd(UpBwdArgs a) {
   constexpr int c = K / 2 - 1;
@@ -97,30 +127,53 @@ __global__ void __launch_bounds__(256) k_up_bwd(UpBwdArgs a) {
   const float* __restrict__ dout = a.dout[li];
   const float* __restrict__ in = a.in[li];
   float* __restrict__ din = a.din[li];
-  const float* f = c_up + a.fidx[li] * KK;
+  float f[KK];
+  const int fb = a.fidx[li] * KK;
+#pragma unroll
+  for (int u = 0; u < KK; ++u) f[u] = c_up[fb + u];
   float facc[KK];
 #pragma unroll
   for (int u = 0; u < KK; ++u) facc[u] = 0.f;
   const int n = a.sh * a.sw;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const int iy = p / a.sw, ix = p - iy * a.sw;
+    const float xin = __ldg(in + p);
+    const int oy0 = 2 * iy - c, ox0 = 2 * ix - c;
+    const bool inner = iy > 0 && ix > 0 && iy < a.sh - 1 && ix < a.sw - 1 && oy0 >= 0 &&
+                       ox0 >= 0 && oy0 + K <= a.dh && ox0 + K <= a.dw;
+    if (inner) {
+      const float* base = dout + oy0 * a.dw + ox0;
+      float g[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int uy = 0; uy < K; ++uy) {
+        const float* row = base + uy * a.dw;
+#pragma unroll
+        for (int ux = 0; ux < K; ++ux) {
+          const float gv = __ldg(row + ux);
+          g[ux & 3] = fmaf(f[uy * K + ux], gv, g[ux & 3]);
+          facc[uy * K + ux] = fmaf(xin, gv, facc[uy * K + ux]);
+        }
+      }
+      din[p] = (g[0] + g[1]) + (g[2] + g[3]);
+      continue;
+    }
     const int vy0 = iy == 0 ? -(K / 4) : iy;
     const int vy1 = iy == a.sh - 1 ? (a.dh - 1 + c) >> 1 : iy;
     const int vx0 = ix == 0 ? -(K / 4) : ix;
     const int vx1 = ix == a.sw - 1 ? (a.dw - 1 + c) >> 1 : ix;
-    const float xin = __ldg(in + p);
     float g = 0.f;
     for (int vy = vy0; vy <= vy1; ++vy) {
       for (int vx = vx0; vx <= vx1; ++vx) {
 #pragma unroll
         for (int uy = 0; uy < K; ++uy) {
           const int oy = 2 * vy - c + uy;
-          if (oy < 0 || oy >= a.dh) continue;
+          const bool oky = oy >= 0 && oy < a.dh;
+          const int oyc = clampi(oy, 0, a.dh - 1);
 #pragma unroll
           for (int ux = 0; ux < K; ++ux) {
             const int ox = 2 * vx - c + ux;
-            if (ox < 0 || ox >= a.dw) continue;
-            const float gv = __ldg(dout + oy * a.dw + ox);
+            const bool ok = oky && ox >= 0 && ox < a.dw;
+            const float gv = ok ? __ldg(dout + oyc * a.dw + clampi(ox, 0, a.dw - 1)) : 0.f;
             g = fmaf(f[uy * K + ux], gv, g);
             facc[uy * K + ux] = fmaf(xin, gv, facc[uy * K + ux]);
           }
@@ -159,7 +212,7 @@ static cudaError_t up_forward_k(const Arch& ar, const Geo& g, const float* yhat,
       a.fidx[n] = ar.per_level ? l - 1 : 0;
     }
     a.sh = g.h[j + 1]; a.sw = g.w[j + 1]; a.dh = g.h[j]; a.dw = g.w[j];
-    const int tot = a.dh * a.dw;
+    const int tot = ((a.dh + 1) / 2) * ((a.dw + 1) / 2);
     dim3 grid((tot + 255) / 256 < 1024 ? (tot + 255) / 256 : 1024, n);
     k_up_fwd<K><<<grid, 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
@@ -190,8 +243,11 @@ static cudaError_t up_backward_k(const Arch& ar, const Geo& g, const float* yhat
       a.lev[n] = l;
     }
     a.sh = g.h[j + 1]; a.sw = g.w[j + 1]; a.dh = g.h[j]; a.dw = g.w[j];
+    // rows [j * grid, j * grid + grid) belong to this step; only as many CTAs as there is
+    // work for are launched, the rows of the others stay zero from the context set-up
     a.part = part_up + (long long)j * grid * kLevels * K * K;
-    k_up_bwd<K><<<dim3(grid, n), 256, 0, st>>>(a);
+    const int need = (a.sh * a.sw + 255) / 256;
+    k_up_bwd<K><<<dim3(need < grid ? need : grid, n), 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -287,21 +343,22 @@ __global__ void __launch_bounds__(256, 2) k_syn1x1_bwd(Syn1x1Args a) {
     for (int j = 0; j < 3; ++j) dh2[j] = valid ? __ldg(a.dh2 + j * a.HW + p) : 0.f;
     // recompute z1, h1, z2
     float z2[3] = {c_syn[BB], c_syn[BB + 1], c_syn[BB + 2]};
-    uint64_t m1 = 0;
-    float* hrow = s_h1 + tid * SZ;
-#pragma unroll 4
+    float h1[C];
+#pragma unroll
     for (int o = 0; o < C; ++o) {
       float z = c_syn[BA + o];
 #pragma unroll
       for (int k = 0; k < kLevels; ++k) z = fmaf(c_syn[WA + o * kLevels + k], f[k], z);
-      m1 |= (uint64_t)(z > 0.f) << o;
-      const float h1 = fmaxf(z, 0.f);
-      hrow[o] = valid ? h1 : 0.f;
+      h1[o] = fmaxf(z, 0.f);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) z2[j] = fmaf(c_syn[WB + j * C + o], h1, z2[j]);
+      for (int j = 0; j < 3; ++j) z2[j] = fmaf(c_syn[WB + j * C + o], h1[o], z2[j]);
     }
-    hrow[C] = valid ? 1.f : 0.f;
-    hrow[C + 1] = 0.f; hrow[C + 2] = 0.f; hrow[C + 3] = 0.f;
+    float* hrow = s_h1 + tid * SZ;
+#pragma unroll
+    for (int o = 0; o < C; o += 4)
+      *reinterpret_cast<float4*>(hrow + o) = valid ? make_float4(h1[o], h1[o + 1], h1[o + 2], h1[o + 3])
+                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4*>(hrow + C) = make_float4(valid ? 1.f : 0.f, 0.f, 0.f, 0.f);
     float dz2[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) dz2[j] = z2[j] > 0.f ? dh2[j] : 0.f;
@@ -309,17 +366,19 @@ __global__ void __launch_bounds__(256, 2) k_syn1x1_bwd(Syn1x1Args a) {
     float df[kLevels];
 #pragma unroll
     for (int k = 0; k < kLevels; ++k) df[k] = 0.f;
-    float* zrow = s_dz1 + tid * SZ;
-#pragma unroll 4
+#pragma unroll
     for (int o = 0; o < C; ++o) {
       float dh1 = 0.f;
 #pragma unroll
-      for (int j = 0; j < 3; ++j) dh1 = fmaf(c_syn[WB + j * C + o], dz2[j], dh1);
-      const float dz1 = ((m1 >> o) & 1ull) ? dh1 : 0.f;
-      zrow[o] = dz1;
+      for (int j = 0; j < 3; ++j) dh1 = fmaf(c_synb[WB + j * C + o], dz2[j], dh1);
+      h1[o] = h1[o] > 0.f ? dh1 : 0.f;    // now dz1 (relu'(z1) = [h1 > 0])
 #pragma unroll
-      for (int k = 0; k < kLevels; ++k) df[k] = fmaf(c_syn[WA + o * kLevels + k], dz1, df[k]);
+      for (int k = 0; k < kLevels; ++k) df[k] = fmaf(c_synb[WA + o * kLevels + k], h1[o], df[k]);
     }
+    float* zrow = s_dz1 + tid * SZ;
+#pragma unroll
+    for (int o = 0; o < C; o += 4)
+      *reinterpret_cast<float4*>(zrow + o) = make_float4(h1[o], h1[o + 1], h1[o + 2], h1[o + 3]);
     float* frow = s_f + tid * SF;
 #pragma unroll
     for (int k = 0; k < kLevels; ++k) frow[k] = f[k];
@@ -513,6 +572,23 @@ __global__ void __launch_bounds__(256) k_conv_dx(ConvArgs a) {
     float acc[3];
 #pragma unroll
     for (int ci = 0; ci < 3; ++ci) acc[ci] = __ldg(a.dhout + ci * HW + q);
+    if (qy > 0 && qx > 0 && qy < a.H - 1 && qx < a.W - 1) {
+      // interior: output p = q - (dy, dx) read q through tap (dy, dx), no clamping
+#pragma unroll
+      for (int o = 0; o < 3; ++o)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+          for (int dx = -1; dx <= 1; ++dx) {
+            const float d = __ldg(a.dz + o * HW + q - dy * a.W - dx);
+#pragma unroll
+            for (int ci = 0; ci < 3; ++ci)
+              acc[ci] = fmaf(c_syn[Wo + o * 27 + ci * 9 + (dy + 1) * 3 + (dx + 1)], d, acc[ci]);
+          }
+#pragma unroll
+      for (int ci = 0; ci < 3; ++ci) a.dhin[ci * HW + q] = acc[ci];
+      continue;
+    }
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy) {
       for (int py = qy - dy - 1; py <= qy - dy + 1; ++py) {
@@ -665,14 +741,16 @@ cudaError_t syn_upload(const float* d_params, const Layout& lay, const Arch& a,
                        cudaStream_t st) {
   // bank c_syn: [3x3 layer 0 | 3x3 layer 1 | W_a b_a W_b b_b]; c_up: the filters
   const size_t n1x1 = (size_t)(11 * a.C + 3);
-  cudaError_t e = cudaMemcpyToSymbolAsync(c_syn, d_params + lay.syn0, n1x1 * sizeof(float),
-                                          kSyn1x1Base * sizeof(float),
-                                          cudaMemcpyDeviceToDevice, st);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyToSymbolAsync(c_syn, d_params + lay.syn0 + n1x1,
-                              (size_t)a.NR * k3x3 * sizeof(float), 0,
-                              cudaMemcpyDeviceToDevice, st);
-  if (e != cudaSuccess) return e;
+  for (const void* bank : {(const void*)&c_syn, (const void*)&c_synb}) {
+    cudaError_t e = cudaMemcpyToSymbolAsync(bank, d_params + lay.syn0, n1x1 * sizeof(float),
+                                            kSyn1x1Base * sizeof(float),
+                                            cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyToSymbolAsync(bank, d_params + lay.syn0 + n1x1,
+                                (size_t)a.NR * k3x3 * sizeof(float), 0,
+                                cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
   return cudaMemcpyToSymbolAsync(c_up, d_params + lay.up0,
                                  (size_t)lay.n_up * a.K * a.K * sizeof(float), 0,
                                  cudaMemcpyDeviceToDevice, st);

