@@ -38,6 +38,20 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+def max_over_ranks(x: float, td=None, device="cpu") -> float:
+    """Largest value of x over all ranks (x itself without a process group)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if td is not None:
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(max_ms: float, world: int, H: int, W: int, steps: int) -> float:
+    """Whole-job Mpixel-iter/s of `world` independent replicas, timed by the slowest one."""
+    return world * H * W * steps / (max_ms / 1e3) / 1e6
+
+
 def workload(cfgd):
     return {"workload": f"{cfgd['H']}x{cfgd['W']} synthetic image, 2300-MAC decoder "
                         f"(ARM 24-24-24-2, per-level 8x8 upsampling, synthesis 7-40-3 + 2 x 3x3 "
@@ -246,11 +260,8 @@ def run_ours(a, cfgd):
         # dominant kernel (ARM + rate, forward and backward), timed live with CUDA events
         phases = cc.cc_profile_phases(ctx, max(3, min(20, a.steps)))
     clocks = clk.summary()
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if td:
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * H * W * a.steps / (total_ms / 1e3) / 1e6
+    total_ms = max_over_ranks(total_ms, td, dev)
+    value = replica_throughput(total_ms, world, H, W, a.steps)
 
     # end to end through the C ABI with host buffers
     pinned = torch.from_numpy(rgb).pin_memory()
@@ -264,11 +275,8 @@ def run_ours(a, cfgd):
         it = cc.cc_iteration(ctx)
         last = cc.cc_get_losses(ctx, it - 1, 1)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if td:
-        td.all_reduce(te, op=td.ReduceOp.MAX)
-    e2e_value = world * H * W * n_e2e / float(te.item()) / 1e6
+    e2e_s = max_over_ranks(time.perf_counter() - t0, td, dev)
+    e2e_value = replica_throughput(e2e_s * 1e3, world, H, W, n_e2e)
 
     # the full schedule once, for time to the final RD cost of the plain method
     ctx2 = cc.cc_init_image(cfg, rgb, H, W, init, stream)

@@ -178,7 +178,7 @@ void cc_free(cc_ctx* ctx);
 /* Static description of an error code. */
 const char* cc_strerror(int code);
 
-/* Text of the last CUDA error seen by the library in this thread ("" if none). */
+/* Text of the last error seen by the library in this thread ("" if none). */
 const char* cc_last_cuda_error(void);
 
 #ifdef __cplusplus

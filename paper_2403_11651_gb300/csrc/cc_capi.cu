@@ -131,6 +131,8 @@ int sm_count() {
 
 }  // namespace
 
+void cc::set_error_text(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 struct cc_ctx {
   cc_config cfg;
   Arch arch;

@@ -121,4 +121,7 @@ cudaError_t finish_iteration(const float* part_d, int nd, const float* part_bits
                              double* log, bool advance, cudaStream_t st);
 cudaError_t image_to_planar(const uint8_t* rgb_hwc, float* x, int H, int W, cudaStream_t st);
 
+// Stores a message for cc_last_cuda_error() (thread-local).
+void set_error_text(const char* msg);
+
 }  // namespace cc
