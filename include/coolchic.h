@@ -178,6 +178,29 @@ void cc_free(cc_ctx* ctx);
 /* Static description of an error code. */
 const char* cc_strerror(int code);
 
+/* Rate without allocation.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc -- e.g. a decoder inside a process whose device
+ * memory is all owned by another allocator (a framework's caching allocator, a fixed
+ * pool), or a real-time service that must not allocate once running.
+ *
+ * Computes bits = sum over every latent of -log2 P(y_hat) under the ARM (the rate term of
+ * eq. (1) before division by H W) for a caller-supplied quantised pyramid:
+ *   yhat_flat: device, cc_latent_count floats in flat latent order (any real values);
+ *   params:    device, cc_param_count floats in flat parameter order (ARM part read);
+ *   bits_out:  host or device, one double;  cuda_stream: cudaStream_t or NULL.
+ * Allocates nothing: its scratch -- one float per tile of 128 latents plus the double
+ * total -- is a fixed file-scope __device__ array held by every device that loads the
+ * library until the process exits.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  All calls share the array, so calls whose GPU work overlaps race:
+ * issue them on one stream or synchronise between them.  Every call rewrites all the
+ * scratch it reads.  Pyramids needing more than CC_NOALLOC_MAX_TILES tiles (about 8.4
+ * million latents, e.g. 2048 x 3072 pixels) are rejected with CC_EINVAL and a message in
+ * cc_last_cuda_error().  Synchronises before returning. */
+#define CC_NOALLOC_MAX_TILES 65536
+int cc_rate_bits_noalloc(const cc_config* cfg, const float* yhat_flat, int H, int W,
+                         const float* params, void* cuda_stream, double* bits_out);
+
 /* Text of the last error seen by the library in this thread ("" if none). */
 const char* cc_last_cuda_error(void);
 

@@ -66,6 +66,7 @@ def _declare(lib):
         "cc_graph_kernel_count": (c_int, [P, POINTER(c_int)]),
         "cc_get_state": (c_int, [P, P, POINTER(c_size_t)]),
         "cc_set_state": (c_int, [P, P, c_size_t]),
+        "cc_rate_bits_noalloc": (c_int, [P, P, c_int, c_int, P, P, POINTER(c_double)]),
         "cc_free": (None, [P]),
         "cc_strerror": (ctypes.c_char_p, [c_int]),
         "cc_last_cuda_error": (ctypes.c_char_p, []),
@@ -344,6 +345,15 @@ def cc_set_state(ctx, blob: bytes):
     _check(_lib().cc_set_state(ctx, buf, len(blob)), "cc_set_state")
 
 
+def cc_rate_bits_noalloc(cfg: cc_config, yhat_flat, H: int, W: int, params, stream=None) -> float:
+    """Total rate (bits) of a quantised pyramid, computed without allocating device memory."""
+    out = c_double()
+    _check(_lib().cc_rate_bits_noalloc(ctypes.byref(cfg), _ptr(yhat_flat), H, W, _ptr(params),
+                                       _stream_handle(stream), ctypes.byref(out)),
+           "cc_rate_bits_noalloc")
+    return out.value
+
+
 def cc_free(ctx):
     if ctx:
         _lib().cc_free(ctx)
@@ -357,5 +367,5 @@ EXPORTED = ["cc_param_count", "cc_latent_count", "cc_workspace_size", "cc_init_i
             "cc_init_image_ws", "cc_set_image", "cc_encode_iters", "cc_rd_cost", "cc_decode",
             "cc_get_grads", "cc_forward_backward", "cc_get_losses", "cc_iteration", "cc_noise",
             "cc_set_latents", "cc_get_latents", "cc_set_params", "cc_get_params",
-            "cc_profile_phases", "cc_graph_kernel_count",
+            "cc_profile_phases", "cc_graph_kernel_count", "cc_rate_bits_noalloc",
             "cc_get_state", "cc_set_state", "cc_free", "cc_strerror", "cc_last_cuda_error"]
