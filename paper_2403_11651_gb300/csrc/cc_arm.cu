@@ -67,38 +67,53 @@ __device__ __forceinline__ void store_row(float* p, const float (&v)[N]) {
     *reinterpret_cast<float4*>(p + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
 }
 
-template <int N, int NL>
+template <int N, int NL, int LPT>
 struct ArmShape {
   static constexpr int S = N + 4;               // smem row stride (conflict-free float4 rows)
   static constexpr int LW = N * N + N;          // floats per LinR layer (W then b)
   static constexpr int OW = NL * LW;            // W_out
   static constexpr int OB = OW + 2 * N;         // b_out
   static constexpr int NP = OB + 2;             // ARM parameters
-  static constexpr int T = kArmTile;
-  static constexpr int tile_floats = 2 * NL * T * S + T * S + 2 * T;
+  static constexpr int T = kArmTile;            // latents per tile
+  static constexpr int TT = kArmTile / LPT;     // threads per CTA
+  // per-layer arrays are LS floats apart: T*S plus an 8-float skew, so that the same row
+  // of two layers falls in different shared-memory banks
+  static constexpr int LS = T * S + 8;
+  static constexpr int tile_floats = 2 * NL * LS + T * S + 2 * T;
   static constexpr int NBLK = NL * ArmBlocking<N>::NB * ArmBlocking<N>::NB;
-  static constexpr int G = T / NBLK;            // interleaved latent groups
+  static constexpr int G = TT / NBLK;           // interleaved latent groups
   static constexpr int NCH_B = NL * N / 4;      // bias chunks of 4
   static constexpr int NCH = NCH_B + N / 4;     // + W_out column chunks (b_out rides on #0)
   static constexpr int XPER = (NCH + NBLK - 1) / NBLK;
   static constexpr int red_floats = G * NP;
   static constexpr int smem_floats = tile_floats > red_floats ? tile_floats : red_floats;
-  static_assert(T % NBLK == 0, "tile must split evenly into weight blocks");
+  static_assert(TT % NBLK == 0 && G >= 1, "threads must split evenly into weight blocks");
 };
 
-template <int N, int NL, bool BWD>
-__global__ void __launch_bounds__(kArmTile, 3) k_arm(ArmArgs a) {
-  using Sh = ArmShape<N, NL>;
+// LPT latents per thread: thread t owns latents t, t + TT, ... of the tile, so each weight
+// operand taken from the constant bank feeds LPT multiply-adds.
+// CTAs per SM of the ARM kernels (one tile of kArmTile latents per CTA): one CTA of 12
+// warps for the wider ARMs keeps every warp of an SM in the same phase of the tile, so
+// they share the instruction stream of the fully unrolled layer code.
+template <int N>
+struct ArmOcc {
+  static constexpr int blocks = N >= 16 ? 1 : 2;
+};
+
+template <int N, int NL, bool BWD, int LPT>
+__global__ void __launch_bounds__(kArmTile / LPT, ArmOcc<N>::blocks) k_arm(ArmArgs a) {
+  using Sh = ArmShape<N, NL, LPT>;
   constexpr int S = Sh::S, LW = Sh::LW, OW = Sh::OW, OB = Sh::OB, NP = Sh::NP, T = Sh::T;
+  constexpr int LS = Sh::LS, TT = Sh::TT;
   constexpr int RB = ArmBlocking<N>::RB, NB = ArmBlocking<N>::NB;
   constexpr int NBLK = Sh::NBLK, G = Sh::G, NCH_B = Sh::NCH_B, NCH = Sh::NCH;
   constexpr int XPER = Sh::XPER;
 
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
-  float* s_in = sm;                    // [NL][T][S] input of LinR layer L
-  float* s_dz = s_in + NL * T * S;     // [NL][T][S] dz of LinR layer L
-  float* s_ho = s_dz + NL * T * S;     // [T][S]     input of the output layer
+  float* s_in = sm;                    // [NL][T][S] input of LinR layer L (layer stride LS)
+  float* s_dz = s_in + NL * LS;        // [NL][T][S] dz of LinR layer L (layer stride LS)
+  float* s_ho = s_dz + NL * LS;        // [T][S]     input of the output layer
   float* s_do = s_ho + T * S;          // [T][2]     (d bits/d mu, d bits/d s)
 
   const int tid = threadIdx.x;
@@ -124,85 +139,123 @@ __global__ void __launch_bounds__(kArmTile, 3) k_arm(ArmArgs a) {
     const int l = td.x;
     const int w = a.g.w[l];
     const int n_l = a.g.h[l] * w;
-    const int i = td.y + tid;
-    const bool valid = i < n_l;
+    const int pw = a.g.pw[l];
     // zero-bordered plane: every causal neighbour is inside the allocation, outside the
     // grid it reads the zero border
-    const int pw = a.g.pw[l];
-    int r = 0, c = 0;
-    if (valid) { r = i / w; c = i - r * w; }
-    const float* ctr = a.yhat + a.g.poff[l] + (long long)(r + kCtxPad) * pw + c + kCtxPad;
-    float h[N];
+    bool valid[LPT];
+    float h[LPT][N], yq[LPT];
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const int2 o = c_off[k];
-      h[k] = __ldg(ctr + o.x * pw + o.y);
-    }
-    const float yq = __ldg(ctr);
-    if (!valid) {
+    for (int q = 0; q < LPT; ++q) {
+      const int i = td.y + tid + q * TT;
+      valid[q] = i < n_l;
+      int r = 0, c = 0;
+      if (valid[q]) { r = i / w; c = i - r * w; }
+      const float* ctr = a.yhat + a.g.poff[l] + (long long)(r + kCtxPad) * pw + c + kCtxPad;
 #pragma unroll
-      for (int k = 0; k < N; ++k) h[k] = 0.f;
+      for (int k = 0; k < N; ++k) {
+        const int2 o = c_off[k];
+        h[q][k] = valid[q] ? __ldg(ctr + o.x * pw + o.y) : 0.f;
+      }
+      yq[q] = valid[q] ? __ldg(ctr) : 0.f;
     }
 
     // forward: h <- h + relu(W h + b), NL times
-    uint32_t mask[NL];
+    uint32_t mask[LPT][NL];
 #pragma unroll
     for (int L = 0; L < NL; ++L) {
-      if constexpr (BWD) store_row<N>(s_in + (L * T + tid) * S, h);
-      float z[N];
+      if constexpr (BWD) {
 #pragma unroll
-      for (int o = 0; o < N; ++o) z[o] = c_arm[L * LW + N * N + o];
+        for (int q = 0; q < LPT; ++q) store_row<N>(s_in + L * LS + (tid + q * TT) * S, h[q]);
+      }
+      float z[LPT][N];
+#pragma unroll
+      for (int o = 0; o < N; ++o)
+#pragma unroll
+        for (int q = 0; q < LPT; ++q) z[q][o] = c_arm[L * LW + N * N + o];
 #pragma unroll
       for (int k = 0; k < N; ++k)
 #pragma unroll
-        for (int o = 0; o < N; ++o) z[o] = fmaf(c_arm[L * LW + o * N + k], h[k], z[o]);
-      uint32_t mk = 0;
+        for (int o = 0; o < N; ++o)
 #pragma unroll
-      for (int o = 0; o < N; ++o) {
-        mk |= (z[o] > 0.f ? 1u : 0u) << o;
-        h[o] += fmaxf(z[o], 0.f);
+          for (int q = 0; q < LPT; ++q)
+            z[q][o] = fmaf(c_arm[L * LW + o * N + k], h[q][k], z[q][o]);
+#pragma unroll
+      for (int q = 0; q < LPT; ++q) {
+        uint32_t mk = 0;
+#pragma unroll
+        for (int o = 0; o < N; ++o) {
+          mk |= (z[q][o] > 0.f ? 1u : 0u) << o;
+          h[q][o] += fmaxf(z[q][o], 0.f);
+        }
+        mask[q][L] = mk;
       }
-      mask[L] = mk;
     }
-    if constexpr (BWD) store_row<N>(s_ho + tid * S, h);
-    float mu = c_arm[OB], s = c_arm[OB + 1];
+    LapOut lo[LPT];
+    {
+      float mu[LPT], s[LPT];
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      mu = fmaf(c_arm[OW + k], h[k], mu);
-      s = fmaf(c_arm[OW + N + k], h[k], s);
+      for (int q = 0; q < LPT; ++q) {
+        if constexpr (BWD) store_row<N>(s_ho + (tid + q * TT) * S, h[q]);
+        mu[q] = c_arm[OB];
+        s[q] = c_arm[OB + 1];
+      }
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+#pragma unroll
+        for (int q = 0; q < LPT; ++q) {
+          mu[q] = fmaf(c_arm[OW + k], h[q][k], mu[q]);
+          s[q] = fmaf(c_arm[OW + N + k], h[q][k], s[q]);
+        }
+#pragma unroll
+      for (int q = 0; q < LPT; ++q) {
+        lo[q] = laplace_bits(yq[q], mu[q], s[q]);
+        if (!valid[q]) lo[q].bits = lo[q].g_y = lo[q].g_mu = lo[q].g_s = 0.f;
+        bits_acc += lo[q].bits;
+      }
     }
-    LapOut lo = laplace_bits(yq, mu, s);
-    if (!valid) lo.bits = lo.g_y = lo.g_mu = lo.g_s = 0.f;
-    bits_acc += lo.bits;
 
     if constexpr (BWD) {
-      reinterpret_cast<float2*>(s_do)[tid] = make_float2(lo.g_mu, lo.g_s);
-      float dh[N];
+      float dh[LPT][N];
 #pragma unroll
-      for (int k = 0; k < N; ++k) dh[k] = lo.g_mu * c_armb[OW + k] + lo.g_s * c_armb[OW + N + k];
+      for (int q = 0; q < LPT; ++q) {
+        reinterpret_cast<float2*>(s_do)[tid + q * TT] = make_float2(lo[q].g_mu, lo[q].g_s);
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+          dh[q][k] = lo[q].g_mu * c_armb[OW + k] + lo[q].g_s * c_armb[OW + N + k];
+      }
 #pragma unroll
       for (int L = NL - 1; L >= 0; --L) {
-        float dz[N];
+        float dz[LPT][N];
 #pragma unroll
-        for (int o = 0; o < N; ++o) dz[o] = ((mask[L] >> o) & 1u) ? dh[o] : 0.f;
-        store_row<N>(s_dz + (L * T + tid) * S, dz);
+        for (int q = 0; q < LPT; ++q) {
+#pragma unroll
+          for (int o = 0; o < N; ++o) dz[q][o] = ((mask[q][L] >> o) & 1u) ? dh[q][o] : 0.f;
+          store_row<N>(s_dz + L * LS + (tid + q * TT) * S, dz[q]);
+        }
 #pragma unroll
         for (int k = 0; k < N; ++k)
 #pragma unroll
-          for (int o = 0; o < N; ++o) dh[k] = fmaf(c_armb[L * LW + o * N + k], dz[o], dh[k]);
-      }
-      if (valid) {
-        const long long q = a.g.off[l] + i;
+          for (int o = 0; o < N; ++o)
 #pragma unroll
-        for (int k = 0; k < N; ++k) a.dctx[k * a.g.n_pad + q] = dh[k];
-        a.gself[q] = lo.g_y;
+            for (int q = 0; q < LPT; ++q)
+              dh[q][k] = fmaf(c_armb[L * LW + o * N + k], dz[q][o], dh[q][k]);
+      }
+#pragma unroll
+      for (int q = 0; q < LPT; ++q) {
+        if (valid[q]) {
+          const long long qq = a.g.off[l] + td.y + tid + q * TT;
+#pragma unroll
+          for (int k = 0; k < N; ++k) a.dctx[k * a.g.n_pad + qq] = dh[q][k];
+          a.gself[qq] = lo[q].g_y;
+        }
       }
       __syncthreads();
 
       // weight gradients of the LinR layers: acc += sum_p dz_L[p][rows] (x) in_L[p][cols]
       {
-        const float* A = s_dz + uL * T * S + urb * RB;
-        const float* B = s_in + uL * T * S + ucb * RB;
+        const float* A = s_dz + uL * LS + urb * RB;
+        const float* B = s_in + uL * LS + ucb * RB;
+#pragma unroll 2
         for (int p = grp; p < T; p += G) {
           float av[RB], bv[RB];
           load_row<RB>(av, A + p * S);
@@ -219,7 +272,7 @@ __global__ void __launch_bounds__(kArmTile, 3) k_arm(ArmArgs a) {
         const int q = unit + qi * NBLK;
         if (q < NCH_B) {
           const int L = q / (N / 4), i0 = (q % (N / 4)) * 4;
-          const float* A = s_dz + L * T * S + i0;
+          const float* A = s_dz + L * LS + i0;
           for (int p = grp; p < T; p += G) {
             const float4 t = *reinterpret_cast<const float4*>(A + p * S);
             xacc[qi][0] += t.x; xacc[qi][1] += t.y; xacc[qi][2] += t.z; xacc[qi][3] += t.w;
@@ -246,13 +299,13 @@ __global__ void __launch_bounds__(kArmTile, 3) k_arm(ArmArgs a) {
     float v = bits_acc;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __shared__ float s_bits[T / 32];
+    __shared__ float s_bits[TT / 32];
     if ((tid & 31) == 0) s_bits[tid >> 5] = v;
     __syncthreads();
     if (tid == 0) {
       float t = 0.f;
 #pragma unroll
-      for (int k = 0; k < T / 32; ++k) t += s_bits[k];
+      for (int k = 0; k < TT / 32; ++k) t += s_bits[k];
       a.part_bits[blockIdx.x] = t;
     }
   }
@@ -284,7 +337,7 @@ __global__ void __launch_bounds__(kArmTile, 3) k_arm(ArmArgs a) {
       }
     }
     __syncthreads();
-    for (int j = tid; j < NP; j += T) {
+    for (int j = tid; j < NP; j += TT) {
       float t = 0.f;
 #pragma unroll
       for (int g = 0; g < G; ++g) t += red[g * NP + j];
@@ -293,24 +346,32 @@ __global__ void __launch_bounds__(kArmTile, 3) k_arm(ArmArgs a) {
   }
 }
 
+// latents per thread of the instantiated ARM kernels
+template <int N, int NL>
+struct ArmLpt {
+  static constexpr int value = 1;
+};
+
 template <int N, int NL, bool BWD>
 static cudaError_t launch_t(const ArmArgs& a, int grid, cudaStream_t st) {
-  using Sh = ArmShape<N, NL>;
+  constexpr int LPT = ArmLpt<N, NL>::value;
+  using Sh = ArmShape<N, NL, LPT>;
   const size_t smem = BWD ? (size_t)Sh::smem_floats * sizeof(float) : 0;
-  k_arm<N, NL, BWD><<<grid, kArmTile, smem, st>>>(a);
+  k_arm<N, NL, BWD, LPT><<<grid, kArmTile / LPT, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <int N, int NL>
 static cudaError_t prepare_t() {
-  return cudaFuncSetAttribute(k_arm<N, NL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(ArmShape<N, NL>::smem_floats * sizeof(float)));
+  constexpr int LPT = ArmLpt<N, NL>::value;
+  return cudaFuncSetAttribute(k_arm<N, NL, true, LPT>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(ArmShape<N, NL, LPT>::smem_floats * sizeof(float)));
 }
-
 
 template <int N, int NL>
 static size_t smem_t(bool bwd) {
-  return bwd ? (size_t)ArmShape<N, NL>::smem_floats * sizeof(float) : 0;
+  return bwd ? (size_t)ArmShape<N, NL, ArmLpt<N, NL>::value>::smem_floats * sizeof(float) : 0;
 }
 
 #define CC_ARM_DISPATCH(FN, ...)                                              \
@@ -350,8 +411,8 @@ size_t arm_smem_bytes(const Arch& a, bool backward) {
 }
 
 int arm_blocks_per_sm(const Arch& a, bool backward) {
-  (void)a;
-  return backward ? 3 : 4;
+  (void)backward;
+  return a.N >= 16 ? ArmOcc<24>::blocks : ArmOcc<8>::blocks;
 }
 
 cudaError_t arm_upload(const float* d_params, int n_arm, const int2* d_offsets, int N,

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <vector>
 
 #include "cc_internal.cuh"
@@ -143,6 +144,8 @@ struct cc_ctx {
   int dev = 0;
   cudaStream_t st = nullptr;
   cudaStream_t cap = nullptr;
+  cudaStream_t side = nullptr;        // ARM branch of a pass, concurrent with the synthesis
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool own_mem = false;
   void* mem = nullptr;
   size_t bytes = 0;
@@ -233,7 +236,13 @@ int setup(cc_ctx* c, const cc_config* cfg, int H, int W) {
   c->n_tiles = (int)c->h_tiles.size();
   const int sms = sm_count();
   if (sms <= 0) return fail_cuda(cudaErrorNoDevice, "cudaDeviceGetAttribute");
-  c->grid_arm = std::min(c->n_tiles, sms * arm_blocks_per_sm(c->arch, true));
+  // the ARM kernel runs beside the synthesis chain: it gets a share of the SMs
+  // (CC_ARM_SM_SHARE, default 0.5), the rest stay free for the chain's kernels
+  double share = 0.5;
+  if (const char* env = getenv("CC_ARM_SM_SHARE")) share = atof(env);
+  share = share < 0.05 ? 0.05 : (share > 1.0 ? 1.0 : share);
+  const int arm_sms = std::max(1, (int)std::lround(share * sms));
+  c->grid_arm = std::min(c->n_tiles, arm_sms * arm_blocks_per_sm(c->arch, true));
   c->grid_syn = std::max(1, std::min((c->HW + kPixTile - 1) / kPixTile, 2 * sms));
   const int n1x1 = 11 * c->arch.C + 3;
   const int vconv = c->lay.n_arm + n1x1;
@@ -266,21 +275,31 @@ void build_sections(cc_ctx* c) {
 // One pass of the hot path.  qmode: quantisation mode of k_quantize.  backward: run the
 // backward kernels (and the update when apply).  grad_out: device buffer receiving dL/dy
 // then dL/dparams, or nullptr.
+// With ev (per-phase timing) every kernel runs in order on s; otherwise the ARM kernel
+// runs on the side stream, concurrently with the upsampling and synthesis chain, and the
+// reductions wait for both.
 cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bool apply,
                          float* grad_out, bool advance, cudaEvent_t* ev = nullptr) {
   const Arch& a = c->arch;
   const size_t HW = (size_t)c->HW;
   auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], s) : cudaSuccess; };
+  const bool fork = ev == nullptr;
+  cudaStream_t sa = fork ? c->side : s;
   CKE(mark(0));
   CKE(arm_upload(c->params, c->lay.n_arm, c->offs, a.N, s));
   CKE(syn_upload(c->params, c->lay, a, s));
   CKE(quantize_launch(c->geo, c->y, c->yhat, c->yhat_bord, c->noise, qmode, c->sc, c->ste_start, c->cfg.seed,
                       -1, s));
   CKE(mark(1));
+  if (fork) {
+    CKE(cudaEventRecord(c->ev_fork, s));
+    CKE(cudaStreamWaitEvent(sa, c->ev_fork, 0));
+  }
   CKE(arm_launch(a, backward, c->yhat_bord, c->geo, c->tiles, c->n_tiles, c->grid_arm, c->dctx,
-                 c->gself, c->part_arm, c->part_bits, s));
+                 c->gself, c->part_arm, c->part_bits, sa));
+  if (fork) CKE(cudaEventRecord(c->ev_join, sa));
   CKE(mark(2));
-  CKE(up_forward(a, c->geo, c->yhat, c->up, s));
+  CKE(up_forward(a, c->geo, c->yhat, c->up, c->grid_syn, s));
   CKE(mark(3));
   CKE(syn_forward(a, c->geo, c->yhat, c->up, c->x, c->hbuf, c->dhbuf + (size_t)a.NR * 3 * HW,
                   c->part_d, c->grid_syn, s));
@@ -291,12 +310,15 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
     CKE(mark(5));
     CKE(up_backward(a, c->geo, c->yhat, c->up, c->gsyn, c->part_up, c->grid_syn, s));
     CKE(mark(6));
+    if (fork) CKE(cudaStreamWaitEvent(s, c->ev_join, 0));
     CKE(reduce_sections(c->tab, c->part2, c->n_virtual, c->slices, s));
     CKE(param_update(c->lay, a, c->part2, c->slices, c->params, c->mp, c->vp,
                      grad_out ? grad_out + c->geo.n_lat : nullptr, apply, c->cfg.lr, c->sc, s));
     CKE(latent_update(c->geo, a, c->offs, c->gsyn, c->gself, c->dctx,
                       (float)((double)c->cfg.lam / (double)c->HW), c->y, c->my, c->vy, grad_out,
                       apply, c->cfg.lr, c->sc, s));
+  } else if (fork) {
+    CKE(cudaStreamWaitEvent(s, c->ev_join, 0));
   }
   CKE(finish_iteration(c->part_d, c->grid_syn, c->part_bits, c->grid_arm,
                        1.0 / (3.0 * (double)HW), 1.0 / (double)HW, (double)c->cfg.lam, c->sc,
@@ -411,6 +433,11 @@ int init_common(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
   auto bail = [&](int code) { cc_free(c); return code; };
   cudaError_t ce = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
   if (ce != cudaSuccess) return bail(fail_cuda(ce, "cudaStreamCreate"));
+  if ((ce = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(fail_cuda(ce, "cudaStreamCreate"));
+  if ((ce = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+      (ce = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(fail_cuda(ce, "cudaEventCreate"));
   if ((ce = arm_prepare(c->arch)) != cudaSuccess) return bail(fail_cuda(ce, "arm_prepare"));
   if ((ce = syn_prepare(c->arch)) != cudaSuccess) return bail(fail_cuda(ce, "syn_prepare"));
   if ((ce = cudaMemsetAsync(c->mem, 0, need, c->st)) != cudaSuccess)
@@ -553,7 +580,7 @@ int cc_decode(cc_ctx* c, float* rgb_out_hwc) {
   CK(syn_upload(c->params, c->lay, a, c->st));
   CK(quantize_launch(c->geo, c->y, c->yhat, c->yhat_bord, c->noise, 1, c->sc, c->ste_start, c->cfg.seed, -1,
                      c->st));
-  CK(up_forward(a, c->geo, c->yhat, c->up, c->st));
+  CK(up_forward(a, c->geo, c->yhat, c->up, c->grid_syn, c->st));
   CK(syn_forward(a, c->geo, c->yhat, c->up, c->x, c->hbuf, c->dhbuf + (size_t)a.NR * 3 * HW,
                  c->part_d, c->grid_syn, c->st));
   CK(syn_decode(a, c->geo, c->hbuf + (size_t)a.NR * 3 * HW, c->dz, c->st));
@@ -765,7 +792,11 @@ void cc_free(cc_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   if (c->g1) cudaGraphExecDestroy(c->g1);
   if (c->g16) cudaGraphExecDestroy(c->g16);
+  if (c->side) cudaStreamSynchronize(c->side);
   if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->own_mem && c->mem) cudaFree(c->mem);
   delete c;
 }

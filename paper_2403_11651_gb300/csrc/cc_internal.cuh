@@ -9,7 +9,7 @@
 namespace cc {
 
 constexpr int kLevels = 7;        // L of Sec. II "Decoding" item i (fixed by Table 1 "7-C")
-constexpr int kArmTile = 128;     // latents per ARM tile (= threads per ARM block)
+constexpr int kArmTile = 384;     // latents per ARM tile (= threads per ARM block)
 constexpr int kPixTile = 256;     // pixels per synthesis block
 constexpr int kLogCap = 4096;     // per-iteration loss log entries kept on the device
 
@@ -89,7 +89,7 @@ struct UpPlan {
 cudaError_t syn_upload(const float* d_params, const Layout& lay, const Arch& a,
                        cudaStream_t st);
 cudaError_t up_forward(const Arch& a, const Geo& g, const float* yhat, const UpPlan& up,
-                       cudaStream_t st);
+                       int ctas, cudaStream_t st);
 cudaError_t up_backward(const Arch& a, const Geo& g, const float* yhat, const UpPlan& up,
                         float* gsyn, float* part_up, int grid, cudaStream_t st);
 cudaError_t syn_forward(const Arch& a, const Geo& g, const float* yhat, const UpPlan& up,

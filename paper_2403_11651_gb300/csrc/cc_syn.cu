@@ -120,7 +120,7 @@ struct UpBwdArgs {
 // edge), giving dL/d in[i] = sum f[u] dout[o] and the filter gradient in[i] * dout[o].
 // Inputs whose 8 x 8 output window lies inside the plane take a branch-free path.
 template <int K>
-__global__ void __launch_bounds__(256) k_up_bwd(UpBwdArgs a) {
+__global__ void __launch_bounds__(128) k_up_bwd(UpBwdArgs a) {
   constexpr int c = K / 2 - 1;
   constexpr int KK = K * K;
   const int li = blockIdx.y;
@@ -138,52 +138,50 @@ __global__ void __launch_bounds__(256) k_up_bwd(UpBwdArgs a) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const int iy = p / a.sw, ix = p - iy * a.sw;
     const float xin = __ldg(in + p);
-    const int oy0 = 2 * iy - c, ox0 = 2 * ix - c;
-    const bool inner = iy > 0 && ix > 0 && iy < a.sh - 1 && ix < a.sw - 1 && oy0 >= 0 &&
-                       ox0 >= 0 && oy0 + K <= a.dh && ox0 + K <= a.dw;
-    if (inner) {
-      const float* base = dout + oy0 * a.dw + ox0;
-      float g[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int uy = 0; uy < K; ++uy) {
-        const float* row = base + uy * a.dw;
-#pragma unroll
-        for (int ux = 0; ux < K; ++ux) {
-          const float gv = __ldg(row + ux);
-          g[ux & 3] = fmaf(f[uy * K + ux], gv, g[ux & 3]);
-          facc[uy * K + ux] = fmaf(xin, gv, facc[uy * K + ux]);
-        }
-      }
-      din[p] = (g[0] + g[1]) + (g[2] + g[3]);
-      continue;
-    }
+    // virtual input positions folding onto (iy, ix) through the clamp: just (iy, ix)
+    // inside the plane, up to K/4 more beyond an edge
     const int vy0 = iy == 0 ? -(K / 4) : iy;
     const int vy1 = iy == a.sh - 1 ? (a.dh - 1 + c) >> 1 : iy;
     const int vx0 = ix == 0 ? -(K / 4) : ix;
     const int vx1 = ix == a.sw - 1 ? (a.dw - 1 + c) >> 1 : ix;
-    float g = 0.f;
+    float g[4] = {0.f, 0.f, 0.f, 0.f};
     for (int vy = vy0; vy <= vy1; ++vy) {
+      int roff[K];
+      uint32_t rok = 0;
+#pragma unroll
+      for (int uy = 0; uy < K; ++uy) {
+        const int oy = 2 * vy - c + uy;
+        rok |= (oy >= 0 && oy < a.dh ? 1u : 0u) << uy;
+        roff[uy] = clampi(oy, 0, a.dh - 1) * a.dw;
+      }
       for (int vx = vx0; vx <= vx1; ++vx) {
+        int col[K];
+        uint32_t cok = 0;
+#pragma unroll
+        for (int ux = 0; ux < K; ++ux) {
+          const int ox = 2 * vx - c + ux;
+          cok |= (ox >= 0 && ox < a.dw ? 1u : 0u) << ux;
+          col[ux] = clampi(ox, 0, a.dw - 1);
+        }
+        // every read is inside the plane; reads of outputs beyond it count as zero
 #pragma unroll
         for (int uy = 0; uy < K; ++uy) {
-          const int oy = 2 * vy - c + uy;
-          const bool oky = oy >= 0 && oy < a.dh;
-          const int oyc = clampi(oy, 0, a.dh - 1);
+          const float* row = dout + roff[uy];
+          const bool ry = (rok >> uy) & 1u;
 #pragma unroll
           for (int ux = 0; ux < K; ++ux) {
-            const int ox = 2 * vx - c + ux;
-            const bool ok = oky && ox >= 0 && ox < a.dw;
-            const float gv = ok ? __ldg(dout + oyc * a.dw + clampi(ox, 0, a.dw - 1)) : 0.f;
-            g = fmaf(f[uy * K + ux], gv, g);
+            float gv = __ldg(row + col[ux]);
+            gv = (ry && ((cok >> ux) & 1u)) ? gv : 0.f;
+            g[ux & 3] = fmaf(f[uy * K + ux], gv, g[ux & 3]);
             facc[uy * K + ux] = fmaf(xin, gv, facc[uy * K + ux]);
           }
         }
       }
     }
-    din[p] = g;
+    din[p] = (g[0] + g[1]) + (g[2] + g[3]);
   }
   // per-CTA filter gradient: warp sums, then warps in order
-  __shared__ float s_w[8][KK];
+  __shared__ float s_w[4][KK];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int u = 0; u < KK; ++u) {
@@ -202,7 +200,7 @@ __global__ void __launch_bounds__(256) k_up_bwd(UpBwdArgs a) {
 
 template <int K>
 static cudaError_t up_forward_k(const Arch& ar, const Geo& g, const float* yhat,
-                                const UpPlan& up, cudaStream_t st) {
+                                const UpPlan& up, int ctas, cudaStream_t st) {
   for (int j = kLevels - 2; j >= 0; --j) {
     UpFwdArgs a;
     int n = 0;
@@ -212,9 +210,11 @@ static cudaError_t up_forward_k(const Arch& ar, const Geo& g, const float* yhat,
       a.fidx[n] = ar.per_level ? l - 1 : 0;
     }
     a.sh = g.h[j + 1]; a.sw = g.w[j + 1]; a.dh = g.h[j]; a.dw = g.w[j];
+    // about three resident waves in total, so that each thread loads its level's filter
+    // once for several quads
     const int tot = ((a.dh + 1) / 2) * ((a.dw + 1) / 2);
-    dim3 grid((tot + 255) / 256 < 1024 ? (tot + 255) / 256 : 1024, n);
-    k_up_fwd<K><<<grid, 256, 0, st>>>(a);
+    const int need = (tot + 255) / 256, cap = (3 * ctas) / n > 1 ? (3 * ctas) / n : 1;
+    k_up_fwd<K><<<dim3(need < cap ? need : cap, n), 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -222,9 +222,9 @@ static cudaError_t up_forward_k(const Arch& ar, const Geo& g, const float* yhat,
 }
 
 cudaError_t up_forward(const Arch& a, const Geo& g, const float* yhat, const UpPlan& up,
-                       cudaStream_t st) {
-  if (a.K == 8) return up_forward_k<8>(a, g, yhat, up, st);
-  if (a.K == 4) return up_forward_k<4>(a, g, yhat, up, st);
+                       int ctas, cudaStream_t st) {
+  if (a.K == 8) return up_forward_k<8>(a, g, yhat, up, ctas, st);
+  if (a.K == 4) return up_forward_k<4>(a, g, yhat, up, ctas, st);
   return cudaErrorInvalidValue;
 }
 
@@ -246,8 +246,10 @@ static cudaError_t up_backward_k(const Arch& ar, const Geo& g, const float* yhat
     // rows [j * grid, j * grid + grid) belong to this step; only as many CTAs as there is
     // work for are launched, the rows of the others stay zero from the context set-up
     a.part = part_up + (long long)j * grid * kLevels * K * K;
-    const int need = (a.sh * a.sw + 255) / 256;
-    k_up_bwd<K><<<dim3(need < grid ? need : grid, n), 256, 0, st>>>(a);
+    // 128-thread CTAs, about two resident per SM in total (grid = 2 x SMs): each thread
+    // loads its filter once and handles many inputs before the per-CTA reduction
+    const int need = (a.sh * a.sw + 127) / 128, cap = grid / n > 1 ? grid / n : 1;
+    k_up_bwd<K><<<dim3(need < cap ? need : cap, n), 128, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -27,6 +27,8 @@ def main():
     ap.add_argument("--phases", type=int, default=3)
     ap.add_argument("--H", type=int, default=0)
     ap.add_argument("--W", type=int, default=0)
+    ap.add_argument("--timed", type=int, default=0,
+                    help="also time this many graph-replayed iterations with CUDA events")
     a = ap.parse_args()
     d = cc.load_config(a.config)
     H, W = a.H or d["H"], a.W or d["W"]
@@ -37,10 +39,21 @@ def main():
     try:
         cc.cc_encode_iters(ctx, a.warmup)
         cc.cc_encode_iters(ctx, a.iters)
+        iter_ms = None
+        if a.timed:
+            import torch
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(torch.cuda.default_stream())
+            cc.cc_encode_iters(ctx, a.timed)
+            e1.record(torch.cuda.default_stream())
+            torch.cuda.synchronize()
+            iter_ms = e0.elapsed_time(e1) / a.timed
         ph = cc.cc_profile_phases(ctx, a.phases) if a.phases else []
         D, R, cost = cc.cc_rd_cost(ctx, False)
         print(json.dumps({"H": H, "W": W, "config": a.config,
                           "kernels_per_iteration": cc.cc_graph_kernel_count(ctx),
+                          "iter_ms": iter_ms,
                           "phase_ms": {n: float(v) for n, v in zip(cc.PHASES, ph)},
                           "D": D, "R": R, "cost": cost}))
     finally:
