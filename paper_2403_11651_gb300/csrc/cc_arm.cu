@@ -20,11 +20,20 @@ namespace cc {
 
 constexpr int kMaxN = 24;
 constexpr int kMaxArmParams = 2 * (kMaxN * kMaxN + kMaxN) + 2 * kMaxN + 2;
-__constant__ float c_arm[kMaxArmParams];
-// A second copy of the weights, read by the backward pass only: with a single bank the
-// compiler keeps every weight used by both passes in a register between its two uses.
-__constant__ float c_armb[kMaxArmParams];
-__constant__ int2 c_off[kMaxN];  // (dy, dx) of each context slot, raster order
+// Constant bank of the ARM kernels, filled by one device-to-device copy of an image built
+// on the device before every pass.  `wb` is a second copy of the weights read by the
+// backward pass only: with a single copy the compiler keeps every weight used by both
+// passes in a register between its two uses.
+constexpr int kArmBankFloats = (kMaxArmParams + 3) & ~3;   // 16-byte aligned copies
+struct __align__(16) ArmBank {
+  float w[kArmBankFloats];
+  float wb[kArmBankFloats];
+  int2 off[kMaxN];  // (dy, dx) of each context slot, raster order
+};
+__constant__ ArmBank c_armbank;
+#define c_arm c_armbank.w
+#define c_armb c_armbank.wb
+#define c_off c_armbank.off
 
 struct ArmArgs {
   const float* yhat;   // zero-bordered copy (Geo::poff, Geo::pw)
@@ -167,18 +176,33 @@ __global__ void __launch_bounds__(kArmTile / LPT, ArmOcc<N>::blocks) k_arm(ArmAr
 #pragma unroll
         for (int q = 0; q < LPT; ++q) store_row<N>(s_in + L * LS + (tid + q * TT) * S, h[q]);
       }
+      // packed FP32 pairs: (z[2m], z[2m+1]) += (W[2m][k], W[2m+1][k]) * (h[k], h[k]); the
+      // forward bank stores every layer's weights in those pairs, input k innermost, so
+      // consecutive multiply-adds use adjacent weights
+      float2 zp[LPT][N / 2];
+      {
+        float2 hd[LPT][N];
+#pragma unroll
+        for (int q = 0; q < LPT; ++q)
+#pragma unroll
+          for (int k = 0; k < N; ++k) hd[q][k] = make_float2(h[q][k], h[q][k]);
+        const float2* wp = reinterpret_cast<const float2*>(c_arm + L * LW);
+#pragma unroll
+        for (int m = 0; m < N / 2; ++m)
+#pragma unroll
+          for (int q = 0; q < LPT; ++q) zp[q][m] = wp[N * N / 2 + m];   // bias pair
+#pragma unroll
+        for (int m = 0; m < N / 2; ++m)
+#pragma unroll
+          for (int k = 0; k < N; ++k)
+#pragma unroll
+            for (int q = 0; q < LPT; ++q) zp[q][m] = __ffma2_rn(wp[m * N + k], hd[q][k], zp[q][m]);
+      }
       float z[LPT][N];
 #pragma unroll
-      for (int o = 0; o < N; ++o)
+      for (int q = 0; q < LPT; ++q)
 #pragma unroll
-        for (int q = 0; q < LPT; ++q) z[q][o] = c_arm[L * LW + N * N + o];
-#pragma unroll
-      for (int k = 0; k < N; ++k)
-#pragma unroll
-        for (int o = 0; o < N; ++o)
-#pragma unroll
-          for (int q = 0; q < LPT; ++q)
-            z[q][o] = fmaf(c_arm[L * LW + o * N + k], h[q][k], z[q][o]);
+        for (int m = 0; m < N / 2; ++m) { z[q][2 * m] = zp[q][m].x; z[q][2 * m + 1] = zp[q][m].y; }
 #pragma unroll
       for (int q = 0; q < LPT; ++q) {
         uint32_t mk = 0;
@@ -193,19 +217,17 @@ __global__ void __launch_bounds__(kArmTile / LPT, ArmOcc<N>::blocks) k_arm(ArmAr
     LapOut lo[LPT];
     {
       float mu[LPT], s[LPT];
+      // (mu, s) as one packed pair; the forward bank stores W_out as (W_out[0][k], W_out[1][k])
+      const float2* wo = reinterpret_cast<const float2*>(c_arm + OW);
 #pragma unroll
       for (int q = 0; q < LPT; ++q) {
         if constexpr (BWD) store_row<N>(s_ho + (tid + q * TT) * S, h[q]);
-        mu[q] = c_arm[OB];
-        s[q] = c_arm[OB + 1];
+        float2 ms = make_float2(c_arm[OB], c_arm[OB + 1]);
+#pragma unroll
+        for (int k = 0; k < N; ++k) ms = __ffma2_rn(wo[k], make_float2(h[q][k], h[q][k]), ms);
+        mu[q] = ms.x;
+        s[q] = ms.y;
       }
-#pragma unroll
-      for (int k = 0; k < N; ++k)
-#pragma unroll
-        for (int q = 0; q < LPT; ++q) {
-          mu[q] = fmaf(c_arm[OW + k], h[q][k], mu[q]);
-          s[q] = fmaf(c_arm[OW + N + k], h[q][k], s[q]);
-        }
 #pragma unroll
       for (int q = 0; q < LPT; ++q) {
         lo[q] = laplace_bits(yq[q], mu[q], s[q]);
@@ -215,31 +237,46 @@ __global__ void __launch_bounds__(kArmTile / LPT, ArmOcc<N>::blocks) k_arm(ArmAr
     }
 
     if constexpr (BWD) {
-      float dh[LPT][N];
+      // packed pairs over inputs: (dh[k], dh[k+1]) += (W[o][k], W[o][k+1]) * (dz[o], dz[o]),
+      // read from the row-major copy of the weights (adjacent along k)
+      float2 dhp[LPT][N / 2];
 #pragma unroll
       for (int q = 0; q < LPT; ++q) {
         reinterpret_cast<float2*>(s_do)[tid + q * TT] = make_float2(lo[q].g_mu, lo[q].g_s);
+        const float2* w0 = reinterpret_cast<const float2*>(c_armb + OW);
+        const float2* w1 = reinterpret_cast<const float2*>(c_armb + OW + N);
+        const float2 gm = make_float2(lo[q].g_mu, lo[q].g_mu), gs = make_float2(lo[q].g_s, lo[q].g_s);
 #pragma unroll
-        for (int k = 0; k < N; ++k)
-          dh[q][k] = lo[q].g_mu * c_armb[OW + k] + lo[q].g_s * c_armb[OW + N + k];
+        for (int j = 0; j < N / 2; ++j) dhp[q][j] = __ffma2_rn(w0[j], gm, __fmul2_rn(w1[j], gs));
       }
 #pragma unroll
       for (int L = NL - 1; L >= 0; --L) {
-        float dz[LPT][N];
+        float2 dzd[LPT][N];
 #pragma unroll
         for (int q = 0; q < LPT; ++q) {
+          float dz[N];
 #pragma unroll
-          for (int o = 0; o < N; ++o) dz[q][o] = ((mask[q][L] >> o) & 1u) ? dh[q][o] : 0.f;
-          store_row<N>(s_dz + L * LS + (tid + q * TT) * S, dz[q]);
+          for (int o = 0; o < N; ++o) {
+            const float dv = (o & 1) ? dhp[q][o >> 1].y : dhp[q][o >> 1].x;
+            dz[o] = ((mask[q][L] >> o) & 1u) ? dv : 0.f;
+            dzd[q][o] = make_float2(dz[o], dz[o]);
+          }
+          store_row<N>(s_dz + L * LS + (tid + q * TT) * S, dz);
         }
+        const float2* wr = reinterpret_cast<const float2*>(c_armb + L * LW);
 #pragma unroll
-        for (int k = 0; k < N; ++k)
+        for (int o = 0; o < N; ++o)
 #pragma unroll
-          for (int o = 0; o < N; ++o)
+          for (int j = 0; j < N / 2; ++j)
 #pragma unroll
             for (int q = 0; q < LPT; ++q)
-              dh[q][k] = fmaf(c_armb[L * LW + o * N + k], dz[q][o], dh[q][k]);
+              dhp[q][j] = __ffma2_rn(wr[o * (N / 2) + j], dzd[q][o], dhp[q][j]);
       }
+      float dh[LPT][N];
+#pragma unroll
+      for (int q = 0; q < LPT; ++q)
+#pragma unroll
+        for (int j = 0; j < N / 2; ++j) { dh[q][2 * j] = dhp[q][j].x; dh[q][2 * j + 1] = dhp[q][j].y; }
 #pragma unroll
       for (int q = 0; q < LPT; ++q) {
         if (valid[q]) {
@@ -415,15 +452,40 @@ int arm_blocks_per_sm(const Arch& a, bool backward) {
   return a.N >= 16 ? ArmOcc<24>::blocks : ArmOcc<8>::blocks;
 }
 
+__global__ void k_arm_image(const float* __restrict__ params, int n_arm,
+                            const int2* __restrict__ offs, int N, int NL, ArmBank* img) {
+  // wb: the flat row-major parameters; w: the same with each LinR layer's W stored as
+  // pairs (W[2m][k], W[2m+1][k]) (m outer, k inner) and W_out as (W_out[0][k], W_out[1][k])
+  const int LW = N * N + N, OW = NL * LW;
+  for (int i = threadIdx.x; i < kArmBankFloats; i += blockDim.x) {
+    const float v = i < n_arm ? params[i] : 0.f;
+    img->wb[i] = v;
+    float f = v;
+    if (i < OW) {
+      const int L = i / LW, r = i - L * LW;
+      if (r < N * N) {
+        const int pair = r >> 1, m = pair / N, k = pair - m * N;
+        f = params[L * LW + (2 * m + (r & 1)) * N + k];
+      }
+    } else if (i < OW + 2 * N) {
+      const int r = i - OW;
+      f = params[OW + (r & 1) * N + (r >> 1)];
+    }
+    img->w[i] = f;
+  }
+  for (int k = threadIdx.x; k < kMaxN; k += blockDim.x)
+    img->off[k] = k < N ? offs[k] : make_int2(0, 0);
+}
+
+size_t arm_image_bytes() { return sizeof(ArmBank); }
+
 cudaError_t arm_upload(const float* d_params, int n_arm, const int2* d_offsets, int N,
-                       cudaStream_t st) {
-  cudaError_t e = cudaMemcpyToSymbolAsync(c_arm, d_params, (size_t)n_arm * sizeof(float), 0,
-                                          cudaMemcpyDeviceToDevice, st);
+                       void* d_image, cudaStream_t st) {
+  const int NL = (n_arm - 2 * N - 2) / (N * N + N);
+  k_arm_image<<<1, 256, 0, st>>>(d_params, n_arm, d_offsets, N, NL, (ArmBank*)d_image);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = cudaMemcpyToSymbolAsync(c_armb, d_params, (size_t)n_arm * sizeof(float), 0,
-                              cudaMemcpyDeviceToDevice, st);
-  if (e != cudaSuccess) return e;
-  return cudaMemcpyToSymbolAsync(c_off, d_offsets, (size_t)N * sizeof(int2), 0,
+  return cudaMemcpyToSymbolAsync(c_armbank, d_image, sizeof(ArmBank), 0,
                                  cudaMemcpyDeviceToDevice, st);
 }
 

@@ -156,6 +156,7 @@ struct cc_ctx {
   float* grad_scratch;
   uint8_t* img_u8;
   int2 *tiles, *offs;
+  void *arm_image, *syn_image;   // constant-bank images built on the device
   IterScalars* sc;
   double* log;
   UpPlan up;
@@ -209,6 +210,8 @@ size_t plan(cc_ctx* c, char* base) {
   c->img_u8 = (uint8_t*)take(3 * HW);
   c->tiles = (int2*)take((size_t)c->n_tiles * sizeof(int2));
   c->offs = (int2*)take(24 * sizeof(int2));
+  c->arm_image = take(arm_image_bytes());
+  c->syn_image = take(syn_image_bytes());
   c->sc = (IterScalars*)take(sizeof(IterScalars));
   c->log = (double*)take((size_t)kLogCap * 3 * sizeof(double));
   for (int l = 1; l < kLevels; ++l)
@@ -286,8 +289,8 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
   const bool fork = ev == nullptr;
   cudaStream_t sa = fork ? c->side : s;
   CKE(mark(0));
-  CKE(arm_upload(c->params, c->lay.n_arm, c->offs, a.N, s));
-  CKE(syn_upload(c->params, c->lay, a, s));
+  CKE(arm_upload(c->params, c->lay.n_arm, c->offs, a.N, c->arm_image, s));
+  CKE(syn_upload(c->params, c->lay, a, c->syn_image, s));
   CKE(quantize_launch(c->geo, c->y, c->yhat, c->yhat_bord, c->noise, qmode, c->sc, c->ste_start, c->cfg.seed,
                       -1, s));
   CKE(mark(1));
@@ -577,7 +580,7 @@ int cc_decode(cc_ctx* c, float* rgb_out_hwc) {
   CK(cudaSetDevice(c->dev));
   const Arch& a = c->arch;
   const size_t HW = (size_t)c->HW;
-  CK(syn_upload(c->params, c->lay, a, c->st));
+  CK(syn_upload(c->params, c->lay, a, c->syn_image, c->st));
   CK(quantize_launch(c->geo, c->y, c->yhat, c->yhat_bord, c->noise, 1, c->sc, c->ste_start, c->cfg.seed, -1,
                      c->st));
   CK(up_forward(a, c->geo, c->yhat, c->up, c->grid_syn, c->st));

@@ -71,8 +71,10 @@ struct IterScalars {
 
 // ---- launchers (each returns the cudaError_t of its launch) ----
 // ARM (cc_arm.cu)
+// Build the ARM constant-bank image in d_image (arm_image_bytes()) and copy it to the bank.
 cudaError_t arm_upload(const float* d_params, int n_arm, const int2* d_offsets, int N,
-                       cudaStream_t st);
+                       void* d_image, cudaStream_t st);
+size_t arm_image_bytes();
 cudaError_t arm_launch(const Arch& a, bool backward, const float* yhat, const Geo& g,
                        const int2* tiles, int n_tiles, int grid, float* dctx, float* gself,
                        float* part_grad, float* part_bits, cudaStream_t st);
@@ -86,8 +88,10 @@ struct UpPlan {
   float* plane[kLevels][kLevels];
   float* dplane[kLevels][kLevels];
 };
-cudaError_t syn_upload(const float* d_params, const Layout& lay, const Arch& a,
+// Build the synthesis / upsampling bank image in d_image (syn_image_bytes()) and copy it.
+cudaError_t syn_upload(const float* d_params, const Layout& lay, const Arch& a, void* d_image,
                        cudaStream_t st);
+size_t syn_image_bytes();
 cudaError_t up_forward(const Arch& a, const Geo& g, const float* yhat, const UpPlan& up,
                        int ctas, cudaStream_t st);
 cudaError_t up_backward(const Arch& a, const Geo& g, const float* yhat, const UpPlan& up,

@@ -19,12 +19,22 @@ namespace cc {
 constexpr int kMaxC = 40;
 constexpr int k3x3 = 84;                  // floats per 3x3 layer (W 3x3x3x3, b 3)
 constexpr int kSyn1x1Base = 2 * k3x3;     // 1x1 layers follow two reserved 3x3 slots
-__constant__ float c_syn[kSyn1x1Base + 11 * kMaxC + 3];
-// A second copy of the bank, read by backward passes only.  With one bank the compiler
-// keeps every weight used by both a forward and a backward loop in a register between the
-// two uses (hundreds of live values); with two, each use is a plain constant operand.
-__constant__ float c_synb[kSyn1x1Base + 11 * kMaxC + 3];
-__constant__ float c_up[(kLevels - 1) * 64];
+constexpr int kSynBank = (kSyn1x1Base + 12 * kMaxC + 4 + 3) & ~3;
+// Constant bank of the synthesis and upsampling kernels, filled by one device-to-device
+// copy of an image built on the device before every pass.  Layout of `syn`:
+// [3x3 layer 0 | 3x3 layer 1 | W_a (C x 7) | b_a (C) | W_b^T (C x 4, 4th column 0) | b_b],
+// W_b transposed so that the three weights of one hidden channel are adjacent.  `synb`
+// is a second copy read by backward passes only: with one copy the compiler keeps every
+// weight used by both a forward and a backward loop in a register between the two uses.
+struct __align__(16) SynBank {
+  float syn[kSynBank];
+  float synb[kSynBank];
+  float up[(kLevels - 1) * 64];
+};
+__constant__ SynBank c_synbank;
+#define c_syn c_synbank.syn
+#define c_synb c_synbank.synb
+#define c_up c_synbank.up
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
@@ -276,7 +286,7 @@ struct Syn1x1Args {
 
 template <int C>
 __global__ void __launch_bounds__(256) k_syn1x1_fwd(Syn1x1Args a) {
-  constexpr int WA = kSyn1x1Base, BA = WA + 7 * C, WB = BA + C, BB = WB + 3 * C;
+  constexpr int WA = kSyn1x1Base, BA = WA + 7 * C, WB = BA + C, BB = WB + 4 * C;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.HW; p += gridDim.x * blockDim.x) {
     float f[kLevels];
 #pragma unroll
@@ -289,7 +299,7 @@ __global__ void __launch_bounds__(256) k_syn1x1_fwd(Syn1x1Args a) {
       for (int k = 0; k < kLevels; ++k) z = fmaf(c_syn[WA + o * kLevels + k], f[k], z);
       const float h1 = fmaxf(z, 0.f);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) z2[j] = fmaf(c_syn[WB + j * C + o], h1, z2[j]);
+      for (int j = 0; j < 3; ++j) z2[j] = fmaf(c_syn[WB + o * 4 + j], h1, z2[j]);
     }
 #pragma unroll
     for (int j = 0; j < 3; ++j) a.h2[j * a.HW + p] = fmaxf(z2[j], 0.f);
@@ -316,7 +326,7 @@ __global__ void __launch_bounds__(256, 2) k_syn1x1_bwd(Syn1x1Args a) {
   using Sh = Syn1x1Shape<C>;
   constexpr int T = Sh::T, SZ = Sh::SZ, SF = Sh::SF, SD = Sh::SD;
   constexpr int NUA = Sh::NUA, NU = Sh::NU, G = Sh::G, NP = Sh::NP;
-  constexpr int WA = kSyn1x1Base, BA = WA + 7 * C, WB = BA + C, BB = WB + 3 * C;
+  constexpr int WA = kSyn1x1Base, BA = WA + 7 * C, WB = BA + C, BB = WB + 4 * C;
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
   float* s_dz1 = sm;               // [T][SZ]
@@ -353,7 +363,7 @@ __global__ void __launch_bounds__(256, 2) k_syn1x1_bwd(Syn1x1Args a) {
       for (int k = 0; k < kLevels; ++k) z = fmaf(c_syn[WA + o * kLevels + k], f[k], z);
       h1[o] = fmaxf(z, 0.f);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) z2[j] = fmaf(c_syn[WB + j * C + o], h1[o], z2[j]);
+      for (int j = 0; j < 3; ++j) z2[j] = fmaf(c_syn[WB + o * 4 + j], h1[o], z2[j]);
     }
     float* hrow = s_h1 + tid * SZ;
 #pragma unroll
@@ -372,7 +382,7 @@ __global__ void __launch_bounds__(256, 2) k_syn1x1_bwd(Syn1x1Args a) {
     for (int o = 0; o < C; ++o) {
       float dh1 = 0.f;
 #pragma unroll
-      for (int j = 0; j < 3; ++j) dh1 = fmaf(c_synb[WB + j * C + o], dz2[j], dh1);
+      for (int j = 0; j < 3; ++j) dh1 = fmaf(c_synb[WB + o * 4 + j], dz2[j], dh1);
       h1[o] = h1[o] > 0.f ? dh1 : 0.f;    // now dz1 (relu'(z1) = [h1 > 0])
 #pragma unroll
       for (int k = 0; k < kLevels; ++k) df[k] = fmaf(c_synb[WA + o * kLevels + k], h1[o], df[k]);
@@ -576,17 +586,22 @@ __global__ void __launch_bounds__(256) k_conv_dx(ConvArgs a) {
     for (int ci = 0; ci < 3; ++ci) acc[ci] = __ldg(a.dhout + ci * HW + q);
     if (qy > 0 && qx > 0 && qy < a.H - 1 && qx < a.W - 1) {
       // interior: output p = q - (dy, dx) read q through tap (dy, dx), no clamping
+      float d[27];
 #pragma unroll
       for (int o = 0; o < 3; ++o)
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
-          for (int dx = -1; dx <= 1; ++dx) {
-            const float d = __ldg(a.dz + o * HW + q - dy * a.W - dx);
+          for (int dx = -1; dx <= 1; ++dx)
+            d[o * 9 + (dy + 1) * 3 + (dx + 1)] = __ldg(a.dz + o * HW + q - dy * a.W - dx);
+      // input channel outer: the nine taps of one (o, ci) pair are adjacent in the bank
 #pragma unroll
-            for (int ci = 0; ci < 3; ++ci)
-              acc[ci] = fmaf(c_syn[Wo + o * 27 + ci * 9 + (dy + 1) * 3 + (dx + 1)], d, acc[ci]);
-          }
+      for (int ci = 0; ci < 3; ++ci)
+#pragma unroll
+        for (int o = 0; o < 3; ++o)
+#pragma unroll
+          for (int t = 0; t < 9; ++t)
+            acc[ci] = fmaf(c_syn[Wo + o * 27 + ci * 9 + t], d[o * 9 + t], acc[ci]);
 #pragma unroll
       for (int ci = 0; ci < 3; ++ci) a.dhin[ci * HW + q] = acc[ci];
       continue;
@@ -739,22 +754,44 @@ cudaError_t syn_decode(const Arch& a, const Geo& g, const float* hbuf_last, floa
   return cudaGetLastError();
 }
 
-cudaError_t syn_upload(const float* d_params, const Layout& lay, const Arch& a,
-                       cudaStream_t st) {
-  // bank c_syn: [3x3 layer 0 | 3x3 layer 1 | W_a b_a W_b b_b]; c_up: the filters
-  const size_t n1x1 = (size_t)(11 * a.C + 3);
-  for (const void* bank : {(const void*)&c_syn, (const void*)&c_synb}) {
-    cudaError_t e = cudaMemcpyToSymbolAsync(bank, d_params + lay.syn0, n1x1 * sizeof(float),
-                                            kSyn1x1Base * sizeof(float),
-                                            cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return e;
-    e = cudaMemcpyToSymbolAsync(bank, d_params + lay.syn0 + n1x1,
-                                (size_t)a.NR * k3x3 * sizeof(float), 0,
-                                cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return e;
+// Bank image from the flat parameters (synthesis section: W_a, b_a, W_b, b_b, then the 3x3
+// layers; upsampling filters).
+__global__ void k_syn_image(const float* __restrict__ syn, int C, int NR,
+                            const float* __restrict__ filters, int n_filt, SynBank* img) {
+  const int n3 = NR * k3x3;
+  const float* p1 = syn;                   // W_a (C x 7), b_a, W_b (3 x C), b_b
+  const float* p3 = syn + 11 * C + 3;      // 3x3 layers
+  for (int i = threadIdx.x; i < kSynBank; i += blockDim.x) {
+    float v = 0.f;
+    if (i < n3) {
+      v = p3[i];
+    } else if (i >= kSyn1x1Base) {
+      const int r = i - kSyn1x1Base;
+      if (r < 8 * C) {
+        v = p1[r];                          // W_a, b_a
+      } else if (r < 12 * C) {
+        const int o = (r - 8 * C) >> 2, j = (r - 8 * C) & 3;
+        v = j < 3 ? p1[8 * C + j * C + o] : 0.f;   // W_b^T
+      } else if (r < 12 * C + 3) {
+        v = p1[11 * C + (r - 12 * C)];      // b_b
+      }
+    }
+    img->syn[i] = v;
+    img->synb[i] = v;
   }
-  return cudaMemcpyToSymbolAsync(c_up, d_params + lay.up0,
-                                 (size_t)lay.n_up * a.K * a.K * sizeof(float), 0,
+  for (int i = threadIdx.x; i < (kLevels - 1) * 64; i += blockDim.x)
+    img->up[i] = i < n_filt ? filters[i] : 0.f;
+}
+
+size_t syn_image_bytes() { return sizeof(SynBank); }
+
+cudaError_t syn_upload(const float* d_params, const Layout& lay, const Arch& a, void* d_image,
+                       cudaStream_t st) {
+  k_syn_image<<<1, 256, 0, st>>>(d_params + lay.syn0, a.C, a.NR, d_params + lay.up0,
+                                 lay.n_up * a.K * a.K, (SynBank*)d_image);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbolAsync(c_synbank, d_image, sizeof(SynBank), 0,
                                  cudaMemcpyDeviceToDevice, st);
 }
 
