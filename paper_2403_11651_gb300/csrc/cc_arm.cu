@@ -111,6 +111,8 @@ struct ArmOcc {
 
 template <int N, int NL, bool BWD, int LPT>
 __global__ void __launch_bounds__(kArmTile / LPT, ArmOcc<N>::blocks) k_arm(ArmArgs a) {
+  pdl_wait();
+  pdl_trigger();
   using Sh = ArmShape<N, NL, LPT>;
   constexpr int S = Sh::S, LW = Sh::LW, OW = Sh::OW, OB = Sh::OB, NP = Sh::NP, T = Sh::T;
   constexpr int LS = Sh::LS, TT = Sh::TT;
@@ -454,6 +456,8 @@ int arm_blocks_per_sm(const Arch& a, bool backward) {
 
 __global__ void k_arm_image(const float* __restrict__ params, int n_arm,
                             const int2* __restrict__ offs, int N, int NL, ArmBank* img) {
+  pdl_wait();
+  pdl_trigger();
   // wb: the flat row-major parameters; w: the same with each LinR layer's W stored as
   // pairs (W[2m][k], W[2m+1][k]) (m outer, k inner) and W_out as (W_out[0][k], W_out[1][k])
   const int LW = N * N + N, OW = NL * LW;

@@ -161,7 +161,7 @@ struct cc_ctx {
   double* log;
   UpPlan up;
   std::vector<int2> h_tiles, h_offs;
-  int n_tiles = 0, grid_arm = 0, grid_syn = 0, slices = 16, n_virtual = 0;
+  int n_tiles = 0, grid_arm = 0, grid_syn = 0, grid_tiles = 0, slices = 16, n_virtual = 0;
   SectionTable tab;
   cudaGraphExec_t g1 = nullptr, g16 = nullptr;
   int iter = 0;
@@ -200,9 +200,9 @@ size_t plan(cc_ctx* c, char* base) {
   c->dz = (float*)take(3 * HW * sizeof(float));
   c->part_arm = (float*)take((size_t)c->grid_arm * c->lay.n_arm * sizeof(float));
   c->part_bits = (float*)take((size_t)c->grid_arm * sizeof(float));
-  c->part_d = (float*)take((size_t)c->grid_syn * sizeof(float));
-  c->part_conv = (float*)take((size_t)a.NR * c->grid_syn * 84 * sizeof(float));
-  c->part_syn = (float*)take((size_t)c->grid_syn * (11 * a.C + 3) * sizeof(float));
+  c->part_d = (float*)take((size_t)c->grid_tiles * sizeof(float));
+  c->part_conv = (float*)take((size_t)a.NR * c->grid_tiles * 84 * sizeof(float));
+  c->part_syn = (float*)take((size_t)c->grid_tiles * (11 * a.C + 3) * sizeof(float));
   c->part_up = (float*)take((size_t)(kLevels - 1) * c->grid_syn * kLevels * a.K * a.K *
                             sizeof(float));
   c->part2 = (float*)take((size_t)c->slices * c->n_virtual * sizeof(float));
@@ -247,6 +247,11 @@ int setup(cc_ctx* c, const cc_config* cfg, int H, int W) {
   const int arm_sms = std::max(1, (int)std::lround(share * sms));
   c->grid_arm = std::min(c->n_tiles, arm_sms * arm_blocks_per_sm(c->arch, true));
   c->grid_syn = std::max(1, std::min((c->HW + kPixTile - 1) / kPixTile, 2 * sms));
+  // synthesis: CC_SYN_CTAS_PER_SM (default 4) CTAs per SM loop over the 8 x 32 tiles, so
+  // that each sums its weight-gradient registers once for several tiles
+  int syn_per_sm = 4;
+  if (const char* env = getenv("CC_SYN_CTAS_PER_SM")) syn_per_sm = std::max(1, std::min(64, atoi(env)));
+  c->grid_tiles = std::max(1, std::min(syn_tile_count(c->geo), syn_per_sm * sms));
   const int n1x1 = 11 * c->arch.C + 3;
   const int vconv = c->lay.n_arm + n1x1;
   const int vup = vconv + c->arch.NR * 84;
@@ -264,9 +269,9 @@ void build_sections(cc_ctx* c) {
   int n = 0;
   t.s[n++] = {c->part_arm, c->grid_arm, c->lay.n_arm, c->lay.n_arm, 0,
               (float)((double)c->cfg.lam / (double)c->HW)};
-  t.s[n++] = {c->part_syn, c->grid_syn, n1x1, n1x1, c->lay.n_arm, 1.f};
+  t.s[n++] = {c->part_syn, c->grid_tiles, n1x1, n1x1, c->lay.n_arm, 1.f};
   for (int i = 0; i < a.NR; ++i)
-    t.s[n++] = {c->part_conv + (size_t)i * c->grid_syn * 84, c->grid_syn, 84, 84,
+    t.s[n++] = {c->part_conv + (size_t)i * c->grid_tiles * 84, c->grid_tiles, 84, 84,
                 c->lay.n_arm + n1x1 + 84 * i, 1.f};
   const int vup = c->lay.n_arm + n1x1 + 84 * a.NR;
   for (int l = 1; l < kLevels; ++l)
@@ -305,11 +310,11 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
   CKE(up_forward(a, c->geo, c->yhat, c->up, c->grid_syn, s));
   CKE(mark(3));
   CKE(syn_forward(a, c->geo, c->yhat, c->up, c->x, c->hbuf, c->dhbuf + (size_t)a.NR * 3 * HW,
-                  c->part_d, c->grid_syn, s));
+                  c->part_d, c->part_conv, c->grid_tiles, s));
   CKE(mark(4));
   if (backward) {
     CKE(syn_backward(a, c->geo, c->yhat, c->up, c->hbuf, c->dhbuf, c->dz, c->gsyn, c->part_conv,
-                     c->part_syn, c->grid_syn, s));
+                     c->part_syn, c->grid_tiles, s));
     CKE(mark(5));
     CKE(up_backward(a, c->geo, c->yhat, c->up, c->gsyn, c->part_up, c->grid_syn, s));
     CKE(mark(6));
@@ -323,9 +328,9 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
   } else if (fork) {
     CKE(cudaStreamWaitEvent(s, c->ev_join, 0));
   }
-  CKE(finish_iteration(c->part_d, c->grid_syn, c->part_bits, c->grid_arm,
+  CKE(finish_iteration(c->part_d, c->grid_tiles, c->part_bits, c->grid_arm,
                        1.0 / (3.0 * (double)HW), 1.0 / (double)HW, (double)c->cfg.lam, c->sc,
-                       c->log, advance, s));
+                       c->log, advance, s, backward));
   return mark(7);
 }
 
@@ -585,7 +590,7 @@ int cc_decode(cc_ctx* c, float* rgb_out_hwc) {
                      c->st));
   CK(up_forward(a, c->geo, c->yhat, c->up, c->grid_syn, c->st));
   CK(syn_forward(a, c->geo, c->yhat, c->up, c->x, c->hbuf, c->dhbuf + (size_t)a.NR * 3 * HW,
-                 c->part_d, c->grid_syn, c->st));
+                 c->part_d, c->part_conv, c->grid_tiles, c->st));
   CK(syn_decode(a, c->geo, c->hbuf + (size_t)a.NR * 3 * HW, c->dz, c->st));
   CK(cudaMemcpyAsync(rgb_out_hwc, c->dz, 3 * HW * sizeof(float), cudaMemcpyDefault, c->st));
   CK(cudaStreamSynchronize(c->st));

@@ -29,6 +29,35 @@ struct Geo {
 };
 constexpr int kCtxPad = 4;        // reach of the largest causal context (N = 24)
 
+// Programmatic dependent launch.  Kernels of the upsampling / synthesis / update chain are
+// launched (launch_k) with programmatic stream serialisation, so that the next kernel's
+// blocks are placed while its predecessor drains.  Every kernel calls pdl_wait() before it
+// touches memory: it returns once the kernels it depends on have completed and their
+// writes are visible (at once for a kernel launched without the attribute).  pdl_trigger()
+// lets the successor be placed; it is issued after the wait, so at most one kernel ahead
+// holds blocks that wait.  CC_PDL=0 in the environment turns the attribute off.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+bool pdl_enabled();
+
+template <typename... P, typename... A>
+cudaError_t launch_k(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // Architecture (Table 1 notation) as the kernels see it.
 struct Arch {
   int N;        // ARM context size and width
@@ -96,9 +125,12 @@ cudaError_t up_forward(const Arch& a, const Geo& g, const float* yhat, const UpP
                        int ctas, cudaStream_t st);
 cudaError_t up_backward(const Arch& a, const Geo& g, const float* yhat, const UpPlan& up,
                         float* gsyn, float* part_up, int grid, cudaStream_t st);
+// Synthesis kernels run on 8 x 32 pixel tiles; `grid` CTAs loop over syn_tile_count(g)
+// tiles and write `grid` rows of partial sums (distortion; 84 per 3x3 layer; 11C + 3).
+int syn_tile_count(const Geo& g);
 cudaError_t syn_forward(const Arch& a, const Geo& g, const float* yhat, const UpPlan& up,
-                        const float* x, float* hbuf, float* dxhat, float* part_d, int grid,
-                        cudaStream_t st);
+                        const float* x, float* hbuf, float* dxhat, float* part_d,
+                        float* part_conv, int grid, cudaStream_t st);
 cudaError_t syn_backward(const Arch& a, const Geo& g, const float* yhat, const UpPlan& up,
                          float* hbuf, float* dhbuf, float* dz, float* gsyn,
                          float* part_conv, float* part_syn, int grid, cudaStream_t st);
@@ -122,7 +154,8 @@ cudaError_t latent_update(const Geo& g, const Arch& a, const int2* d_offsets,
                           bool apply, float lr, const IterScalars* sc, cudaStream_t st);
 cudaError_t finish_iteration(const float* part_d, int nd, const float* part_bits, int nb,
                              double d_scale, double r_scale, double lam, IterScalars* sc,
-                             double* log, bool advance, cudaStream_t st);
+                             double* log, bool advance, cudaStream_t st,
+                             bool pdl);
 cudaError_t image_to_planar(const uint8_t* rgb_hwc, float* x, int H, int W, cudaStream_t st);
 
 // Stores a message for cc_last_cuda_error() (thread-local).

@@ -2,6 +2,8 @@
 // as used in Sec. IV-B), plus the deterministic reductions of the per-CTA partial sums.
 #include "cc_internal.cuh"
 
+#include <cstdlib>
+
 namespace cc {
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, Sec. 3.3): ten rounds of
@@ -31,6 +33,8 @@ __global__ void __launch_bounds__(256) k_quantize(Geo g, const float* __restrict
                                                   const float* __restrict__ noise, int mode,
                                                   const IterScalars* sc, int ste_start,
                                                   uint2 key, int iter_override) {
+  pdl_wait();
+  pdl_trigger();
   const int l = blockIdx.y;
   const int n = g.h[l] * g.w[l];
   const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -81,6 +85,8 @@ cudaError_t quantize_launch(const Geo& g, const float* y, float* yhat, float* yh
 // in a fixed tree (8 interleaved sequential sums, then those 8 in order).
 __global__ void __launch_bounds__(256) k_reduce_sections(SectionTable tab, float* part2,
                                                          int n_virtual) {
+  pdl_wait();
+  pdl_trigger();
   const Section s = tab.s[blockIdx.z];
   const int j = blockIdx.x * 32 + threadIdx.x;
   const int slices = gridDim.y, slice = blockIdx.y;
@@ -142,6 +148,8 @@ __global__ void __launch_bounds__(128) k_param_update(VirtualMap vm, const float
                                                       int slices, float* params, float* m,
                                                       float* v, float* grad_out, int apply,
                                                       float lr, IterScalars* sc, int total) {
+  pdl_wait();
+  pdl_trigger();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   __shared__ AdamStep s_st;
   if (threadIdx.x == 0) {
@@ -190,10 +198,9 @@ cudaError_t param_update(const Layout& lay, const Arch& a, const float* part2, i
   vm.per_level = a.per_level;
   vm.vsyn = lay.n_arm; vm.vconv = vm.vsyn + vm.n1x1; vm.vup = vm.vconv + vm.nconv;
   vm.n_virtual = vm.vup + (kLevels - 1) * vm.K2;
-  k_param_update<<<(lay.total + 127) / 128, 128, 0, st>>>(vm, part2, slices, params, m, v,
-                                                          grad_out, apply ? 1 : 0, lr,
-                                                          const_cast<IterScalars*>(sc), lay.total);
-  return cudaGetLastError();
+  return launch_k(k_param_update, dim3((lay.total + 127) / 128), dim3(128), 0, st, vm, part2,
+                  slices, params, m, v, grad_out, apply ? 1 : 0, lr,
+                  const_cast<IterScalars*>(sc), lay.total);
 }
 
 // Gradient of a latent: the synthesis path, plus lambda/(HW) times the rate terms in
@@ -206,6 +213,8 @@ __global__ void __launch_bounds__(256) k_latent_update(Geo g, const int2* __rest
                                                        float rate_scale, float* y, float* m,
                                                        float* v, float* grad_out, int apply,
                                                        float lr, const IterScalars* sc) {
+  pdl_wait();
+  pdl_trigger();
   const int l = blockIdx.y;
   const int w = g.w[l], h = g.h[l];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -243,15 +252,16 @@ cudaError_t latent_update(const Geo& g, const Arch& a, const int2* d_offsets,
   int maxn = 0;
   for (int l = 0; l < kLevels; ++l) maxn = g.h[l] * g.w[l] > maxn ? g.h[l] * g.w[l] : maxn;
   dim3 grid((maxn + 255) / 256, kLevels);
-  k_latent_update<<<grid, 256, 0, st>>>(g, d_offsets, a.N, gsyn, gself, dctx, rate_scale, y,
-                                        m, v, grad_out, apply ? 1 : 0, lr, sc);
-  return cudaGetLastError();
+  return launch_k(k_latent_update, grid, dim3(256), 0, st, g, d_offsets, a.N, gsyn, gself, dctx,
+                  rate_scale, y, m, v, grad_out, apply ? 1 : 0, lr, sc);
 }
 
 __global__ void __launch_bounds__(256) k_finish(const float* part_d, int nd,
                                                 const float* part_bits, int nb, double d_scale,
                                                 double r_scale, double lam, IterScalars* sc,
                                                 double* log, int advance) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sd[256], sb[256];
   double a = 0.0, b = 0.0;
   for (int k = threadIdx.x; k < nd; k += 256) a += (double)part_d[k];
@@ -282,7 +292,10 @@ __global__ void __launch_bounds__(256) k_finish(const float* part_d, int nd,
 
 cudaError_t finish_iteration(const float* part_d, int nd, const float* part_bits, int nb,
                              double d_scale, double r_scale, double lam, IterScalars* sc,
-                             double* log, bool advance, cudaStream_t st) {
+                             double* log, bool advance, cudaStream_t st, bool pdl) {
+  if (pdl)
+    return launch_k(k_finish, dim3(1), dim3(256), 0, st, part_d, nd, part_bits, nb, d_scale,
+                    r_scale, lam, sc, log, advance ? 1 : 0);
   k_finish<<<1, 256, 0, st>>>(part_d, nd, part_bits, nb, d_scale, r_scale, lam, sc, log,
                               advance ? 1 : 0);
   return cudaGetLastError();
@@ -290,6 +303,8 @@ cudaError_t finish_iteration(const float* part_d, int nd, const float* part_bits
 
 __global__ void k_image_to_planar(const uint8_t* __restrict__ rgb, float* __restrict__ x,
                                   int HW) {
+  pdl_wait();
+  pdl_trigger();
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) x[c * HW + p] = (float)rgb[p * 3 + c] / 255.0f;
@@ -301,6 +316,14 @@ cudaError_t image_to_planar(const uint8_t* rgb_hwc, float* x, int H, int W, cuda
   const int blocks = (HW + 255) / 256 < 4096 ? (HW + 255) / 256 : 4096;
   k_image_to_planar<<<blocks, 256, 0, st>>>(rgb_hwc, x, HW);
   return cudaGetLastError();
+}
+
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("CC_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
 }
 
 }  // namespace cc

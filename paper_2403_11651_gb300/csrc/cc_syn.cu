@@ -22,8 +22,8 @@ constexpr int kSyn1x1Base = 2 * k3x3;     // 1x1 layers follow two reserved 3x3 
 constexpr int kSynBank = (kSyn1x1Base + 12 * kMaxC + 4 + 3) & ~3;
 // Constant bank of the synthesis and upsampling kernels, filled by one device-to-device
 // copy of an image built on the device before every pass.  Layout of `syn`:
-// [3x3 layer 0 | 3x3 layer 1 | W_a (C x 7) | b_a (C) | W_b^T (C x 4, 4th column 0) | b_b],
-// W_b transposed so that the three weights of one hidden channel are adjacent.  `synb`
+// [3x3 layer 0 | 3x3 layer 1 | W_a^T (7 x C) | b_a (C) | W_b (3 x C) | b_b], the 1x1
+// weights laid out so that those of hidden channels 2m and 2m + 1 are adjacent.  `synb`
 // is a second copy read by backward passes only: with one copy the compiler keeps every
 // weight used by both a forward and a backward loop in a register between the two uses.
 struct __align__(16) SynBank {
@@ -67,6 +67,8 @@ struct UpFwdArgs {
 // quad needs a (K/2 + 1)^2 input patch and every tap index is a compile-time constant.
 template <int K>
 __global__ void __launch_bounds__(256) k_up_fwd(UpFwdArgs a) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int c = K / 2 - 1;
   constexpr int R = K / 4;          // patch rows t - R .. t + R
   constexpr int P = 2 * R + 1;
@@ -122,17 +124,46 @@ struct UpBwdArgs {
   int fidx[kLevels - 1];
   int lev[kLevels - 1];
   int sh, sw, dh, dw;
+  int tiles_x, tiles;               // input tiles of kUpTY x kUpTX
   float* part;                      // [gridDim.x][kLevels][K*K] of this step
 };
 
-// Adjoint of one step.  Thread per input position i: it gathers every output that read
-// i, directly or through the clamp (virtual positions beyond the border fold onto the
-// edge), giving dL/d in[i] = sum f[u] dout[o] and the filter gradient in[i] * dout[o].
-// Inputs whose 8 x 8 output window lies inside the plane take a branch-free path.
+constexpr int kUpTY = 16, kUpTX = 32;
+
+// Shared-memory tile of one adjoint step.  Positions v of the input, real or virtual
+// (beyond an edge, folding onto it through the clamp), read the outputs 2v - c + u.  A
+// tile of kUpTY x kUpTX real inputs together with R = K/4 virtual positions on each side
+// reads DR output rows; their columns are kept as two parity planes (even / odd offset
+// from the tile's first column) so that lanes with consecutive inputs read consecutive
+// words.  A holds the forward input at the tile's positions (clamped at the virtual ones).
 template <int K>
-__global__ void __launch_bounds__(128) k_up_bwd(UpBwdArgs a) {
-  constexpr int c = K / 2 - 1;
-  constexpr int KK = K * K;
+struct UpBwdShape {
+  static constexpr int c = K / 2 - 1, R = K / 4, H = K / 2;
+  static constexpr int DR = 2 * kUpTY + 4 * R + K - 2;
+  static constexpr int DW = kUpTX + 2 * R + H - 1;
+  static constexpr int DS = DW | 1;
+  static constexpr int AR = kUpTY + 2 * R, AW = kUpTX + 2 * R;
+  static constexpr int AS = AW + 1;
+  static constexpr int G = 2 * K, NW = 256 / G;   // filter-gradient lanes per worker, workers
+};
+
+// Adjoint of one step over tiles of the input plane.
+//  din[i] = sum over positions v folding onto i of sum_u f[u] dout[2v - c + u]
+//  dF[u]  = sum over positions v of in[clamp(v)] dout[2v - c + u]
+// with outputs outside the plane counting as zero.  Each thread computes din at two
+// vertically adjacent inputs (rows of their windows overlap), then, as one of 2K lanes
+// of a row worker, the K/2 filter-gradient taps (uy, px + 2k) along one row of positions,
+// each loaded output feeding K/2 taps through a sliding window.  Filter-gradient
+// partials stay in registers over the CTA's tiles and are summed in a fixed order.
+template <int K>
+__global__ void __launch_bounds__(256, 2) k_up_bwd(UpBwdArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  using S = UpBwdShape<K>;
+  constexpr int c = S::c, R = S::R, H = S::H, KK = K * K;
+  __shared__ float s_d[2][S::DR][S::DS];
+  __shared__ float s_a[S::AR][S::AS];
+  __shared__ float s_red[S::NW][KK];
   const int li = blockIdx.y;
   const float* __restrict__ dout = a.dout[li];
   const float* __restrict__ in = a.in[li];
@@ -141,69 +172,117 @@ __global__ void __launch_bounds__(128) k_up_bwd(UpBwdArgs a) {
   const int fb = a.fidx[li] * KK;
 #pragma unroll
   for (int u = 0; u < KK; ++u) f[u] = c_up[fb + u];
-  float facc[KK];
+  const int tid = threadIdx.x;
+  // input-gradient role: column tx, rows 2 ty and 2 ty + 1 of the tile
+  const int tx = tid & 31, ty = tid >> 5;
+  // filter-gradient role: taps (uy, px + 2k), row worker w
+  const int gi = tid % S::G, w = tid / S::G;
+  const int fuy = gi >> 1, fpx = gi & 1;
+  float acc[H];
 #pragma unroll
-  for (int u = 0; u < KK; ++u) facc[u] = 0.f;
-  const int n = a.sh * a.sw;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const int iy = p / a.sw, ix = p - iy * a.sw;
-    const float xin = __ldg(in + p);
-    // virtual input positions folding onto (iy, ix) through the clamp: just (iy, ix)
-    // inside the plane, up to K/4 more beyond an edge
-    const int vy0 = iy == 0 ? -(K / 4) : iy;
-    const int vy1 = iy == a.sh - 1 ? (a.dh - 1 + c) >> 1 : iy;
-    const int vx0 = ix == 0 ? -(K / 4) : ix;
-    const int vx1 = ix == a.sw - 1 ? (a.dw - 1 + c) >> 1 : ix;
-    float g[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int vy = vy0; vy <= vy1; ++vy) {
-      int roff[K];
-      uint32_t rok = 0;
+  for (int k = 0; k < H; ++k) acc[k] = 0.f;
+  const int vymax = (a.dh - 1 + c) >> 1, vxmax = (a.dw - 1 + c) >> 1;
+  for (int tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) {
+    const int y0 = (tile / a.tiles_x) * kUpTY, x0 = (tile % a.tiles_x) * kUpTX;
+    const int rb = 2 * (y0 - R) - c, cb = 2 * (x0 - R) - c;
+    for (int i = tid; i < S::DR * 2 * S::DW; i += 256) {
+      const int r = i / (2 * S::DW), cc2 = i - r * (2 * S::DW);
+      const int oy = rb + r, ox = cb + cc2;
+      float v = 0.f;
+      if (oy >= 0 && oy < a.dh && ox >= 0 && ox < a.dw) v = __ldg(dout + (size_t)oy * a.dw + ox);
+      s_d[cc2 & 1][r][cc2 >> 1] = v;
+    }
+    for (int i = tid; i < S::AR * S::AW; i += 256) {
+      const int r = i / S::AW, m = i - r * S::AW;
+      const int vy = clampi(y0 - R + r, 0, a.sh - 1), vx = clampi(x0 - R + m, 0, a.sw - 1);
+      s_a[r][m] = __ldg(in + (size_t)vy * a.sw + vx);
+    }
+    __syncthreads();
+    // ---- input gradient at (iy, ix) and (iy + 1, ix)
+    {
+      const int iy = y0 + 2 * ty, ix = x0 + tx;
+      const int r0 = 2 * (2 * ty + R), m0 = tx + R;
+      float g0 = 0.f, g1 = 0.f;
 #pragma unroll
-      for (int uy = 0; uy < K; ++uy) {
-        const int oy = 2 * vy - c + uy;
-        rok |= (oy >= 0 && oy < a.dh ? 1u : 0u) << uy;
-        roff[uy] = clampi(oy, 0, a.dh - 1) * a.dw;
-      }
-      for (int vx = vx0; vx <= vx1; ++vx) {
-        int col[K];
-        uint32_t cok = 0;
+      for (int rr = 0; rr < K + 2; ++rr) {
+        float q[K];
 #pragma unroll
-        for (int ux = 0; ux < K; ++ux) {
-          const int ox = 2 * vx - c + ux;
-          cok |= (ox >= 0 && ox < a.dw ? 1u : 0u) << ux;
-          col[ux] = clampi(ox, 0, a.dw - 1);
+        for (int ux = 0; ux < K; ++ux) q[ux] = s_d[ux & 1][r0 + rr][m0 + (ux >> 1)];
+        if (rr < K) {
+#pragma unroll
+          for (int ux = 0; ux < K; ++ux) g0 = fmaf(f[rr * K + ux], q[ux], g0);
         }
-        // every read is inside the plane; reads of outputs beyond it count as zero
+        if (rr >= 2) {
 #pragma unroll
-        for (int uy = 0; uy < K; ++uy) {
-          const float* row = dout + roff[uy];
-          const bool ry = (rok >> uy) & 1u;
+          for (int ux = 0; ux < K; ++ux) g1 = fmaf(f[(rr - 2) * K + ux], q[ux], g1);
+        }
+      }
+      // virtual positions beyond an edge fold onto the border inputs
+      if (ix < a.sw) {
 #pragma unroll
-          for (int ux = 0; ux < K; ++ux) {
-            float gv = __ldg(row + col[ux]);
-            gv = (ry && ((cok >> ux) & 1u)) ? gv : 0.f;
-            g[ux & 3] = fmaf(f[uy * K + ux], gv, g[ux & 3]);
-            facc[uy * K + ux] = fmaf(xin, gv, facc[uy * K + ux]);
+        for (int e = 0; e < 2; ++e) {
+          const int py = iy + e;
+          if (py >= a.sh) break;
+          const int vy0 = py == 0 ? -R : py, vy1 = py == a.sh - 1 ? vymax : py;
+          const int vx0 = ix == 0 ? -R : ix, vx1 = ix == a.sw - 1 ? vxmax : ix;
+          float g = e ? g1 : g0;
+          if (vy0 != vy1 || vx0 != vx1) {
+            for (int vy = vy0; vy <= vy1; ++vy)
+              for (int vx = vx0; vx <= vx1; ++vx) {
+                if (vy == py && vx == ix) continue;
+                const int rr0 = 2 * (vy - y0 + R), mm0 = vx - x0 + R;
+#pragma unroll
+                for (int uy = 0; uy < K; ++uy)
+#pragma unroll
+                  for (int ux = 0; ux < K; ++ux)
+                    g = fmaf(f[uy * K + ux], s_d[ux & 1][rr0 + uy][mm0 + (ux >> 1)], g);
+              }
           }
+          din[(size_t)py * a.sw + ix] = g;
         }
       }
     }
-    din[p] = (g[0] + g[1]) + (g[2] + g[3]);
-  }
-  // per-CTA filter gradient: warp sums, then warps in order
-  __shared__ float s_w[4][KK];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // ---- filter gradient over the positions this tile owns
+    {
+      const int ry0 = y0 == 0 ? -R : y0;
+      const int ry1 = y0 + kUpTY >= a.sh ? vymax : y0 + kUpTY - 1;
+      const int cx0 = x0 == 0 ? -R : x0;
+      const int cx1 = x0 + kUpTX >= a.sw ? vxmax : x0 + kUpTX - 1;
+      const int m_lo = cx0 - x0 + R, m_hi = cx1 - x0 + R;   // inclusive, in [0, AW)
+      for (int vy = ry0 + w; vy <= ry1; vy += S::NW) {
+        const float* drow = &s_d[fpx][2 * (vy - y0 + R) + fuy][0];
+        const float* arow = &s_a[vy - y0 + R][0];
+        float q[H];
 #pragma unroll
-  for (int u = 0; u < KK; ++u) {
-    float v = facc[u];
+        for (int k = 0; k < H - 1; ++k) q[k] = drow[m_lo + k];
+        int m = m_lo;
+        for (; m + H - 1 <= m_hi; m += H) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) s_w[wid][u] = v;
+          for (int s = 0; s < H; ++s) {
+            // window q[(s + k) % H] holds drow[m + s + k]
+            q[(s + H - 1) % H] = drow[m + s + H - 1];
+            const float av = arow[m + s];
+#pragma unroll
+            for (int k = 0; k < H; ++k) acc[k] = fmaf(av, q[(s + k) % H], acc[k]);
+          }
+        }
+        for (; m <= m_hi; ++m) {
+          const float av = arow[m];
+#pragma unroll
+          for (int k = 0; k < H; ++k) acc[k] = fmaf(av, drow[m + k], acc[k]);
+        }
+      }
+    }
+    __syncthreads();
   }
+  // per-CTA filter gradient: row workers summed in order
+#pragma unroll
+  for (int k = 0; k < H; ++k) s_red[w][fuy * K + fpx + 2 * k] = acc[k];
   __syncthreads();
-  for (int u = threadIdx.x; u < KK; u += blockDim.x) {
+  for (int u = tid; u < KK; u += 256) {
     float t = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_w[w][u];
+#pragma unroll
+    for (int r = 0; r < S::NW; ++r) t += s_red[r][u];
     a.part[((long long)blockIdx.x * kLevels + a.lev[li]) * KK + u] = t;
   }
 }
@@ -224,8 +303,7 @@ static cudaError_t up_forward_k(const Arch& ar, const Geo& g, const float* yhat,
     // once for several quads
     const int tot = ((a.dh + 1) / 2) * ((a.dw + 1) / 2);
     const int need = (tot + 255) / 256, cap = (3 * ctas) / n > 1 ? (3 * ctas) / n : 1;
-    k_up_fwd<K><<<dim3(need < cap ? need : cap, n), 256, 0, st>>>(a);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_k(k_up_fwd<K>, dim3(need < cap ? need : cap, n), dim3(256), 0, st, a);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -253,14 +331,15 @@ static cudaError_t up_backward_k(const Arch& ar, const Geo& g, const float* yhat
       a.lev[n] = l;
     }
     a.sh = g.h[j + 1]; a.sw = g.w[j + 1]; a.dh = g.h[j]; a.dw = g.w[j];
-    // rows [j * grid, j * grid + grid) belong to this step; only as many CTAs as there is
-    // work for are launched, the rows of the others stay zero from the context set-up
+    // rows [j * grid, j * grid + grid) belong to this step
     a.part = part_up + (long long)j * grid * kLevels * K * K;
-    // 128-thread CTAs, about two resident per SM in total (grid = 2 x SMs): each thread
-    // loads its filter once and handles many inputs before the per-CTA reduction
-    const int need = (a.sh * a.sw + 127) / 128, cap = grid / n > 1 ? grid / n : 1;
-    k_up_bwd<K><<<dim3(need < cap ? need : cap, n), 128, 0, st>>>(a);
-    cudaError_t e = cudaGetLastError();
+    // one CTA per input tile and level, at most `grid` per level (a CTA then loops over
+    // several tiles); the part rows of CTAs that are not launched stay zero from the
+    // context set-up
+    a.tiles_x = (a.sw + kUpTX - 1) / kUpTX;
+    a.tiles = a.tiles_x * ((a.sh + kUpTY - 1) / kUpTY);
+    const int nb = a.tiles < grid ? a.tiles : grid;
+    cudaError_t e = launch_k(k_up_bwd<K>, dim3(nb, n), dim3(256), 0, st, a);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -273,223 +352,58 @@ cudaError_t up_backward(const Arch& a, const Geo& g, const float* yhat, const Up
   return cudaErrorInvalidValue;
 }
 
-// ------------------------------------------------------------------ synthesis 1x1 layers
-
-struct Syn1x1Args {
-  const float* feat[kLevels];   // level-0 latents, then the upsampled planes of l = 1..6
-  const float* dh2;             // [3][HW] gradient of the C-3 layer output
-  float* h2;                    // [3][HW]
-  float* dfeat[kLevels];        // gradient of each feature plane
-  float* part;                  // [gridDim.x][11C + 3]
-  int HW;
-};
-
-template <int C>
-__global__ void __launch_bounds__(256) k_syn1x1_fwd(Syn1x1Args a) {
-  constexpr int WA = kSyn1x1Base, BA = WA + 7 * C, WB = BA + C, BB = WB + 4 * C;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.HW; p += gridDim.x * blockDim.x) {
-    float f[kLevels];
-#pragma unroll
-    for (int k = 0; k < kLevels; ++k) f[k] = __ldg(a.feat[k] + p);
-    float z2[3] = {c_syn[BB], c_syn[BB + 1], c_syn[BB + 2]};
-#pragma unroll
-    for (int o = 0; o < C; ++o) {
-      float z = c_syn[BA + o];
-#pragma unroll
-      for (int k = 0; k < kLevels; ++k) z = fmaf(c_syn[WA + o * kLevels + k], f[k], z);
-      const float h1 = fmaxf(z, 0.f);
-#pragma unroll
-      for (int j = 0; j < 3; ++j) z2[j] = fmaf(c_syn[WB + o * 4 + j], h1, z2[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < 3; ++j) a.h2[j * a.HW + p] = fmaxf(z2[j], 0.f);
-  }
-}
-
-template <int C>
-struct Syn1x1Shape {
-  static constexpr int T = kPixTile;
-  static constexpr int SZ = C + 4;   // stride of dz1 and [h1, 1] rows
-  static constexpr int SF = 12;      // stride of [f, 1] rows
-  static constexpr int SD = 4;       // stride of [dz2, 0] rows
-  static constexpr int NUA = C / 4;          // 4x8 blocks of [dW_a | db_a]
-  static constexpr int NUB = (C + 4) / 4;    // 4x4 blocks of [dW_b | db_b] (row 3 unused)
-  static constexpr int NU = NUA + NUB;
-  static constexpr int G = T / NU;
-  static constexpr int NP = 11 * C + 3;
-  static constexpr int tile_floats = T * (2 * SZ + SF + SD);
-  static constexpr int smem_floats = tile_floats > G * NP ? tile_floats : G * NP;
-};
-
-template <int C>
-__global__ void __launch_bounds__(256, 2) k_syn1x1_bwd(Syn1x1Args a) {
-  using Sh = Syn1x1Shape<C>;
-  constexpr int T = Sh::T, SZ = Sh::SZ, SF = Sh::SF, SD = Sh::SD;
-  constexpr int NUA = Sh::NUA, NU = Sh::NU, G = Sh::G, NP = Sh::NP;
-  constexpr int WA = kSyn1x1Base, BA = WA + 7 * C, WB = BA + C, BB = WB + 4 * C;
-  extern __shared__ float4 smem4[];
-  float* sm = reinterpret_cast<float*>(smem4);
-  float* s_dz1 = sm;               // [T][SZ]
-  float* s_h1 = s_dz1 + T * SZ;    // [T][SZ]  (h1, 1, 0, 0, 0)
-  float* s_f = s_h1 + T * SZ;      // [T][SF]  (f0..f6, 1, 0...)
-  float* s_dz2 = s_f + T * SF;     // [T][SD]  (dz2, 0)
-
-  const int tid = threadIdx.x;
-  const bool worker = tid < G * NU;
-  const int unit = tid % NU, grp = tid / NU;
-  float acc[4][8];
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int k = 0; k < 8; ++k) acc[r][k] = 0.f;
-
-  const int n_tiles = (a.HW + T - 1) / T;
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int p = tile * T + tid;
-    const bool valid = p < a.HW;
-    float f[kLevels];
-#pragma unroll
-    for (int k = 0; k < kLevels; ++k) f[k] = valid ? __ldg(a.feat[k] + p) : 0.f;
-    float dh2[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) dh2[j] = valid ? __ldg(a.dh2 + j * a.HW + p) : 0.f;
-    // recompute z1, h1, z2
-    float z2[3] = {c_syn[BB], c_syn[BB + 1], c_syn[BB + 2]};
-    float h1[C];
-#pragma unroll
-    for (int o = 0; o < C; ++o) {
-      float z = c_syn[BA + o];
-#pragma unroll
-      for (int k = 0; k < kLevels; ++k) z = fmaf(c_syn[WA + o * kLevels + k], f[k], z);
-      h1[o] = fmaxf(z, 0.f);
-#pragma unroll
-      for (int j = 0; j < 3; ++j) z2[j] = fmaf(c_syn[WB + o * 4 + j], h1[o], z2[j]);
-    }
-    float* hrow = s_h1 + tid * SZ;
-#pragma unroll
-    for (int o = 0; o < C; o += 4)
-      *reinterpret_cast<float4*>(hrow + o) = valid ? make_float4(h1[o], h1[o + 1], h1[o + 2], h1[o + 3])
-                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
-    *reinterpret_cast<float4*>(hrow + C) = make_float4(valid ? 1.f : 0.f, 0.f, 0.f, 0.f);
-    float dz2[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) dz2[j] = z2[j] > 0.f ? dh2[j] : 0.f;
-    *reinterpret_cast<float4*>(s_dz2 + tid * SD) = make_float4(dz2[0], dz2[1], dz2[2], 0.f);
-    float df[kLevels];
-#pragma unroll
-    for (int k = 0; k < kLevels; ++k) df[k] = 0.f;
-#pragma unroll
-    for (int o = 0; o < C; ++o) {
-      float dh1 = 0.f;
-#pragma unroll
-      for (int j = 0; j < 3; ++j) dh1 = fmaf(c_synb[WB + o * 4 + j], dz2[j], dh1);
-      h1[o] = h1[o] > 0.f ? dh1 : 0.f;    // now dz1 (relu'(z1) = [h1 > 0])
-#pragma unroll
-      for (int k = 0; k < kLevels; ++k) df[k] = fmaf(c_synb[WA + o * kLevels + k], h1[o], df[k]);
-    }
-    float* zrow = s_dz1 + tid * SZ;
-#pragma unroll
-    for (int o = 0; o < C; o += 4)
-      *reinterpret_cast<float4*>(zrow + o) = make_float4(h1[o], h1[o + 1], h1[o + 2], h1[o + 3]);
-    float* frow = s_f + tid * SF;
-#pragma unroll
-    for (int k = 0; k < kLevels; ++k) frow[k] = f[k];
-    frow[7] = valid ? 1.f : 0.f;
-    if (valid) {
-#pragma unroll
-      for (int k = 0; k < kLevels; ++k) a.dfeat[k][p] = df[k];
-    }
-    __syncthreads();
-    if (worker) {
-      if (unit < NUA) {   // rows c = 4 unit .. +3 of [dW_a | db_a]
-        const int c0 = unit * 4;
-        for (int q = grp; q < T; q += G) {
-          const float4 dz = *reinterpret_cast<const float4*>(s_dz1 + q * SZ + c0);
-          const float4 f0 = *reinterpret_cast<const float4*>(s_f + q * SF);
-          const float4 f1 = *reinterpret_cast<const float4*>(s_f + q * SF + 4);
-          const float dv[4] = {dz.x, dz.y, dz.z, dz.w};
-          const float fv[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
-#pragma unroll
-          for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int k = 0; k < 8; ++k) acc[r][k] = fmaf(dv[r], fv[k], acc[r][k]);
-        }
-      } else {            // cols 4 (unit - NUA) .. +3 of [dW_b | db_b]
-        const int h0 = (unit - NUA) * 4;
-        for (int q = grp; q < T; q += G) {
-          const float4 dz = *reinterpret_cast<const float4*>(s_dz2 + q * SD);
-          const float4 hv = *reinterpret_cast<const float4*>(s_h1 + q * SZ + h0);
-          const float dv[4] = {dz.x, dz.y, dz.z, dz.w};
-          const float hh[4] = {hv.x, hv.y, hv.z, hv.w};
-#pragma unroll
-          for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc[r][k] = fmaf(dv[r], hh[k], acc[r][k]);
-        }
-      }
-    }
-    __syncthreads();
-  }
-  // partial layout: W_a (C x 7), b_a (C), W_b (3 x C), b_b (3)
-  float* red = sm;
-  if (worker) {
-    float* mine = red + grp * NP;
-    if (unit < NUA) {
-      const int c0 = unit * 4;
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-#pragma unroll
-        for (int k = 0; k < 7; ++k) mine[(c0 + r) * 7 + k] = acc[r][k];
-        mine[7 * C + c0 + r] = acc[r][7];
-      }
-    } else {
-      const int h0 = (unit - NUA) * 4;
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int col = h0 + k;
-          if (col < C) mine[8 * C + r * C + col] = acc[r][k];
-          else if (col == C) mine[11 * C + r] = acc[r][k];
-        }
-    }
-  }
-  __syncthreads();
-  for (int j = tid; j < NP; j += T) {
-    float t = 0.f;
-    for (int g = 0; g < G; ++g) t += red[g * NP + j];
-    a.part[(long long)blockIdx.x * NP + j] = t;
-  }
-}
-
 // ------------------------------------------------------------------ 3x3 residual layers
+//
+// The synthesis kernels work on tiles of kSTY x kSTX pixels, one pixel per thread, with
+// a one-pixel halo of the 3-channel planes they gather staged in shared memory (rows of
+// kSHX floats, channels kSHS floats apart: the 27 taps of one pixel fall in distinct
+// banks).  Loads are replicate-clamped at the image border, which is the padding of the
+// forward convolution.  With NR layers (ReLU on all but the last, which is linear):
+//   forward : 1x1 stack -> h_0; layers 0 .. NR-2 (k_conv3_fwd); layer NR-1 with the
+//             distortion, dL/dx_hat and the layer's weight gradient (k_conv3_last), since
+//             the pre-activation gradient of a linear layer is its output gradient;
+//   backward: (NR = 2) layer 1's input gradient, layer 0's pre-activation gradient and
+//             weight gradient (k_conv3_mid); layer 0's input gradient inside the 1x1
+//             backward (k_syn1x1_bwd).
+// Per-CTA partial sums of weight gradients and distortion are written in a fixed order.
 
-struct ConvArgs {
-  const float* hin;    // [3][HW] layer input
-  float* hout;         // [3][HW] layer output (forward)
-  const float* dhout;  // [3][HW] gradient of the layer output (backward)
-  float* dz;           // [3][HW] gradient of the pre-activation
-  float* dhin;         // [3][HW] gradient of the layer input
-  const float* x;      // [3][HW] image (last layer)
-  float* part;         // per-CTA partials
-  float dscale;        // 2 / (3 H W)
-  int H, W;
+constexpr int kSTY = 8, kSTX = 32;            // synthesis tile, kSTY * kSTX = 256 threads
+constexpr int kSHX = 35;                       // halo row stride (kSTX + 2 used)
+constexpr int kSHS = 361;                      // halo channel stride ((kSTY + 2) rows used)
+constexpr int kSHR = kSTY + 2;
+
+struct SynTileGeo {
+  int H, W, ntx, n_tiles;
 };
 
-__device__ __forceinline__ void gather3x3(float (&v)[27], const float* h, int y, int x, int H,
-                                          int W) {
+__device__ __forceinline__ void tile_xy(const SynTileGeo& t, int tile, int& y0, int& x0) {
+  const int ty = tile / t.ntx;
+  y0 = ty * kSTY;
+  x0 = (tile - ty * t.ntx) * kSTX;
+}
+
+// s[ci * kSHS + r * kSHX + c] = h[ci][clamp(y0 - 1 + r)][clamp(x0 - 1 + c)]
+__device__ __forceinline__ void load_halo3(float* s, const float* __restrict__ h, int y0, int x0,
+                                           int H, int W) {
   const int HW = H * W;
-#pragma unroll
-  for (int dy = -1; dy <= 1; ++dy) {
-    const int yy = clampi(y + dy, 0, H - 1);
-#pragma unroll
-    for (int dx = -1; dx <= 1; ++dx) {
-      const int xx = clampi(x + dx, 0, W - 1);
-#pragma unroll
-      for (int ci = 0; ci < 3; ++ci)
-        v[ci * 9 + (dy + 1) * 3 + (dx + 1)] = __ldg(h + ci * HW + yy * W + xx);
-    }
+  constexpr int n = kSHR * (kSTX + 2);
+  for (int i = threadIdx.x; i < 3 * n; i += kSTY * kSTX) {
+    const int ci = i / n, rc = i - ci * n;
+    const int r = rc / (kSTX + 2), c = rc - r * (kSTX + 2);
+    const int gy = clampi(y0 - 1 + r, 0, H - 1), gx = clampi(x0 - 1 + c, 0, W - 1);
+    s[ci * kSHS + r * kSHX + c] = __ldg(h + ci * HW + gy * W + gx);
   }
+}
+
+// the 27 inputs of pixel (ty, tx) of the tile: v[ci * 9 + (dy + 1) * 3 + dx + 1]
+__device__ __forceinline__ void gather_halo(float (&v)[27], const float* s, int ty, int tx) {
+#pragma unroll
+  for (int ci = 0; ci < 3; ++ci)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx)
+        v[ci * 9 + dy * 3 + dx] = s[ci * kSHS + (ty + dy) * kSHX + tx + dx];
 }
 
 template <int I>
@@ -504,130 +418,479 @@ __device__ __forceinline__ void conv_z(float (&z)[3], const float (&v)[27]) {
   }
 }
 
-template <int I, bool LAST>
-__global__ void __launch_bounds__(256) k_conv_fwd(ConvArgs a) {
-  const int HW = a.H * a.W;
-  float dsum = 0.f;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x) {
-    const int y = p / a.W, x = p - y * a.W;
-    float v[27];
-    gather3x3(v, a.hin, y, x, a.H, a.W);
-    float z[3];
-    conv_z<I>(z, v);
-#pragma unroll
-    for (int o = 0; o < 3; ++o) {
-      const float out = v[o * 9 + 4] + (LAST ? z[o] : fmaxf(z[o], 0.f));
-      a.hout[o * HW + p] = out;
-      if (LAST) {
-        const float d = out - __ldg(a.x + o * HW + p);
-        dsum = fmaf(d, d, dsum);
-        a.dz[o * HW + p] = d * a.dscale;   // dL/dx_hat, stored as the gradient buffer
-      }
-    }
-  }
-  if (LAST) {
-    __shared__ float s_tmp[8];
-    const float t = block_sum<256>(dsum, s_tmp);
-    if (threadIdx.x == 0) a.part[blockIdx.x] = t;
-  }
-}
-
-// dz = dL/dh_out * act'(z) and the layer's weight / bias gradient partials.
-template <int I, bool LAST>
-__global__ void __launch_bounds__(256) k_conv_dz(ConvArgs a) {
-  const int HW = a.H * a.W;
-  float acc[84];
-#pragma unroll
-  for (int k = 0; k < 84; ++k) acc[k] = 0.f;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x) {
-    const int y = p / a.W, x = p - y * a.W;
-    float v[27];
-    gather3x3(v, a.hin, y, x, a.H, a.W);
-    float z[3];
-    if (!LAST) conv_z<I>(z, v);
-#pragma unroll
-    for (int o = 0; o < 3; ++o) {
-      const float g = __ldg(a.dhout + o * HW + p);
-      const float d = (LAST || z[o] > 0.f) ? g : 0.f;
-      a.dz[o * HW + p] = d;
-#pragma unroll
-      for (int k = 0; k < 27; ++k) acc[o * 27 + k] = fmaf(d, v[k], acc[o * 27 + k]);
-      acc[81 + o] += d;
-    }
-  }
-  __shared__ float s_w[8][84];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < 84; ++k) {
-    float v = acc[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) s_w[wid][k] = v;
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < 84; k += blockDim.x) {
-    float t = 0.f;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) t += s_w[w][k];
-    a.part[(long long)blockIdx.x * 84 + k] = t;
-  }
-}
-
-// dL/dh_in = dL/dh_out + conv^T(dz): gathers, for each input pixel q, every (p, tap)
-// whose replicate-clamped read landed on q.
+// Adjoint of layer I at pixel (y, x) = tile (ty, tx): sum over the outputs p and taps whose
+// replicate-clamped read landed on (y, x) of W[o][ci][tap] dz[o][p].  s_dz holds dz over
+// the tile and its halo; inside the image only p = (y, x) - tap qualify.
 template <int I>
-__global__ void __launch_bounds__(256) k_conv_dx(ConvArgs a) {
+__device__ __forceinline__ void conv_adjoint(float (&acc)[3], const float* s_dz, int ty, int tx,
+                                             int y, int x, int y0, int x0, int H, int W) {
   constexpr int Wo = I * k3x3;
-  const int HW = a.H * a.W;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < HW; q += gridDim.x * blockDim.x) {
-    const int qy = q / a.W, qx = q - qy * a.W;
-    float acc[3];
+  if (y > 0 && x > 0 && y < H - 1 && x < W - 1) {
 #pragma unroll
-    for (int ci = 0; ci < 3; ++ci) acc[ci] = __ldg(a.dhout + ci * HW + q);
-    if (qy > 0 && qx > 0 && qy < a.H - 1 && qx < a.W - 1) {
-      // interior: output p = q - (dy, dx) read q through tap (dy, dx), no clamping
-      float d[27];
+    for (int ci = 0; ci < 3; ++ci)
 #pragma unroll
       for (int o = 0; o < 3; ++o)
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
           for (int dx = -1; dx <= 1; ++dx)
-            d[o * 9 + (dy + 1) * 3 + (dx + 1)] = __ldg(a.dz + o * HW + q - dy * a.W - dx);
-      // input channel outer: the nine taps of one (o, ci) pair are adjacent in the bank
+            acc[ci] = fmaf(c_synb[Wo + o * 27 + ci * 9 + (dy + 1) * 3 + (dx + 1)],
+                           s_dz[o * kSHS + (ty + 1 - dy) * kSHX + tx + 1 - dx], acc[ci]);
+    return;
+  }
+  for (int dy = -1; dy <= 1; ++dy)
+    for (int py = y - dy - 1; py <= y - dy + 1; ++py) {
+      if (py < 0 || py >= H || clampi(py + dy, 0, H - 1) != y) continue;
+      for (int dx = -1; dx <= 1; ++dx)
+        for (int px = x - dx - 1; px <= x - dx + 1; ++px) {
+          if (px < 0 || px >= W || clampi(px + dx, 0, W - 1) != x) continue;
+          const float* d = s_dz + (py - y0 + 1) * kSHX + (px - x0 + 1);
 #pragma unroll
-      for (int ci = 0; ci < 3; ++ci)
+          for (int o = 0; o < 3; ++o)
 #pragma unroll
-        for (int o = 0; o < 3; ++o)
-#pragma unroll
-          for (int t = 0; t < 9; ++t)
-            acc[ci] = fmaf(c_syn[Wo + o * 27 + ci * 9 + t], d[o * 9 + t], acc[ci]);
-#pragma unroll
-      for (int ci = 0; ci < 3; ++ci) a.dhin[ci * HW + q] = acc[ci];
-      continue;
-    }
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy) {
-      for (int py = qy - dy - 1; py <= qy - dy + 1; ++py) {
-        if (py < 0 || py >= a.H || clampi(py + dy, 0, a.H - 1) != qy) continue;
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          for (int px = qx - dx - 1; px <= qx - dx + 1; ++px) {
-            if (px < 0 || px >= a.W || clampi(px + dx, 0, a.W - 1) != qx) continue;
-            const int pp = py * a.W + px;
-#pragma unroll
-            for (int o = 0; o < 3; ++o) {
-              const float d = __ldg(a.dz + o * HW + pp);
-#pragma unroll
-              for (int ci = 0; ci < 3; ++ci)
-                acc[ci] = fmaf(c_syn[Wo + o * 27 + ci * 9 + (dy + 1) * 3 + (dx + 1)], d, acc[ci]);
-            }
-          }
+            for (int ci = 0; ci < 3; ++ci)
+              acc[ci] = fmaf(c_synb[Wo + o * 27 + ci * 9 + (dy + 1) * 3 + (dx + 1)],
+                             d[o * kSHS], acc[ci]);
         }
+    }
+}
+
+// Weight-gradient partial of one 3x3 layer over a tile.  Thread t < 255 owns input
+// channel ci = t / 85 and the pixels q = t % 85 + 85 j of the tile; it adds the 27 products
+// dz[o][q] h[ci][q + tap] (o < 3, 9 taps) and the bias terms dz[o][q] into registers that
+// persist over the CTA's tiles.  s_dz: [3][256], s_h: the layer input's halo tile.
+constexpr int kWG = 85;                        // pixel groups per channel
+__device__ __forceinline__ void conv_wgrad(float (&acc)[30], const float* s_dz, const float* s_h) {
+  const int t = threadIdx.x;
+  if (t >= 3 * kWG) return;
+  const int ci = t / kWG;
+  for (int q = t - ci * kWG; q < 256; q += kWG) {
+    const float* hh = s_h + ci * kSHS + (q >> 5) * kSHX + (q & 31);
+    float hv[9];
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) hv[dy * 3 + dx] = hh[dy * kSHX + dx];
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+      const float d = s_dz[o * 256 + q];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) acc[o * 9 + k] = fmaf(d, hv[k], acc[o * 9 + k]);
+      acc[27 + o] += d;
+    }
+  }
+}
+
+// Per-CTA sum of conv_wgrad's registers in a fixed order: s_red holds kWG x 84 floats
+// (it may alias the tiles, which are dead by then).
+__device__ __forceinline__ void conv_wgrad_store(const float (&acc)[30], float* s_red, float* part) {
+  const int t = threadIdx.x;
+  __syncthreads();
+  if (t < 3 * kWG) {
+    const int ci = t / kWG, g = t - ci * kWG;
+    float* row = s_red + g * 84;
+#pragma unroll
+    for (int o = 0; o < 3; ++o)
+#pragma unroll
+      for (int k = 0; k < 9; ++k) row[o * 27 + ci * 9 + k] = acc[o * 9 + k];
+    if (ci == 0) {
+#pragma unroll
+      for (int o = 0; o < 3; ++o) row[81 + o] = acc[27 + o];
+    }
+  }
+  __syncthreads();
+  if (t < 84) {
+    float sum = 0.f;
+    for (int g = 0; g < kWG; ++g) sum += s_red[g * 84 + t];
+    part[(long long)blockIdx.x * 84 + t] = sum;
+  }
+}
+
+struct ConvArgs {
+  SynTileGeo t;
+  const float* hin;    // [3][HW] layer input
+  float* hout;         // [3][HW] layer output
+  const float* x;      // [3][HW] image (last layer)
+  float* dxhat;        // [3][HW] dL/dx_hat (last layer)
+  const float* g;      // [3][HW] output gradient of layer 1 (= its pre-activation gradient)
+  float* dh;           // [3][HW] gradient of layer 1's input
+  float* dz;           // [3][HW] pre-activation gradient of layer 0
+  float* part;         // per-CTA partials (84 per CTA)
+  float* part_d;       // per-CTA distortion partials (last layer)
+  float dscale;        // 2 / (3 H W)
+};
+
+// Layer I (not the last): h_out = h_in + ReLU(conv(h_in) + b).
+template <int I>
+__global__ void __launch_bounds__(256) k_conv3_fwd(ConvArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ float s_h[3 * kSHS];
+  const int HW = a.t.H * a.t.W;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int tile = blockIdx.x; tile < a.t.n_tiles; tile += gridDim.x) {
+    int y0, x0;
+    tile_xy(a.t, tile, y0, x0);
+    load_halo3(s_h, a.hin, y0, x0, a.t.H, a.t.W);
+    __syncthreads();
+    const int y = y0 + ty, x = x0 + tx;
+    if (y < a.t.H && x < a.t.W) {
+      float v[27], z[3];
+      gather_halo(v, s_h, ty, tx);
+      conv_z<I>(z, v);
+#pragma unroll
+      for (int o = 0; o < 3; ++o) a.hout[o * HW + y * a.t.W + x] = v[o * 9 + 4] + fmaxf(z[o], 0.f);
+    }
+    __syncthreads();
+  }
+}
+
+// Last layer I (linear): x_hat = h_in + conv(h_in) + b, the distortion partial sum of
+// (x_hat - x)^2, dL/dx_hat = 2 (x_hat - x) / (3HW), and the layer's weight gradient.
+template <int I>
+__global__ void __launch_bounds__(256) k_conv3_last(ConvArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ float s_all[kWG * 84];   // halo tile + dz, then the reduction
+  __shared__ float s_tmp[8];
+  float* s_h = s_all;
+  float* s_dz = s_all + 3 * kSHS;
+  const int HW = a.t.H * a.t.W;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float dsum = 0.f;
+  float wacc[30];
+#pragma unroll
+  for (int k = 0; k < 30; ++k) wacc[k] = 0.f;
+  for (int tile = blockIdx.x; tile < a.t.n_tiles; tile += gridDim.x) {
+    int y0, x0;
+    tile_xy(a.t, tile, y0, x0);
+    load_halo3(s_h, a.hin, y0, x0, a.t.H, a.t.W);
+    __syncthreads();
+    const int y = y0 + ty, x = x0 + tx;
+    const bool valid = y < a.t.H && x < a.t.W;
+    float v[27], z[3];
+    gather_halo(v, s_h, ty, tx);
+    conv_z<I>(z, v);
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+      float g = 0.f;
+      if (valid) {
+        const int p = o * HW + y * a.t.W + x;
+        const float out = v[o * 9 + 4] + z[o];
+        a.hout[p] = out;
+        const float d = out - __ldg(a.x + p);
+        dsum = fmaf(d, d, dsum);
+        g = d * a.dscale;
+        a.dxhat[p] = g;
+      }
+      s_dz[o * 256 + threadIdx.x] = g;
+    }
+    __syncthreads();
+    conv_wgrad(wacc, s_dz, s_h);
+    __syncthreads();
+  }
+  const float t = block_sum<256>(dsum, s_tmp);
+  if (threadIdx.x == 0) a.part_d[blockIdx.x] = t;
+  conv_wgrad_store(wacc, s_all, a.part);
+}
+
+// NR = 2: gradient of layer 1's input, dh = g + conv_1^T(g) (layer 1 is linear, so g is
+// also its pre-activation gradient); layer 0's pre-activation gradient dz = [z_0 > 0] dh
+// with z_0 recomputed from h_0; layer 0's weight gradient.
+__global__ void __launch_bounds__(256) k_conv3_mid(ConvArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ float s_all[kWG * 84];   // two halo tiles + dz, then the reduction
+  float* s_g = s_all;
+  float* s_h = s_all + 3 * kSHS;
+  float* s_dz = s_all + 6 * kSHS;
+  const int HW = a.t.H * a.t.W;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float wacc[30];
+#pragma unroll
+  for (int k = 0; k < 30; ++k) wacc[k] = 0.f;
+  for (int tile = blockIdx.x; tile < a.t.n_tiles; tile += gridDim.x) {
+    int y0, x0;
+    tile_xy(a.t, tile, y0, x0);
+    load_halo3(s_g, a.g, y0, x0, a.t.H, a.t.W);
+    load_halo3(s_h, a.hin, y0, x0, a.t.H, a.t.W);
+    __syncthreads();
+    const int y = y0 + ty, x = x0 + tx;
+    const bool valid = y < a.t.H && x < a.t.W;
+    float dz[3] = {0.f, 0.f, 0.f};
+    if (valid) {
+      float dh[3];
+#pragma unroll
+      for (int ci = 0; ci < 3; ++ci) dh[ci] = s_g[ci * kSHS + (ty + 1) * kSHX + tx + 1];
+      conv_adjoint<1>(dh, s_g, ty, tx, y, x, y0, x0, a.t.H, a.t.W);
+      float v[27], z[3];
+      gather_halo(v, s_h, ty, tx);
+      conv_z<0>(z, v);
+#pragma unroll
+      for (int o = 0; o < 3; ++o) {
+        const int p = o * HW + y * a.t.W + x;
+        dz[o] = z[o] > 0.f ? dh[o] : 0.f;
+        a.dh[p] = dh[o];
+        a.dz[p] = dz[o];
       }
     }
 #pragma unroll
-    for (int ci = 0; ci < 3; ++ci) a.dhin[ci * HW + q] = acc[ci];
+    for (int o = 0; o < 3; ++o) s_dz[o * 256 + threadIdx.x] = dz[o];
+    __syncthreads();
+    conv_wgrad(wacc, s_dz, s_h);
+    __syncthreads();
+  }
+  conv_wgrad_store(wacc, s_all, a.part);
+}
+
+// ------------------------------------------------------------------ synthesis 1x1 layers
+
+struct Syn1x1Args {
+  const float* feat[kLevels];   // level-0 latents, then the upsampled planes of l = 1..6
+  float* h2;                    // [3][HW] output of the C-3 layer (forward)
+  const float* dhout;           // [3][HW] output gradient of 3x3 layer 0 (backward)
+  const float* dz0;             // [3][HW] its pre-activation gradient (backward)
+  float* dfeat[kLevels];        // gradient of each feature plane
+  float* part;                  // [gridDim.x][11C + 3]
+  int HW;
+  SynTileGeo t;
+};
+
+// The 1x1 layers run on packed FP32 pairs over the hidden channel: the bank holds W_a
+// transposed (7 x C) and W_b row-major (3 x C), so that the weights of channels 2m and
+// 2m + 1 are adjacent.  z_1 and dL/dh_1 are exact per channel; z_2 and dL/df sum the even
+// and the odd channels separately and add the two halves at the end.
+template <int C>
+struct Syn1x1W {
+  static constexpr int WAT = kSyn1x1Base, BA = WAT + 7 * C, WBR = BA + C, BB = WBR + 3 * C;
+  static constexpr int M = C / 2;   // channel pairs
+};
+
+template <int C>
+__global__ void __launch_bounds__(256) k_syn1x1_fwd(Syn1x1Args a) {
+  pdl_wait();
+  pdl_trigger();
+  using Wt = Syn1x1W<C>;
+  constexpr int M = Wt::M;
+  const float2* wa = reinterpret_cast<const float2*>(c_syn + Wt::WAT);   // [7][M]
+  const float2* ba = reinterpret_cast<const float2*>(c_syn + Wt::BA);    // [M]
+  const float2* wb = reinterpret_cast<const float2*>(c_syn + Wt::WBR);   // [3][M]
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.HW; p += gridDim.x * blockDim.x) {
+    float2 fd[kLevels];
+#pragma unroll
+    for (int k = 0; k < kLevels; ++k) {
+      const float v = __ldg(a.feat[k] + p);
+      fd[k] = make_float2(v, v);
+    }
+    float2 z2p[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      float2 z = ba[m];
+#pragma unroll
+      for (int k = 0; k < kLevels; ++k) z = __ffma2_rn(wa[k * M + m], fd[k], z);
+      const float2 h = make_float2(fmaxf(z.x, 0.f), fmaxf(z.y, 0.f));
+#pragma unroll
+      for (int j = 0; j < 3; ++j) z2p[j] = __ffma2_rn(wb[j * M + m], h, z2p[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      a.h2[j * a.HW + p] = fmaxf(c_syn[Wt::BB + j] + (z2p[j].x + z2p[j].y), 0.f);
+  }
+}
+
+// Backward tile shapes.  Weight gradients from the staged rows: [dW_a | db_a] in 4 x 8
+// blocks (channels c..c+3 x [f, 1]) by the first kTA threads, [dW_b | db_b] in 3 x 4 blocks
+// (outputs x channels h..h+3 of [h_1, 1]) by the others, so that every warp runs one kind.
+constexpr int kTA = 160;
+template <int C>
+struct Syn1x1Shape {
+  static constexpr int T = kPixTile;
+  static constexpr int SZ = C + 4;   // stride of dz1 and [h1, 1] rows
+  static constexpr int SF = 12;      // stride of [f, 1] rows
+  static constexpr int SD = 4;       // stride of [dz2, 0] rows
+  static constexpr int NUA = C / 4;          // 4 x 8 blocks of [dW_a | db_a]
+  static constexpr int NUB = (C + 4) / 4;    // 3 x 4 blocks of [dW_b | db_b]
+  static constexpr int GA = kTA / NUA;       // pixel groups of the A blocks
+  static constexpr int GB = (T - kTA) / NUB; // and of the B blocks
+  static constexpr int GM = GA > GB ? GA : GB;
+  static constexpr int NP = 11 * C + 3;
+  static constexpr int tile_floats = T * (2 * SZ + SF + SD);
+  static constexpr int halo_floats = 3 * kSHS;   // dz of 3x3 layer 0 over the tile + halo
+  static constexpr int smem_floats =
+      tile_floats + halo_floats > GM * NP ? tile_floats + halo_floats : GM * NP;
+};
+
+template <int C>
+__global__ void __launch_bounds__(256, 2) k_syn1x1_bwd(Syn1x1Args a) {
+  pdl_wait();
+  pdl_trigger();
+  using Sh = Syn1x1Shape<C>;
+  using Wt = Syn1x1W<C>;
+  constexpr int T = Sh::T, SZ = Sh::SZ, SF = Sh::SF, SD = Sh::SD, M = Wt::M;
+  constexpr int NUA = Sh::NUA, NUB = Sh::NUB, GA = Sh::GA, GB = Sh::GB, NP = Sh::NP;
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  float* s_dz1 = sm;               // [T][SZ]
+  float* s_h1 = s_dz1 + T * SZ;    // [T][SZ]  (h1, 1, 0, 0, 0)
+  float* s_f = s_h1 + T * SZ;      // [T][SF]  (f0..f6, 1, 0...)
+  float* s_dz2 = s_f + T * SF;     // [T][SD]  (dz2, 0)
+  float* s_halo = s_dz2 + T * SD;  // 3 x kSHS
+
+  const int tid = threadIdx.x;
+  const bool is_a = tid < kTA;
+  const int unit = is_a ? tid % NUA : (tid - kTA) % NUB;
+  const int grp = is_a ? tid / NUA : (tid - kTA) / NUB;
+  const bool worker = is_a ? grp < GA : grp < GB;
+  // A blocks: acc[r][kk] = (dW[c0 + r][2kk], dW[c0 + r][2kk + 1]); B blocks use r < 3, kk < 2
+  float2 acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[r][k] = make_float2(0.f, 0.f);
+
+  const float2* wa = reinterpret_cast<const float2*>(c_syn + Wt::WAT);
+  const float2* ba = reinterpret_cast<const float2*>(c_syn + Wt::BA);
+  const float2* wb = reinterpret_cast<const float2*>(c_syn + Wt::WBR);
+  const float2* wab = reinterpret_cast<const float2*>(c_synb + Wt::WAT);
+  const float2* wbb = reinterpret_cast<const float2*>(c_synb + Wt::WBR);
+  const int tx = tid & 31, ty = tid >> 5;
+  for (int tile = blockIdx.x; tile < a.t.n_tiles; tile += gridDim.x) {
+    int y0, x0;
+    tile_xy(a.t, tile, y0, x0);
+    load_halo3(s_halo, a.dz0, y0, x0, a.t.H, a.t.W);
+    __syncthreads();
+    const int y = y0 + ty, x = x0 + tx;
+    const bool valid = y < a.t.H && x < a.t.W;
+    const int p = valid ? y * a.t.W + x : 0;
+    float f[kLevels];
+#pragma unroll
+    for (int k = 0; k < kLevels; ++k) f[k] = valid ? __ldg(a.feat[k] + p) : 0.f;
+    // gradient of h2: output gradient of 3x3 layer 0 plus its input-gradient stencil
+    float dh2[3] = {0.f, 0.f, 0.f};
+    if (valid) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) dh2[j] = __ldg(a.dhout + j * a.HW + p);
+      conv_adjoint<0>(dh2, s_halo, ty, tx, y, x, y0, x0, a.t.H, a.t.W);
+    }
+    // recompute z1, h1, z2
+    float2 fd[kLevels];
+#pragma unroll
+    for (int k = 0; k < kLevels; ++k) fd[k] = make_float2(f[k], f[k]);
+    float2 h1[M];
+    float2 z2p[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      float2 z = ba[m];
+#pragma unroll
+      for (int k = 0; k < kLevels; ++k) z = __ffma2_rn(wa[k * M + m], fd[k], z);
+      h1[m] = make_float2(fmaxf(z.x, 0.f), fmaxf(z.y, 0.f));
+#pragma unroll
+      for (int j = 0; j < 3; ++j) z2p[j] = __ffma2_rn(wb[j * M + m], h1[m], z2p[j]);
+    }
+    float* hrow = s_h1 + tid * SZ;
+#pragma unroll
+    for (int m = 0; m < M; m += 2)
+      *reinterpret_cast<float4*>(hrow + 2 * m) =
+          valid ? make_float4(h1[m].x, h1[m].y, h1[m + 1].x, h1[m + 1].y)
+                : make_float4(0.f, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4*>(hrow + C) = make_float4(valid ? 1.f : 0.f, 0.f, 0.f, 0.f);
+    float dz2[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      dz2[j] = c_syn[Wt::BB + j] + (z2p[j].x + z2p[j].y) > 0.f ? dh2[j] : 0.f;
+    *reinterpret_cast<float4*>(s_dz2 + tid * SD) = make_float4(dz2[0], dz2[1], dz2[2], 0.f);
+    // backward: dh1 = W_b^T dz2, dz1 = [h1 > 0] dh1, df = W_a^T dz1
+    const float2 g0 = make_float2(dz2[0], dz2[0]), g1 = make_float2(dz2[1], dz2[1]),
+                 g2 = make_float2(dz2[2], dz2[2]);
+    float2 dfp[kLevels];
+#pragma unroll
+    for (int k = 0; k < kLevels; ++k) dfp[k] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      float2 dh = __fmul2_rn(wbb[m], g0);
+      dh = __ffma2_rn(wbb[M + m], g1, dh);
+      dh = __ffma2_rn(wbb[2 * M + m], g2, dh);
+      h1[m] = make_float2(h1[m].x > 0.f ? dh.x : 0.f, h1[m].y > 0.f ? dh.y : 0.f);   // dz1
+#pragma unroll
+      for (int k = 0; k < kLevels; ++k) dfp[k] = __ffma2_rn(wab[k * M + m], h1[m], dfp[k]);
+    }
+    float* zrow = s_dz1 + tid * SZ;
+#pragma unroll
+    for (int m = 0; m < M; m += 2)
+      *reinterpret_cast<float4*>(zrow + 2 * m) = make_float4(h1[m].x, h1[m].y, h1[m + 1].x, h1[m + 1].y);
+    float* frow = s_f + tid * SF;
+#pragma unroll
+    for (int k = 0; k < kLevels; ++k) frow[k] = f[k];
+    frow[7] = valid ? 1.f : 0.f;
+    if (valid) {
+#pragma unroll
+      for (int k = 0; k < kLevels; ++k) a.dfeat[k][p] = dfp[k].x + dfp[k].y;
+    }
+    __syncthreads();
+    if (worker) {
+      if (is_a) {   // rows c = 4 unit .. +3 of [dW_a | db_a]
+        const int c0 = unit * 4;
+        for (int q = grp; q < T; q += GA) {
+          const float4 dz = *reinterpret_cast<const float4*>(s_dz1 + q * SZ + c0);
+          const float4 f0 = *reinterpret_cast<const float4*>(s_f + q * SF);
+          const float4 f1 = *reinterpret_cast<const float4*>(s_f + q * SF + 4);
+          const float dv[4] = {dz.x, dz.y, dz.z, dz.w};
+          const float2 fp[4] = {make_float2(f0.x, f0.y), make_float2(f0.z, f0.w),
+                                make_float2(f1.x, f1.y), make_float2(f1.z, f1.w)};
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              acc[r][k] = __ffma2_rn(make_float2(dv[r], dv[r]), fp[k], acc[r][k]);
+        }
+      } else {      // cols 4 unit .. +3 of [dW_b | db_b]
+        const int h0 = unit * 4;
+        for (int q = grp; q < T; q += GB) {
+          const float4 dz = *reinterpret_cast<const float4*>(s_dz2 + q * SD);
+          const float4 hv = *reinterpret_cast<const float4*>(s_h1 + q * SZ + h0);
+          const float dv[3] = {dz.x, dz.y, dz.z};
+          const float2 hp[2] = {make_float2(hv.x, hv.y), make_float2(hv.z, hv.w)};
+#pragma unroll
+          for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+              acc[r][k] = __ffma2_rn(make_float2(dv[r], dv[r]), hp[k], acc[r][k]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // partial layout: W_a (C x 7), b_a (C), W_b (3 x C), b_b (3); groups summed in order
+  float* red = sm;
+  if (worker) {
+    float* mine = red + grp * NP;
+    if (is_a) {
+      const int c0 = unit * 4;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) mine[(c0 + r) * 7 + k] = (k & 1) ? acc[r][k >> 1].y : acc[r][k >> 1].x;
+        mine[7 * C + c0 + r] = acc[r][3].y;
+      }
+    } else {
+      const int h0 = unit * 4;
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int col = h0 + k;
+          const float v = (k & 1) ? acc[r][k >> 1].y : acc[r][k >> 1].x;
+          if (col < C) mine[8 * C + r * C + col] = v;
+          else if (col == C) mine[11 * C + r] = v;
+        }
+    }
+  }
+  __syncthreads();
+  for (int j = tid; j < NP; j += T) {
+    const int ng = j < 8 * C ? GA : GB;
+    float t = 0.f;
+    for (int g = 0; g < ng; ++g) t += red[g * NP + j];
+    a.part[(long long)blockIdx.x * NP + j] = t;
   }
 }
 
@@ -635,15 +898,13 @@ __global__ void __launch_bounds__(256) k_conv_dx(ConvArgs a) {
 
 template <int C>
 static cudaError_t syn1x1_fwd_t(const Syn1x1Args& a, int grid, cudaStream_t st) {
-  k_syn1x1_fwd<C><<<grid, 256, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_k(k_syn1x1_fwd<C>, dim3(grid), dim3(256), 0, st, a);
 }
 
 template <int C>
 static cudaError_t syn1x1_bwd_t(const Syn1x1Args& a, int grid, cudaStream_t st) {
   const size_t smem = (size_t)Syn1x1Shape<C>::smem_floats * sizeof(float);
-  k_syn1x1_bwd<C><<<grid, kPixTile, smem, st>>>(a);
-  return cudaGetLastError();
+  return launch_k(k_syn1x1_bwd<C>, dim3(grid), dim3(kPixTile), smem, st, a);
 }
 
 template <int C>
@@ -671,9 +932,20 @@ static Syn1x1Args make_1x1(const Geo& g, const float* yhat, const UpPlan& up) {
 
 int syn1x1_partial_cols(const Arch& a) { return 11 * a.C + 3; }
 
+static SynTileGeo tile_geo(const Geo& g) {
+  SynTileGeo t;
+  t.H = g.H;
+  t.W = g.W;
+  t.ntx = (g.W + kSTX - 1) / kSTX;
+  t.n_tiles = t.ntx * ((g.H + kSTY - 1) / kSTY);
+  return t;
+}
+
+int syn_tile_count(const Geo& g) { return tile_geo(g).n_tiles; }
+
 cudaError_t syn_forward(const Arch& ar, const Geo& g, const float* yhat, const UpPlan& up,
-                        const float* x, float* hbuf, float* dxhat, float* part_d, int grid,
-                        cudaStream_t st) {
+                        const float* x, float* hbuf, float* dxhat, float* part_d,
+                        float* part_conv, int grid, cudaStream_t st) {
   const int HW = g.H * g.W;
   Syn1x1Args s = make_1x1(g, yhat, up);
   s.h2 = hbuf;
@@ -685,21 +957,20 @@ cudaError_t syn_forward(const Arch& ar, const Geo& g, const float* yhat, const U
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
-  for (int i = 0; i < ar.NR; ++i) {
-    ConvArgs c{};
-    c.hin = hbuf + (size_t)i * 3 * HW;
-    c.hout = hbuf + (size_t)(i + 1) * 3 * HW;
-    c.x = x; c.dz = dxhat; c.part = part_d;
-    c.dscale = 2.0f / (3.0f * (float)HW);
-    c.H = g.H; c.W = g.W;
-    const bool last = i == ar.NR - 1;
-    if (i == 0 && last) k_conv_fwd<0, true><<<grid, 256, 0, st>>>(c);
-    else if (i == 0) k_conv_fwd<0, false><<<grid, 256, 0, st>>>(c);
-    else k_conv_fwd<1, true><<<grid, 256, 0, st>>>(c);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  ConvArgs c{};
+  c.t = tile_geo(g);
+  c.x = x;
+  c.dxhat = dxhat;
+  c.part_d = part_d;
+  c.part = part_conv + (size_t)(ar.NR - 1) * grid * 84;
+  c.dscale = 2.0f / (3.0f * (float)HW);
+  c.hin = hbuf;
+  c.hout = hbuf + (size_t)3 * HW;
+  if (ar.NR == 1) return launch_k(k_conv3_last<0>, dim3(grid), dim3(256), 0, st, c);
+  if ((e = launch_k(k_conv3_fwd<0>, dim3(grid), dim3(256), 0, st, c)) != cudaSuccess) return e;
+  c.hin = hbuf + (size_t)3 * HW;
+  c.hout = hbuf + (size_t)6 * HW;
+  return launch_k(k_conv3_last<1>, dim3(grid), dim3(256), 0, st, c);
 }
 
 // dhbuf holds NR + 1 gradient planes-of-3: dhbuf[NR] = dL/dx_hat (written by the forward).
@@ -707,26 +978,26 @@ cudaError_t syn_backward(const Arch& ar, const Geo& g, const float* yhat, const 
                          float* hbuf, float* dhbuf, float* dz, float* gsyn, float* part_conv,
                          float* part_syn, int grid, cudaStream_t st) {
   const int HW = g.H * g.W;
-  cudaError_t e;
-  for (int i = ar.NR - 1; i >= 0; --i) {
-    ConvArgs c{};
-    c.hin = hbuf + (size_t)i * 3 * HW;
-    c.dhout = dhbuf + (size_t)(i + 1) * 3 * HW;
-    c.dz = dz;
-    c.dhin = dhbuf + (size_t)i * 3 * HW;
-    c.part = part_conv + (size_t)i * grid * 84;
-    c.H = g.H; c.W = g.W;
-    const bool last = i == ar.NR - 1;
-    if (i == 0 && last) k_conv_dz<0, true><<<grid, 256, 0, st>>>(c);
-    else if (i == 0) k_conv_dz<0, false><<<grid, 256, 0, st>>>(c);
-    else k_conv_dz<1, true><<<grid, 256, 0, st>>>(c);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (i == 0) k_conv_dx<0><<<grid, 256, 0, st>>>(c);
-    else k_conv_dx<1><<<grid, 256, 0, st>>>(c);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
+  const float* dxhat = dhbuf + (size_t)ar.NR * 3 * HW;
   Syn1x1Args s = make_1x1(g, yhat, up);
-  s.dh2 = dhbuf;
+  s.t = tile_geo(g);
+  if (ar.NR == 2) {
+    ConvArgs c{};
+    c.t = s.t;
+    c.g = dxhat;
+    c.hin = hbuf;
+    c.dh = dhbuf + (size_t)3 * HW;
+    c.dz = dz;
+    c.part = part_conv;
+    cudaError_t e = launch_k(k_conv3_mid, dim3(grid), dim3(256), 0, st, c);
+    if (e != cudaSuccess) return e;
+    s.dhout = c.dh;
+    s.dz0 = dz;
+  } else {
+    // one linear layer: its output gradient is also its pre-activation gradient
+    s.dhout = dxhat;
+    s.dz0 = dxhat;
+  }
   s.dfeat[0] = gsyn + g.off[0];
   for (int l = 1; l < kLevels; ++l) s.dfeat[l] = up.dplane[l][0];
   s.part = part_syn;
@@ -739,6 +1010,8 @@ cudaError_t syn_backward(const Arch& ar, const Geo& g, const float* yhat, const 
 }
 
 __global__ void k_planar_to_hwc(const float* __restrict__ xh, float* __restrict__ out, int HW) {
+  pdl_wait();
+  pdl_trigger();
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) out[p * 3 + c] = xh[c * HW + p];
@@ -749,15 +1022,16 @@ cudaError_t syn_decode(const Arch& a, const Geo& g, const float* hbuf_last, floa
                        cudaStream_t st) {
   (void)a;
   const int HW = g.H * g.W;
-  k_planar_to_hwc<<<(HW + 255) / 256 < 2048 ? (HW + 255) / 256 : 2048, 256, 0, st>>>(
-      hbuf_last, out_hwc, HW);
-  return cudaGetLastError();
+  return launch_k(k_planar_to_hwc, dim3((HW + 255) / 256 < 2048 ? (HW + 255) / 256 : 2048),
+                  dim3(256), 0, st, hbuf_last, out_hwc, HW);
 }
 
 // Bank image from the flat parameters (synthesis section: W_a, b_a, W_b, b_b, then the 3x3
 // layers; upsampling filters).
 __global__ void k_syn_image(const float* __restrict__ syn, int C, int NR,
                             const float* __restrict__ filters, int n_filt, SynBank* img) {
+  pdl_wait();
+  pdl_trigger();
   const int n3 = NR * k3x3;
   const float* p1 = syn;                   // W_a (C x 7), b_a, W_b (3 x C), b_b
   const float* p3 = syn + 11 * C + 3;      // 3x3 layers
@@ -767,13 +1041,10 @@ __global__ void k_syn_image(const float* __restrict__ syn, int C, int NR,
       v = p3[i];
     } else if (i >= kSyn1x1Base) {
       const int r = i - kSyn1x1Base;
-      if (r < 8 * C) {
-        v = p1[r];                          // W_a, b_a
-      } else if (r < 12 * C) {
-        const int o = (r - 8 * C) >> 2, j = (r - 8 * C) & 3;
-        v = j < 3 ? p1[8 * C + j * C + o] : 0.f;   // W_b^T
-      } else if (r < 12 * C + 3) {
-        v = p1[11 * C + (r - 12 * C)];      // b_b
+      if (r < 7 * C) {
+        v = p1[(r % C) * 7 + r / C];        // W_a^T
+      } else if (r < 11 * C + 3) {
+        v = p1[r];                          // b_a, W_b, b_b as in the parameters
       }
     }
     img->syn[i] = v;
