@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -31,6 +32,10 @@ METRIC = "encode Mpixel-iter/s (fwd+bwd+Adam) vs plain; s to RD-cost within 1% o
 UNIT = "Mpixel-iter/s"
 PAPER_DERIVED_MPXIT = 22.5   # 512x768, 2300-MAC, 102 950 iterations in ~30 min (Sec. V, Fig. 5)
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) of one launch of the ARM kernel on this workload, from the ncu
+# capture summarised in profiles/k_arm_512x768_full.md; None when the kernel has changed
+# since the counters were taken
+ARM_DRAM_BYTES_PER_LAUNCH = None
 
 
 def dist_env():
@@ -249,15 +254,18 @@ def run_ours(a, cfgd):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
     barrier()
+    arm_ms_steps = []
     with ClockSampler(local) as clk:
         for k in range(a.steps):
             flush.zero_()
             starts[k].record(stream)
             cc.cc_encode_iters(ctx, 1)
             ends[k].record(stream)
+            # the ARM kernel of this replay, between two events recorded on its stream
+            arm_ms_steps.append(cc.cc_arm_kernel_ms(ctx))
         barrier()
         total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-        # dominant kernel (ARM + rate, forward and backward), timed live with CUDA events
+        # per-phase breakdown of eager iterations (kernels in stream order, no overlap)
         phases = cc.cc_profile_phases(ctx, max(3, min(20, a.steps)))
     clocks = clk.summary()
     total_ms = max_over_ranks(total_ms, td, dev)
@@ -294,8 +302,12 @@ def run_ours(a, cfgd):
     sms = props.multi_processor_count
     clk_max = float(pk.get("sm_max_mhz", 2070.0))
     peak_tflops = sms * FP32_LANES_PER_SM * 2 * clk_max * 1e6 / 1e12
-    arm_ms = float(phases[1])
+    arm_ms = float(np.mean(arm_ms_steps))
     arm_tflops = arm_flops_per_launch(cfgd, n_lat) / (arm_ms / 1e3) / 1e12
+    # the ARM kernel runs on its share of the SMs (one CTA per SM) beside the chain
+    share = min(1.0, max(0.05, float(os.environ.get("CC_ARM_SM_SHARE", "0.5"))))
+    arm_sms = max(1, int(math.floor(share * sms + 0.5)))
+    arm_peak = arm_sms * FP32_LANES_PER_SM * 2 * clk_max * 1e6 / 1e12
     kappa = decoder_macs_per_pixel(cfgd, H, W)
     it_ms = total_ms / a.steps
     out = {
@@ -304,11 +316,13 @@ def run_ours(a, cfgd):
         "vs_baseline": value / PAPER_DERIVED_MPXIT / world if world else None,
         "dtype": "f32", "data": "synthetic", "config": workload(cfgd),
         "roofline": {"bound": "alu", "kernel": "k_arm<24,2,true> (ARM + rate, fwd+bwd)",
-                     "achieved": arm_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": arm_tflops / peak_tflops, "traffic": None,
-                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {clk_max:.0f} MHz "
-                                   f"(sm_max_mhz, {src})",
-                     "arm_ms": arm_ms,
+                     "achieved": arm_tflops, "peak": arm_peak, "unit": "TFLOP/s",
+                     "frac": arm_tflops / arm_peak, "traffic": ARM_DRAM_BYTES_PER_LAUNCH,
+                     "peak_basis": f"{arm_sms} of {sms} SMs (the ARM kernel's share) x 128 FP32 "
+                                   f"lanes x 2 x {clk_max:.0f} MHz (sm_max_mhz, {src})",
+                     "frac_of_whole_gpu": arm_tflops / peak_tflops,
+                     "arm_ms": arm_ms, "arm_ms_source": "CUDA events on the ARM stream inside "
+                                                        "every timed graph replay",
                      "phase_ms": {n: float(v) for n, v in zip(cc.PHASES, phases)}},
         "whole_iteration": {"flop_per_pixel_iter": 6 * kappa,
                             "tflops": 6 * kappa * H * W / (it_ms / 1e3) / 1e12,

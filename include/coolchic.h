@@ -159,11 +159,19 @@ int cc_noise(cc_ctx* ctx, int iter, float* out);
  * recording CUDA events around each phase, and writes the mean milliseconds per phase to
  * ms_out[CC_N_PHASES] (host): 0 weight upload + quantisation, 1 ARM + rate forward and
  * backward, 2 upsampling forward, 3 synthesis forward + distortion, 4 synthesis backward,
- * 5 upsampling backward, 6 reductions + Adam + loss bookkeeping.  Synchronises.
+ * 5 upsampling backward, 6 context-gradient gather, reductions, Adam and loss
+ * bookkeeping.  Synchronises.
  * cc_graph_kernel_count gives the number of kernel launches in one captured iteration. */
 #define CC_N_PHASES 7
 int cc_profile_phases(cc_ctx* ctx, int reps, float* ms_out);
 int cc_graph_kernel_count(cc_ctx* ctx, int* n_kernels);
+
+/* Milliseconds of the ARM kernel (forward + backward, rate) in the most recent pass that
+ * ran it beside the synthesis chain (a captured iteration replayed by cc_encode_iters, or
+ * an eager pass), measured by two CUDA events recorded on the ARM's stream around its
+ * launch.  Measurement support with no counterpart in the paper.  Waits for the second
+ * event; CC_ECUDA (event not yet recorded) before the first such pass.  ms: host. */
+int cc_arm_kernel_ms(cc_ctx* ctx, float* ms);
 
 /* Checkpoint: a flat versioned blob with y, parameters, Adam moments, the iteration
  * counter and the seed.  With buf = NULL, *nbytes receives the size.  cc_set_state

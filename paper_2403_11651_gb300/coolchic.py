@@ -70,6 +70,7 @@ def _declare(lib):
         "cc_free": (None, [P]),
         "cc_strerror": (ctypes.c_char_p, [c_int]),
         "cc_last_cuda_error": (ctypes.c_char_p, []),
+        "cc_arm_kernel_ms": (c_int, [P, POINTER(ctypes.c_float)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -326,6 +327,13 @@ def cc_profile_phases(ctx, reps: int = 10):
     return out
 
 
+def cc_arm_kernel_ms(ctx) -> float:
+    """Milliseconds of the ARM kernel in the most recent pass that ran it on its own stream."""
+    ms = ctypes.c_float()
+    _check(_lib().cc_arm_kernel_ms(ctx, ctypes.byref(ms)), "cc_arm_kernel_ms")
+    return float(ms.value)
+
+
 def cc_graph_kernel_count(ctx) -> int:
     n = c_int()
     _check(_lib().cc_graph_kernel_count(ctx, ctypes.byref(n)), "cc_graph_kernel_count")
@@ -367,5 +375,5 @@ EXPORTED = ["cc_param_count", "cc_latent_count", "cc_workspace_size", "cc_init_i
             "cc_init_image_ws", "cc_set_image", "cc_encode_iters", "cc_rd_cost", "cc_decode",
             "cc_get_grads", "cc_forward_backward", "cc_get_losses", "cc_iteration", "cc_noise",
             "cc_set_latents", "cc_get_latents", "cc_set_params", "cc_get_params",
-            "cc_profile_phases", "cc_graph_kernel_count", "cc_rate_bits_noalloc",
+            "cc_profile_phases", "cc_graph_kernel_count", "cc_arm_kernel_ms", "cc_rate_bits_noalloc",
             "cc_get_state", "cc_set_state", "cc_free", "cc_strerror", "cc_last_cuda_error"]

@@ -131,13 +131,14 @@ __global__ void __launch_bounds__(kArmTile / LPT, ArmOcc<N>::blocks) k_arm(ArmAr
   const int unit = tid % NBLK, grp = tid / NBLK;
   const int uL = unit / (NB * NB), urb = (unit / NB) % NB, ucb = unit % NB;
 
-  float acc[RB][RB];
+  // weight-gradient block as packed pairs along its columns
+  float2 acc[RB][RB / 2];
   float xacc[XPER][10];
   if constexpr (BWD) {
 #pragma unroll
     for (int r = 0; r < RB; ++r)
 #pragma unroll
-      for (int c = 0; c < RB; ++c) acc[r][c] = 0.f;
+      for (int c = 0; c < RB / 2; ++c) acc[r][c] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < XPER; ++q)
 #pragma unroll
@@ -300,9 +301,12 @@ __global__ void __launch_bounds__(kArmTile / LPT, ArmOcc<N>::blocks) k_arm(ArmAr
           load_row<RB>(av, A + p * S);
           load_row<RB>(bv, B + p * S);
 #pragma unroll
-          for (int rr = 0; rr < RB; ++rr)
+          for (int rr = 0; rr < RB; ++rr) {
+            const float2 ad = make_float2(av[rr], av[rr]);
 #pragma unroll
-            for (int cc = 0; cc < RB; ++cc) acc[rr][cc] = fmaf(av[rr], bv[cc], acc[rr][cc]);
+            for (int cc = 0; cc < RB / 2; ++cc)
+              acc[rr][cc] = __ffma2_rn(ad, make_float2(bv[2 * cc], bv[2 * cc + 1]), acc[rr][cc]);
+          }
         }
       }
       // biases and the output layer, in chunks of four columns
@@ -357,7 +361,8 @@ __global__ void __launch_bounds__(kArmTile / LPT, ArmOcc<N>::blocks) k_arm(ArmAr
     for (int rr = 0; rr < RB; ++rr)
 #pragma unroll
       for (int cc = 0; cc < RB; ++cc)
-        mine[uL * LW + (urb * RB + rr) * N + ucb * RB + cc] = acc[rr][cc];
+        mine[uL * LW + (urb * RB + rr) * N + ucb * RB + cc] =
+            (cc & 1) ? acc[rr][cc >> 1].y : acc[rr][cc >> 1].x;
 #pragma unroll
     for (int qi = 0; qi < XPER; ++qi) {
       const int q = unit + qi * NBLK;

@@ -146,6 +146,7 @@ struct cc_ctx {
   cudaStream_t cap = nullptr;
   cudaStream_t side = nullptr;        // ARM branch of a pass, concurrent with the synthesis
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_a0 = nullptr, ev_a1 = nullptr;   // timing of the ARM kernel in forked passes
   bool own_mem = false;
   void* mem = nullptr;
   size_t bytes = 0;
@@ -303,8 +304,22 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
     CKE(cudaEventRecord(c->ev_fork, s));
     CKE(cudaStreamWaitEvent(sa, c->ev_fork, 0));
   }
+  // timing events around the ARM kernel: graph nodes when the pass is being captured
+  auto record_on_side = [&](cudaEvent_t e) -> cudaError_t {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t err = cudaStreamIsCapturing(sa, &cs);
+    if (err != cudaSuccess) return err;
+    return cs == cudaStreamCaptureStatusActive
+               ? cudaEventRecordWithFlags(e, sa, cudaEventRecordExternal)
+               : cudaEventRecord(e, sa);
+  };
+  if (fork) CKE(record_on_side(c->ev_a0));
   CKE(arm_launch(a, backward, c->yhat_bord, c->geo, c->tiles, c->n_tiles, c->grid_arm, c->dctx,
                  c->gself, c->part_arm, c->part_bits, sa));
+  if (fork) CKE(record_on_side(c->ev_a1));
+  // the context gather follows the ARM on its stream; timed per phase it runs after the
+  // upsampling adjoint instead, so that the phase events stay in stream order
+  if (backward && fork) CKE(ctx_gather(c->geo, c->offs, a.N, c->gself, c->dctx, sa));
   if (fork) CKE(cudaEventRecord(c->ev_join, sa));
   CKE(mark(2));
   CKE(up_forward(a, c->geo, c->yhat, c->up, c->grid_syn, s));
@@ -319,12 +334,12 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
     CKE(up_backward(a, c->geo, c->yhat, c->up, c->gsyn, c->part_up, c->grid_syn, s));
     CKE(mark(6));
     if (fork) CKE(cudaStreamWaitEvent(s, c->ev_join, 0));
+    else CKE(ctx_gather(c->geo, c->offs, a.N, c->gself, c->dctx, s));
     CKE(reduce_sections(c->tab, c->part2, c->n_virtual, c->slices, s));
     CKE(param_update(c->lay, a, c->part2, c->slices, c->params, c->mp, c->vp,
                      grad_out ? grad_out + c->geo.n_lat : nullptr, apply, c->cfg.lr, c->sc, s));
-    CKE(latent_update(c->geo, a, c->offs, c->gsyn, c->gself, c->dctx,
-                      (float)((double)c->cfg.lam / (double)c->HW), c->y, c->my, c->vy, grad_out,
-                      apply, c->cfg.lr, c->sc, s));
+    CKE(latent_update(c->geo, c->gsyn, c->gself, (float)((double)c->cfg.lam / (double)c->HW),
+                      c->y, c->my, c->vy, grad_out, apply, c->cfg.lr, c->sc, s));
   } else if (fork) {
     CKE(cudaStreamWaitEvent(s, c->ev_join, 0));
   }
@@ -444,7 +459,9 @@ int init_common(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
   if ((ce = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(fail_cuda(ce, "cudaStreamCreate"));
   if ((ce = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
-      (ce = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess)
+      (ce = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess ||
+      (ce = cudaEventCreate(&c->ev_a0)) != cudaSuccess ||
+      (ce = cudaEventCreate(&c->ev_a1)) != cudaSuccess)
     return bail(fail_cuda(ce, "cudaEventCreate"));
   if ((ce = arm_prepare(c->arch)) != cudaSuccess) return bail(fail_cuda(ce, "arm_prepare"));
   if ((ce = syn_prepare(c->arch)) != cudaSuccess) return bail(fail_cuda(ce, "syn_prepare"));
@@ -462,6 +479,9 @@ int init_common(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
   if ((ce = cudaMemcpyAsync(c->params, src, (size_t)c->lay.total * sizeof(float),
                             cudaMemcpyDefault, c->st)))
     return bail(fail_cuda(ce, "params copy"));
+  const IterScalars sc0 = iter_scalars_at(0);
+  if ((ce = cudaMemcpyAsync(c->sc, &sc0, sizeof(sc0), cudaMemcpyHostToDevice, c->st)))
+    return bail(fail_cuda(ce, "scalars copy"));
   if ((ce = cudaMemcpyAsync(c->tiles, c->h_tiles.data(), c->h_tiles.size() * sizeof(int2),
                             cudaMemcpyHostToDevice, c->st)))
     return bail(fail_cuda(ce, "tiles copy"));
@@ -702,6 +722,14 @@ int cc_profile_phases(cc_ctx* c, int reps, float* ms_out) {
   return CC_OK;
 }
 
+int cc_arm_kernel_ms(cc_ctx* c, float* ms) {
+  if (!c || !ms) return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  CK(cudaEventSynchronize(c->ev_a1));
+  CK(cudaEventElapsedTime(ms, c->ev_a0, c->ev_a1));
+  return CC_OK;
+}
+
 int cc_graph_kernel_count(cc_ctx* c, int* n_kernels) {
   if (!c || !n_kernels) return CC_EINVAL;
   CK(cudaSetDevice(c->dev));
@@ -786,8 +814,7 @@ int cc_set_state(cc_ctx* c, const void* buf, size_t nbytes) {
   CK(cudaMemcpyAsync(c->mp, f.data() + 3 * nl + np, np * sizeof(float), cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(c->vp, f.data() + 3 * nl + 2 * np, np * sizeof(float), cudaMemcpyHostToDevice,
                      c->st));
-  IterScalars sc{};
-  sc.t = hd.iter;
+  const IterScalars sc = iter_scalars_at(hd.iter);
   CK(cudaMemcpyAsync(c->sc, &sc, sizeof(sc), cudaMemcpyHostToDevice, c->st));
   CK(cudaStreamSynchronize(c->st));
   c->iter = hd.iter;
@@ -805,6 +832,8 @@ void cc_free(cc_ctx* c) {
   if (c->side) cudaStreamDestroy(c->side);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_a0) cudaEventDestroy(c->ev_a0);
+  if (c->ev_a1) cudaEventDestroy(c->ev_a1);
   if (c->own_mem && c->mem) cudaFree(c->mem);
   delete c;
 }

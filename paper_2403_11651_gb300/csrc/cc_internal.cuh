@@ -36,7 +36,38 @@ constexpr int kCtxPad = 4;        // reach of the largest causal context (N = 24
 // writes are visible (at once for a kernel launched without the attribute).  pdl_trigger()
 // lets the successor be placed; it is issued after the wait, so at most one kernel ahead
 // holds blocks that wait.  CC_PDL=0 in the environment turns the attribute off.
+#ifndef CC_TRACE
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#else
+// Traced build (all sources in one translation unit): block (0, 0, 0) of every kernel
+// records, once its wait returns, the global timer, an FNV-1a hash of the kernel's name
+// and its launch shape.
+struct TraceRec {
+  unsigned long long t;
+  unsigned hash;
+  int gx, gy, bx;
+};
+constexpr int kTraceCap = 8192;
+__device__ TraceRec g_trace[kTraceCap];
+__device__ unsigned g_trace_n;
+__device__ __forceinline__ void pdl_wait_traced(const char* name) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (threadIdx.x == 0 && threadIdx.y == 0 && blockIdx.x == 0 && blockIdx.y == 0 &&
+      blockIdx.z == 0) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    unsigned h = 2166136261u;
+    for (int i = 0; name[i] && i < 64; ++i) h = (h ^ (unsigned char)name[i]) * 16777619u;
+    const unsigned k = atomicAdd(&g_trace_n, 1u) % kTraceCap;
+    g_trace[k].t = t;
+    g_trace[k].hash = h;
+    g_trace[k].gx = gridDim.x;
+    g_trace[k].gy = gridDim.y;
+    g_trace[k].bx = blockDim.x * blockDim.y;
+  }
+}
+#define pdl_wait() pdl_wait_traced(__func__)
+#endif
 __device__ __forceinline__ void pdl_trigger() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
@@ -96,7 +127,10 @@ struct IterScalars {
   float inv_sqrt_bc2; // Adam 1 / sqrt(1 - beta2^(t+1))
   int pad;
   double D, R, loss;
+  double b1t, b2t;    // beta1^t, beta2^t, carried by repeated multiplication
 };
+// IterScalars of iteration t, computed on the host (context set-up, state restore).
+IterScalars iter_scalars_at(int t);
 
 // ---- launchers (each returns the cudaError_t of its launch) ----
 // ARM (cc_arm.cu)
@@ -143,15 +177,20 @@ cudaError_t syn_prepare(const Arch& a);   // kernel attributes; call once before
 cudaError_t quantize_launch(const Geo& g, const float* y, float* yhat, float* yhat_bord,
                             const float* noise, int mode, const IterScalars* sc, int ste_start,
                             uint64_t seed, int iter_override, cudaStream_t st);
+// Context gradient of the rate: gself[q] += sum over the N context positions k of
+// dctx[k][q - offset_k] (the ARM's gradients with respect to its inputs), in place.
+cudaError_t ctx_gather(const Geo& g, const int2* d_offsets, int N, float* gself,
+                       const float* dctx, cudaStream_t st);
 cudaError_t reduce_sections(const SectionTable& tab, float* part2, int n_virtual, int slices,
                             cudaStream_t st);
 cudaError_t param_update(const Layout& lay, const Arch& a, const float* part2, int slices,
                          float* params, float* m, float* v, float* grad_out, bool apply,
                          float lr, const IterScalars* sc, cudaStream_t st);
-cudaError_t latent_update(const Geo& g, const Arch& a, const int2* d_offsets,
-                          const float* gsyn, const float* gself, const float* dctx,
-                          float rate_scale, float* y, float* m, float* v, float* grad_out,
-                          bool apply, float lr, const IterScalars* sc, cudaStream_t st);
+// Total latent gradient dD/dy_hat + lambda / (HW) * dR/dy_hat (grate: the rate gradient
+// after ctx_gather) and Adam on the latents.
+cudaError_t latent_update(const Geo& g, const float* gsyn, const float* grate, float rate_scale,
+                          float* y, float* m, float* v, float* grad_out, bool apply, float lr,
+                          const IterScalars* sc, cudaStream_t st);
 cudaError_t finish_iteration(const float* part_d, int nd, const float* part_bits, int nb,
                              double d_scale, double r_scale, double lam, IterScalars* sc,
                              double* log, bool advance, cudaStream_t st,

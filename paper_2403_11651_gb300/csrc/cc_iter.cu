@@ -2,6 +2,7 @@
 // as used in Sec. IV-B), plus the deterministic reductions of the per-CTA partial sums.
 #include "cc_internal.cuh"
 
+#include <cmath>
 #include <cstdlib>
 
 namespace cc {
@@ -120,16 +121,6 @@ struct AdamStep {
   float lr, inv_bc1, inv_sqrt_bc2;
 };
 
-__device__ __forceinline__ AdamStep adam_step(int t, float lr) {
-  // bias corrections of step t + 1, in double
-  const double s = (double)(t + 1);
-  AdamStep a;
-  a.lr = lr;
-  a.inv_bc1 = (float)(1.0 / (1.0 - pow(0.9, s)));
-  a.inv_sqrt_bc2 = (float)(1.0 / sqrt(1.0 - pow(0.999, s)));
-  return a;
-}
-
 __device__ __forceinline__ void adam_apply(float& p, float& m, float& v, float g,
                                            const AdamStep& a) {
   m = 0.9f * m + 0.1f * g;
@@ -142,8 +133,7 @@ struct VirtualMap {
   int vsyn, vconv, vup, n_virtual;
 };
 
-// Also publishes the Adam bias corrections of this iteration in IterScalars (block 0),
-// for the latent update that runs next on the stream.
+// Adam bias corrections of this iteration are read from IterScalars (set when t advanced).
 __global__ void __launch_bounds__(128) k_param_update(VirtualMap vm, const float* part2,
                                                       int slices, float* params, float* m,
                                                       float* v, float* grad_out, int apply,
@@ -151,17 +141,11 @@ __global__ void __launch_bounds__(128) k_param_update(VirtualMap vm, const float
   pdl_wait();
   pdl_trigger();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  __shared__ AdamStep s_st;
-  if (threadIdx.x == 0) {
-    s_st = adam_step(sc->t, lr);
-    if (blockIdx.x == 0) {
-      sc->inv_bc1 = s_st.inv_bc1;
-      sc->inv_sqrt_bc2 = s_st.inv_sqrt_bc2;
-    }
-  }
-  __syncthreads();
-  const AdamStep st = s_st;
   if (j >= total) return;
+  AdamStep st;
+  st.lr = lr;
+  st.inv_bc1 = sc->inv_bc1;
+  st.inv_sqrt_bc2 = sc->inv_sqrt_bc2;
   int vs[kLevels - 1];
   int nv = 1;
   if (j < vm.n_arm) {
@@ -206,29 +190,18 @@ cudaError_t param_update(const Layout& lay, const Arch& a, const float* part2, i
 // Gradient of a latent: the synthesis path, plus lambda/(HW) times the rate terms in
 // which it appears, as the coded symbol (gself) and in the context of every latent p
 // whose causal neighbourhood contains it (dctx of p at the matching slot).
-__global__ void __launch_bounds__(256) k_latent_update(Geo g, const int2* __restrict__ offs,
-                                                       int N, const float* __restrict__ gsyn,
-                                                       const float* __restrict__ gself,
-                                                       const float* __restrict__ dctx,
+__global__ void __launch_bounds__(256) k_latent_update(Geo g, const float* __restrict__ gsyn,
+                                                       const float* __restrict__ grate,
                                                        float rate_scale, float* y, float* m,
                                                        float* v, float* grad_out, int apply,
                                                        float lr, const IterScalars* sc) {
   pdl_wait();
   pdl_trigger();
   const int l = blockIdx.y;
-  const int w = g.w[l], h = g.h[l];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= h * w) return;
-  const int r = i / w, c = i - r * w;
+  if (i >= g.h[l] * g.w[l]) return;
   const long long q = g.off[l] + i;
-  float gr = __ldg(gself + q);
-  for (int k = 0; k < N; ++k) {
-    const int2 o = __ldg(offs + k);
-    const int pr = r - o.x, pc = c - o.y;
-    if (pr < h && pc >= 0 && pc < w)
-      gr += __ldg(dctx + (long long)k * g.n_pad + g.off[l] + pr * w + pc);
-  }
-  const float gt = __ldg(gsyn + q) + rate_scale * gr;
+  const float gt = __ldg(gsyn + q) + rate_scale * __ldg(grate + q);
   if (grad_out) {
     long long fo = 0;
     for (int k = 0; k < l; ++k) fo += (long long)g.h[k] * g.w[k];
@@ -245,15 +218,14 @@ __global__ void __launch_bounds__(256) k_latent_update(Geo g, const int2* __rest
   }
 }
 
-cudaError_t latent_update(const Geo& g, const Arch& a, const int2* d_offsets,
-                          const float* gsyn, const float* gself, const float* dctx,
-                          float rate_scale, float* y, float* m, float* v, float* grad_out,
-                          bool apply, float lr, const IterScalars* sc, cudaStream_t st) {
+cudaError_t latent_update(const Geo& g, const float* gsyn, const float* grate, float rate_scale,
+                          float* y, float* m, float* v, float* grad_out, bool apply, float lr,
+                          const IterScalars* sc, cudaStream_t st) {
   int maxn = 0;
   for (int l = 0; l < kLevels; ++l) maxn = g.h[l] * g.w[l] > maxn ? g.h[l] * g.w[l] : maxn;
   dim3 grid((maxn + 255) / 256, kLevels);
-  return launch_k(k_latent_update, grid, dim3(256), 0, st, g, d_offsets, a.N, gsyn, gself, dctx,
-                  rate_scale, y, m, v, grad_out, apply ? 1 : 0, lr, sc);
+  return launch_k(k_latent_update, grid, dim3(256), 0, st, g, gsyn, grate, rate_scale, y, m, v,
+                  grad_out, apply ? 1 : 0, lr, sc);
 }
 
 __global__ void __launch_bounds__(256) k_finish(const float* part_d, int nd,
@@ -286,7 +258,14 @@ __global__ void __launch_bounds__(256) k_finish(const float* part_d, int nd,
     e[0] = D;
     e[1] = R;
     e[2] = D + lam * R;
-    if (advance) sc->t = t + 1;
+    if (advance) {
+      const double b1 = sc->b1t * 0.9, b2 = sc->b2t * 0.999;   // beta^(t+1)
+      sc->t = t + 1;
+      sc->b1t = b1;
+      sc->b2t = b2;
+      sc->inv_bc1 = (float)(1.0 / (1.0 - b1 * 0.9));             // step t + 2
+      sc->inv_sqrt_bc2 = (float)(1.0 / sqrt(1.0 - b2 * 0.999));
+    }
   }
 }
 
@@ -318,6 +297,44 @@ cudaError_t image_to_planar(const uint8_t* rgb_hwc, float* x, int H, int W, cuda
   return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(256) k_ctx_gather(Geo g, const int2* __restrict__ offs, int N,
+                                                    float* gself, const float* __restrict__ dctx) {
+  pdl_wait();
+  pdl_trigger();
+  const int l = blockIdx.y;
+  const int w = g.w[l], h = g.h[l];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= h * w) return;
+  const int r = i / w, c = i - r * w;
+  const long long q = g.off[l] + i;
+  float gr = gself[q];
+  for (int k = 0; k < N; ++k) {
+    const int2 o = __ldg(offs + k);
+    const int pr = r - o.x, pc = c - o.y;
+    if (pr < h && pc >= 0 && pc < w)
+      gr += __ldg(dctx + (long long)k * g.n_pad + g.off[l] + pr * w + pc);
+  }
+  gself[q] = gr;
+}
+
+cudaError_t ctx_gather(const Geo& g, const int2* d_offsets, int N, float* gself,
+                       const float* dctx, cudaStream_t st) {
+  int maxn = 0;
+  for (int l = 0; l < kLevels; ++l) maxn = g.h[l] * g.w[l] > maxn ? g.h[l] * g.w[l] : maxn;
+  k_ctx_gather<<<dim3((maxn + 255) / 256, kLevels), 256, 0, st>>>(g, d_offsets, N, gself, dctx);
+  return cudaGetLastError();
+}
+
+IterScalars iter_scalars_at(int t) {
+  IterScalars s{};
+  s.t = t;
+  s.b1t = pow(0.9, (double)t);
+  s.b2t = pow(0.999, (double)t);
+  s.inv_bc1 = (float)(1.0 / (1.0 - s.b1t * 0.9));
+  s.inv_sqrt_bc2 = (float)(1.0 / sqrt(1.0 - s.b2t * 0.999));
+  return s;
+}
+
 bool pdl_enabled() {
   static const bool on = [] {
     const char* e = getenv("CC_PDL");
@@ -327,3 +344,20 @@ bool pdl_enabled() {
 }
 
 }  // namespace cc
+
+#ifdef CC_TRACE
+// Traced build only: copies up to max_n records of the kernel-start trace to host memory
+// (TraceRec layout) and resets it; returns the number of records written since the last
+// reset.
+extern "C" int cc_trace_dump(void* host, int max_n) {
+  unsigned n = 0;
+  if (cudaMemcpyFromSymbol(&n, cc::g_trace_n, sizeof(unsigned)) != cudaSuccess) return -1;
+  int m = (int)(n < (unsigned)max_n ? n : (unsigned)max_n);
+  if (m > cc::kTraceCap) m = cc::kTraceCap;
+  if (m > 0 && cudaMemcpyFromSymbol(host, cc::g_trace, (size_t)m * sizeof(cc::TraceRec)) != cudaSuccess)
+    return -1;
+  const unsigned z = 0;
+  if (cudaMemcpyToSymbol(cc::g_trace_n, &z, sizeof(unsigned)) != cudaSuccess) return -1;
+  return (int)n;
+}
+#endif

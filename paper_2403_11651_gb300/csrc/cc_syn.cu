@@ -382,18 +382,55 @@ __device__ __forceinline__ void tile_xy(const SynTileGeo& t, int tile, int& y0, 
   x0 = (tile - ty * t.ntx) * kSTX;
 }
 
-// s[ci * kSHS + r * kSHX + c] = h[ci][clamp(y0 - 1 + r)][clamp(x0 - 1 + c)]
-__device__ __forceinline__ void load_halo3(float* s, const float* __restrict__ h, int y0, int x0,
-                                           int H, int W) {
-  const int HW = H * W;
-  constexpr int n = kSHR * (kSTX + 2);
-  for (int i = threadIdx.x; i < 3 * n; i += kSTY * kSTX) {
-    const int ci = i / n, rc = i - ci * n;
-    const int r = rc / (kSTX + 2), c = rc - r * (kSTX + 2);
-    const int gy = clampi(y0 - 1 + r, 0, H - 1), gx = clampi(x0 - 1 + c, 0, W - 1);
-    s[ci * kSHS + r * kSHX + c] = __ldg(h + ci * HW + gy * W + gx);
+// A thread's share of a halo tile load: elements i = threadIdx.x + 256 k of the
+// 3 x kSHR x (kSTX + 2) halo, with their shared-memory index and their offset from the
+// tile's first pixel in a [3][H][W] plane set, computed once per kernel.  Tiles whose halo
+// lies inside the image load at base + offset; border tiles clamp each coordinate.  The
+// values pass through registers so that a kernel can issue the next tile's loads before
+// it computes the current one.
+constexpr int kHaloN = 3 * kSHR * (kSTX + 2);
+constexpr int kHaloK = (kHaloN + 255) / 256;
+struct HaloPlan {
+  int sidx[kHaloK];   // -1: no element for this thread
+  int goff[kHaloK];
+  int H, W;
+  __device__ __forceinline__ void init(int H_, int W_) {
+    H = H_;
+    W = W_;
+#pragma unroll
+    for (int k = 0; k < kHaloK; ++k) {
+      const int i = threadIdx.x + 256 * k;
+      const int n = kSHR * (kSTX + 2);
+      const int ci = i / n, rc = i - ci * n;
+      const int r = rc / (kSTX + 2), c = rc - r * (kSTX + 2);
+      sidx[k] = i < kHaloN ? ci * kSHS + r * kSHX + c : -1;
+      goff[k] = ci * H * W + (r - 1) * W + (c - 1);
+    }
   }
-}
+  __device__ __forceinline__ void load(float (&v)[kHaloK], const float* __restrict__ h, int y0,
+                                       int x0) const {
+    if (y0 >= 1 && x0 >= 1 && y0 + kSTY < H && x0 + kSTX < W) {
+      const float* base = h + y0 * W + x0;
+#pragma unroll
+      for (int k = 0; k < kHaloK; ++k) v[k] = sidx[k] >= 0 ? __ldg(base + goff[k]) : 0.f;
+      return;
+    }
+#pragma unroll
+    for (int k = 0; k < kHaloK; ++k) {
+      const int i = threadIdx.x + 256 * k;
+      const int n = kSHR * (kSTX + 2);
+      const int ci = i / n, rc = i - ci * n;
+      const int r = rc / (kSTX + 2), c = rc - r * (kSTX + 2);
+      const int gy = clampi(y0 - 1 + r, 0, H - 1), gx = clampi(x0 - 1 + c, 0, W - 1);
+      v[k] = sidx[k] >= 0 ? __ldg(h + ci * H * W + gy * W + gx) : 0.f;
+    }
+  }
+  __device__ __forceinline__ void store(float* s, const float (&v)[kHaloK]) const {
+#pragma unroll
+    for (int k = 0; k < kHaloK; ++k)
+      if (sidx[k] >= 0) s[sidx[k]] = v[k];
+  }
+};
 
 // the 27 inputs of pixel (ty, tx) of the tile: v[ci * 9 + (dy + 1) * 3 + dx + 1]
 __device__ __forceinline__ void gather_halo(float (&v)[27], const float* s, int ty, int tx) {
@@ -528,11 +565,24 @@ __global__ void __launch_bounds__(256) k_conv3_fwd(ConvArgs a) {
   __shared__ float s_h[3 * kSHS];
   const int HW = a.t.H * a.t.W;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  HaloPlan hp;
+  hp.init(a.t.H, a.t.W);
+  float nv[kHaloK];
+  if (blockIdx.x < a.t.n_tiles) {
+    int y0, x0;
+    tile_xy(a.t, blockIdx.x, y0, x0);
+    hp.load(nv, a.hin, y0, x0);
+  }
   for (int tile = blockIdx.x; tile < a.t.n_tiles; tile += gridDim.x) {
     int y0, x0;
     tile_xy(a.t, tile, y0, x0);
-    load_halo3(s_h, a.hin, y0, x0, a.t.H, a.t.W);
+    hp.store(s_h, nv);
     __syncthreads();
+    if (tile + (int)gridDim.x < a.t.n_tiles) {
+      int ny0, nx0;
+      tile_xy(a.t, tile + gridDim.x, ny0, nx0);
+      hp.load(nv, a.hin, ny0, nx0);
+    }
     const int y = y0 + ty, x = x0 + tx;
     if (y < a.t.H && x < a.t.W) {
       float v[27], z[3];
@@ -548,7 +598,7 @@ __global__ void __launch_bounds__(256) k_conv3_fwd(ConvArgs a) {
 // Last layer I (linear): x_hat = h_in + conv(h_in) + b, the distortion partial sum of
 // (x_hat - x)^2, dL/dx_hat = 2 (x_hat - x) / (3HW), and the layer's weight gradient.
 template <int I>
-__global__ void __launch_bounds__(256) k_conv3_last(ConvArgs a) {
+__global__ void __launch_bounds__(256, 3) k_conv3_last(ConvArgs a) {
   pdl_wait();
   pdl_trigger();
   __shared__ float s_all[kWG * 84];   // halo tile + dz, then the reduction
@@ -561,11 +611,24 @@ __global__ void __launch_bounds__(256) k_conv3_last(ConvArgs a) {
   float wacc[30];
 #pragma unroll
   for (int k = 0; k < 30; ++k) wacc[k] = 0.f;
+  HaloPlan hp;
+  hp.init(a.t.H, a.t.W);
+  float nv[kHaloK];
+  if (blockIdx.x < a.t.n_tiles) {
+    int y0, x0;
+    tile_xy(a.t, blockIdx.x, y0, x0);
+    hp.load(nv, a.hin, y0, x0);
+  }
   for (int tile = blockIdx.x; tile < a.t.n_tiles; tile += gridDim.x) {
     int y0, x0;
     tile_xy(a.t, tile, y0, x0);
-    load_halo3(s_h, a.hin, y0, x0, a.t.H, a.t.W);
+    hp.store(s_h, nv);
     __syncthreads();
+    if (tile + (int)gridDim.x < a.t.n_tiles) {
+      int ny0, nx0;
+      tile_xy(a.t, tile + gridDim.x, ny0, nx0);
+      hp.load(nv, a.hin, ny0, nx0);
+    }
     const int y = y0 + ty, x = x0 + tx;
     const bool valid = y < a.t.H && x < a.t.W;
     float v[27], z[3];
@@ -597,7 +660,7 @@ __global__ void __launch_bounds__(256) k_conv3_last(ConvArgs a) {
 // NR = 2: gradient of layer 1's input, dh = g + conv_1^T(g) (layer 1 is linear, so g is
 // also its pre-activation gradient); layer 0's pre-activation gradient dz = [z_0 > 0] dh
 // with z_0 recomputed from h_0; layer 0's weight gradient.
-__global__ void __launch_bounds__(256) k_conv3_mid(ConvArgs a) {
+__global__ void __launch_bounds__(256, 3) k_conv3_mid(ConvArgs a) {
   pdl_wait();
   pdl_trigger();
   __shared__ float s_all[kWG * 84];   // two halo tiles + dz, then the reduction
@@ -609,12 +672,27 @@ __global__ void __launch_bounds__(256) k_conv3_mid(ConvArgs a) {
   float wacc[30];
 #pragma unroll
   for (int k = 0; k < 30; ++k) wacc[k] = 0.f;
+  HaloPlan hp;
+  hp.init(a.t.H, a.t.W);
+  float nvg[kHaloK], nvh[kHaloK];
+  if (blockIdx.x < a.t.n_tiles) {
+    int y0, x0;
+    tile_xy(a.t, blockIdx.x, y0, x0);
+    hp.load(nvg, a.g, y0, x0);
+    hp.load(nvh, a.hin, y0, x0);
+  }
   for (int tile = blockIdx.x; tile < a.t.n_tiles; tile += gridDim.x) {
     int y0, x0;
     tile_xy(a.t, tile, y0, x0);
-    load_halo3(s_g, a.g, y0, x0, a.t.H, a.t.W);
-    load_halo3(s_h, a.hin, y0, x0, a.t.H, a.t.W);
+    hp.store(s_g, nvg);
+    hp.store(s_h, nvh);
     __syncthreads();
+    if (tile + (int)gridDim.x < a.t.n_tiles) {
+      int ny0, nx0;
+      tile_xy(a.t, tile + gridDim.x, ny0, nx0);
+      hp.load(nvg, a.g, ny0, nx0);
+      hp.load(nvh, a.hin, ny0, nx0);
+    }
     const int y = y0 + ty, x = x0 + tx;
     const bool valid = y < a.t.H && x < a.t.W;
     float dz[3] = {0.f, 0.f, 0.f};
@@ -754,11 +832,24 @@ __global__ void __launch_bounds__(256, 2) k_syn1x1_bwd(Syn1x1Args a) {
   const float2* wab = reinterpret_cast<const float2*>(c_synb + Wt::WAT);
   const float2* wbb = reinterpret_cast<const float2*>(c_synb + Wt::WBR);
   const int tx = tid & 31, ty = tid >> 5;
+  HaloPlan hp;
+  hp.init(a.t.H, a.t.W);
+  float nv[kHaloK];
+  if (blockIdx.x < a.t.n_tiles) {
+    int y0, x0;
+    tile_xy(a.t, blockIdx.x, y0, x0);
+    hp.load(nv, a.dz0, y0, x0);
+  }
   for (int tile = blockIdx.x; tile < a.t.n_tiles; tile += gridDim.x) {
     int y0, x0;
     tile_xy(a.t, tile, y0, x0);
-    load_halo3(s_halo, a.dz0, y0, x0, a.t.H, a.t.W);
+    hp.store(s_halo, nv);
     __syncthreads();
+    if (tile + (int)gridDim.x < a.t.n_tiles) {
+      int ny0, nx0;
+      tile_xy(a.t, tile + gridDim.x, ny0, nx0);
+      hp.load(nv, a.dz0, ny0, nx0);
+    }
     const int y = y0 + ty, x = x0 + tx;
     const bool valid = y < a.t.H && x < a.t.W;
     const int p = valid ? y * a.t.W + x : 0;
