@@ -5,16 +5,25 @@
 // two outputs are the mean mu and log-scale s of a Laplace law, and the rate of a latent
 // is -log2 P(y_hat) with P the mass of [y_hat - 1/2, y_hat + 1/2] (eq. (1)).
 //
-// One thread owns one latent.  The weights live in a __constant__ bank refreshed before
-// every pass, so every multiply-add of the forward and input-gradient passes takes its
-// weight straight from the constant cache (all lanes read the same weight at once).  The
-// weight gradients, sum over latents of dz (x) input, are contracted per tile of 128
-// latents from shared memory: each thread owns an RB x RB block of one weight matrix
-// for one interleaved quarter of the tile's latents and keeps it in registers for the
-// whole persistent loop, so a CTA writes one partial sum per parameter at the end.
-// Every sum has a fixed order, so results are bit-reproducible on a given device.
+// One thread owns one latent; a tile is 128 latents of one level (kArmTile).  The weights
+// live in a __constant__ bank refreshed before every pass.
+//
+// Forward and backward (the encoder iteration), k_arm_tc: the N x N layers of the forward
+// pass (z = W h + b) and of the input gradient (dh += W^T dz) run on the tensor cores
+// (tcgen05.mma kind::tf32 with operands split into TF32 high and low parts, FP32
+// accumulation in tensor memory, cc_tc.cuh): M = the 128 latents of the tile, N = the
+// layer width padded to a multiple of 16, K = N.  Each thread writes its latent's row of
+// the A operand to shared memory and reads its row of the result back from its lane of
+// the tensor memory.  The output layer (N -> 2), the Laplace rate and the weight gradients
+// (sums over latents of dz (x) input: RB x RB register blocks of packed FP32 pairs over
+// fp32 rows in shared memory, kept in registers over the CTA's tiles) run on the CUDA
+// cores.  Every sum has a fixed order, so results are bit-reproducible on a given device.
+//
+// Forward only (rate of a pass without gradients), k_arm_fwd: every layer on the CUDA
+// cores, weights as constant-bank operands in packed FP32 pairs.
 #include "cc_internal.cuh"
 #include "cc_laplace.cuh"
+#include "cc_tc.cuh"
 
 namespace cc {
 
@@ -43,6 +52,7 @@ struct ArmArgs {
   float* part_bits;  // [gridDim.x]
   const int2* tiles; // (level, first latent of the tile within the level)
   int n_tiles;
+  int* fault;        // set when a tensor-core wait gives up
   Geo g;
 };
 
@@ -76,346 +86,425 @@ __device__ __forceinline__ void store_row(float* p, const float (&v)[N]) {
     *reinterpret_cast<float4*>(p + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
 }
 
-template <int N, int NL, int LPT>
-struct ArmShape {
-  static constexpr int S = N + 4;               // smem row stride (conflict-free float4 rows)
+// The N causal neighbours of latent td.y + tid of the tile and the latent itself, read
+// from the zero-bordered plane (every neighbour is inside the allocation; outside the grid
+// it reads the zero border).  Returns whether the latent exists.
+template <int N>
+__device__ __forceinline__ bool gather_context(const ArmArgs& a, int2 td, int tid,
+                                               float (&h)[N], float& yq) {
+  const int l = td.x;
+  const int w = a.g.w[l];
+  const int i = td.y + tid;
+  const bool valid = i < a.g.h[l] * w;
+  int r = 0, c = 0;
+  if (valid) { r = i / w; c = i - r * w; }
+  const int pw = a.g.pw[l];
+  const float* ctr = a.yhat + a.g.poff[l] + (long long)(r + kCtxPad) * pw + c + kCtxPad;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const int2 o = c_off[k];
+    h[k] = valid ? __ldg(ctr + o.x * pw + o.y) : 0.f;
+  }
+  yq = valid ? __ldg(ctr) : 0.f;
+  return valid;
+}
+
+// (mu, s) = W_out h + b_out as one packed pair; the forward bank stores W_out as
+// (W_out[0][k], W_out[1][k])
+template <int N, int NL>
+__device__ __forceinline__ float2 output_layer(const float (&h)[N]) {
+  constexpr int OW = NL * (N * N + N), OB = OW + 2 * N;
+  const float2* wo = reinterpret_cast<const float2*>(c_arm + OW);
+  float2 ms = make_float2(c_arm[OB], c_arm[OB + 1]);
+#pragma unroll
+  for (int k = 0; k < N; ++k) ms = __ffma2_rn(wo[k], make_float2(h[k], h[k]), ms);
+  return ms;
+}
+
+// ------------------------------------------------------------ forward only (CUDA cores)
+
+template <int N, int NL>
+__global__ void __launch_bounds__(kArmTile) k_arm_fwd(ArmArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int LW = N * N + N;
+  const int tid = threadIdx.x;
+  float bits_acc = 0.f;
+  for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+    const int2 td = a.tiles[tile];
+    float h[N], yq;
+    const bool valid = gather_context<N>(a, td, tid, h, yq);
+#pragma unroll
+    for (int L = 0; L < NL; ++L) {
+      // packed FP32 pairs: (z[2m], z[2m+1]) += (W[2m][k], W[2m+1][k]) * (h[k], h[k]); the
+      // forward bank stores every layer's weights in those pairs, input k innermost
+      float2 zp[N / 2];
+      const float2* wp = reinterpret_cast<const float2*>(c_arm + L * LW);
+#pragma unroll
+      for (int m = 0; m < N / 2; ++m) zp[m] = wp[N * N / 2 + m];   // bias pair
+#pragma unroll
+      for (int m = 0; m < N / 2; ++m)
+#pragma unroll
+        for (int k = 0; k < N; ++k) zp[m] = __ffma2_rn(wp[m * N + k], make_float2(h[k], h[k]), zp[m]);
+#pragma unroll
+      for (int m = 0; m < N / 2; ++m) {
+        h[2 * m] += fmaxf(zp[m].x, 0.f);
+        h[2 * m + 1] += fmaxf(zp[m].y, 0.f);
+      }
+    }
+    const float2 ms = output_layer<N, NL>(h);
+    const LapOut lo = laplace_bits(yq, ms.x, ms.y);
+    if (valid) bits_acc += lo.bits;
+  }
+  float v = bits_acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __shared__ float s_bits[kArmTile / 32];
+  if ((tid & 31) == 0) s_bits[tid >> 5] = v;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < kArmTile / 32; ++k) t += s_bits[k];
+    a.part_bits[blockIdx.x] = t;
+  }
+}
+
+// ------------------------------------------------------------ forward + backward (tensor cores)
+
+template <int N, int NL>
+struct ArmTcShape {
+  static constexpr int T = kArmTile;            // latents per tile = threads per CTA
+  static constexpr int NP = (N + 15) / 16 * 16; // MMA N: the layer width padded
+  static constexpr int KS = N / 8;              // K steps of 8
   static constexpr int LW = N * N + N;          // floats per LinR layer (W then b)
   static constexpr int OW = NL * LW;            // W_out
   static constexpr int OB = OW + 2 * N;         // b_out
-  static constexpr int NP = OB + 2;             // ARM parameters
-  static constexpr int T = kArmTile;            // latents per tile
-  static constexpr int TT = kArmTile / LPT;     // threads per CTA
-  // per-layer arrays are LS floats apart: T*S plus an 8-float skew, so that the same row
-  // of two layers falls in different shared-memory banks
-  static constexpr int LS = T * S + 8;
-  static constexpr int tile_floats = 2 * NL * LS + T * S + 2 * T;
+  static constexpr int NP_ARM = OB + 2;         // ARM parameters
+  static constexpr int S = N;                   // fp32 row stride of the weight-gradient rows
+  static constexpr int LS = T * S + 8;          // per-layer arrays (8-float bank skew)
+  // bytes: A operand (hi, lo), then per layer W (hi, lo) and W^T (hi, lo), NP rows each
+  static constexpr int A_BYTES = T * N * 4;
+  static constexpr int W_BYTES = NP * N * 4;
+  static constexpr int TC_BYTES = 2 * A_BYTES + NL * 4 * W_BYTES;
+  // floats after the operands: s_in [NL][LS], s_dz [NL][LS], s_ho [T][S], s_do [T][2]
+  static constexpr int F_FLOATS = 2 * NL * LS + T * S + 2 * T;
   static constexpr int NBLK = NL * ArmBlocking<N>::NB * ArmBlocking<N>::NB;
-  static constexpr int G = TT / NBLK;           // interleaved latent groups
+  static constexpr int G = T / NBLK;            // interleaved latent groups
   static constexpr int NCH_B = NL * N / 4;      // bias chunks of 4
   static constexpr int NCH = NCH_B + N / 4;     // + W_out column chunks (b_out rides on #0)
   static constexpr int XPER = (NCH + NBLK - 1) / NBLK;
-  static constexpr int red_floats = G * NP;
-  static constexpr int smem_floats = tile_floats > red_floats ? tile_floats : red_floats;
-  static_assert(TT % NBLK == 0 && G >= 1, "threads must split evenly into weight blocks");
+  static constexpr int RED_FLOATS = G * NP_ARM;
+  static constexpr int BYTES_MAIN = TC_BYTES + F_FLOATS * 4;
+  static constexpr int BYTES = (BYTES_MAIN > RED_FLOATS * 4 ? BYTES_MAIN : RED_FLOATS * 4) + 16;
+  static constexpr uint32_t TMEM_COLS = 32;
+  static_assert(T % NBLK == 0 && G >= 1, "threads must split evenly into weight blocks");
+  static_assert(N % 8 == 0 && NP <= 32, "tensor-core ARM widths: 8, 16, 24");
 };
 
-// LPT latents per thread: thread t owns latents t, t + TT, ... of the tile, so each weight
-// operand taken from the constant bank feeds LPT multiply-adds.
-// CTAs per SM of the ARM kernels (one tile of kArmTile latents per CTA): one CTA of 12
-// warps for the wider ARMs keeps every warp of an SM in the same phase of the tile, so
-// they share the instruction stream of the fully unrolled layer code.
-template <int N>
-struct ArmOcc {
-  static constexpr int blocks = N >= 16 ? 1 : 2;
-};
+// wait budget of a tensor-core phase (SM clocks, about half a second)
+constexpr long long kTcWaitCycles = 1ll << 30;
 
-template <int N, int NL, bool BWD, int LPT>
-__global__ void __launch_bounds__(kArmTile / LPT, ArmOcc<N>::blocks) k_arm(ArmArgs a) {
+template <int N, int NL>
+__global__ void __launch_bounds__(kArmTile, 2) k_arm_tc(ArmArgs a) {
   pdl_wait();
   pdl_trigger();
-  using Sh = ArmShape<N, NL, LPT>;
-  constexpr int S = Sh::S, LW = Sh::LW, OW = Sh::OW, OB = Sh::OB, NP = Sh::NP, T = Sh::T;
-  constexpr int LS = Sh::LS, TT = Sh::TT;
+  using Sh = ArmTcShape<N, NL>;
+  constexpr int T = Sh::T, NP = Sh::NP, KS = Sh::KS, LW = Sh::LW, OW = Sh::OW, OB = Sh::OB;
+  constexpr int S = Sh::S, LS = Sh::LS, NPA = Sh::NP_ARM;
   constexpr int RB = ArmBlocking<N>::RB, NB = ArmBlocking<N>::NB;
-  constexpr int NBLK = Sh::NBLK, G = Sh::G, NCH_B = Sh::NCH_B, NCH = Sh::NCH;
-  constexpr int XPER = Sh::XPER;
+  constexpr int NBLK = Sh::NBLK, G = Sh::G, NCH_B = Sh::NCH_B, NCH = Sh::NCH, XPER = Sh::XPER;
+  constexpr uint32_t SBO_A = (N / 4) * 128;
+  constexpr uint32_t IDESC = tc_idesc_tf32(T, NP);
 
-  extern __shared__ float4 smem4[];
-  float* sm = reinterpret_cast<float*>(smem4);
-  float* s_in = sm;                    // [NL][T][S] input of LinR layer L (layer stride LS)
-  float* s_dz = s_in + NL * LS;        // [NL][T][S] dz of LinR layer L (layer stride LS)
-  float* s_ho = s_dz + NL * LS;        // [T][S]     input of the output layer
-  float* s_do = s_ho + T * S;          // [T][2]     (d bits/d mu, d bits/d s)
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sA_hi = smem;
+  unsigned char* sA_lo = sA_hi + Sh::A_BYTES;
+  unsigned char* sW = sA_lo + Sh::A_BYTES;   // [L][W hi, W lo, W^T hi, W^T lo]
+  float* sf = reinterpret_cast<float*>(smem + Sh::TC_BYTES);
+  float* s_in = sf;                  // [NL][T][S] input of LinR layer L (layer stride LS)
+  float* s_dz = s_in + NL * LS;      // [NL][T][S] dz of LinR layer L
+  float* s_ho = s_dz + NL * LS;      // [T][S]     input of the output layer
+  float* s_do = s_ho + T * S;        // [T][2]     (d bits/d mu, d bits/d s)
+  __shared__ __align__(8) uint64_t s_mbar;
+  __shared__ uint32_t s_tmem;
 
   const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  // weights as B operands: W (K = input, rows = outputs) and W^T, split into TF32 parts;
+  // rows N .. NP-1 are zero
+  for (int i = tid; i < NL * NP * N; i += T) {
+    const int L = i / (NP * N), rk = i - L * NP * N, row = rk / N, k = rk - row * N;
+    const float wf = row < N ? c_armb[L * LW + row * N + k] : 0.f;   // W[row][k]
+    const float wt = row < N ? c_armb[L * LW + k * N + row] : 0.f;   // W^T[row][k] = W[k][row]
+    const float fh = tf32_hi(wf), th = tf32_hi(wt);
+    unsigned char* base = sW + L * 4 * Sh::W_BYTES;
+    const int off = tc_off(row, k, N);
+    *reinterpret_cast<float*>(base + off) = fh;
+    *reinterpret_cast<float*>(base + Sh::W_BYTES + off) = wf - fh;
+    *reinterpret_cast<float*>(base + 2 * Sh::W_BYTES + off) = th;
+    *reinterpret_cast<float*>(base + 3 * Sh::W_BYTES + off) = wt - th;
+  }
+  if (tid == 0) mbar_init(smem_u32(&s_mbar), 1);
+  if (warp == 0) tc_alloc(smem_u32(&s_tmem), Sh::TMEM_COLS);
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's lanes
+  const uint32_t mbar = smem_u32(&s_mbar);
+  uint32_t phase = 0;
+
+  // Stage the A operand (this thread's row, split), run D = A B^T for B = layer L's W
+  // (transpose = false) or W^T (true), and return this thread's row of D.  False when a
+  // wait gave up (the CTA then stops).
+  auto layer_mma = [&](const float (&x)[N], int L, bool transpose, float (&d)[NP]) -> bool {
+#pragma unroll
+    for (int k = 0; k < N; k += 4) {
+      const float4 hi = make_float4(tf32_hi(x[k]), tf32_hi(x[k + 1]), tf32_hi(x[k + 2]),
+                                    tf32_hi(x[k + 3]));
+      const float4 lo = make_float4(x[k] - hi.x, x[k + 1] - hi.y, x[k + 2] - hi.z, x[k + 3] - hi.w);
+      *reinterpret_cast<float4*>(sA_hi + tc_off(tid, k, N)) = hi;
+      *reinterpret_cast<float4*>(sA_lo + tc_off(tid, k, N)) = lo;
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t ah = smem_u32(sA_hi), al = smem_u32(sA_lo);
+      const uint32_t wb = smem_u32(sW + L * 4 * Sh::W_BYTES + (transpose ? 2 : 0) * Sh::W_BYTES);
+      const uint32_t bh = wb, bl = wb + Sh::W_BYTES;
+#pragma unroll
+      for (int s = 0; s < KS; ++s) {
+        const uint32_t ko = (uint32_t)s * 256u;
+        tc_mma_tf32(tmem, tc_desc(ah + ko, SBO_A), tc_desc(bh + ko, SBO_A), IDESC, s > 0 ? 1u : 0u);
+        tc_mma_tf32(tmem, tc_desc(ah + ko, SBO_A), tc_desc(bl + ko, SBO_A), IDESC, 1u);
+        tc_mma_tf32(tmem, tc_desc(al + ko, SBO_A), tc_desc(bh + ko, SBO_A), IDESC, 1u);
+      }
+      tc_commit(mbar);
+    }
+    const bool ok = mbar_wait(mbar, phase, kTcWaitCycles);
+    phase ^= 1u;
+    if (__syncthreads_or(ok ? 0 : 1)) return false;   // every thread takes the same branch
+    tc_fence_after();
+    tc_ld_row<NP>(t_row, d);
+    return true;
+  };
+
+  float2 acc[RB][RB / 2];   // weight-gradient block as packed pairs along its columns
+  float xacc[XPER][10];
+#pragma unroll
+  for (int r = 0; r < RB; ++r)
+#pragma unroll
+    for (int c = 0; c < RB / 2; ++c) acc[r][c] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < XPER; ++q)
+#pragma unroll
+    for (int e = 0; e < 10; ++e) xacc[q][e] = 0.f;
   const int unit = tid % NBLK, grp = tid / NBLK;
   const int uL = unit / (NB * NB), urb = (unit / NB) % NB, ucb = unit % NB;
-
-  // weight-gradient block as packed pairs along its columns
-  float2 acc[RB][RB / 2];
-  float xacc[XPER][10];
-  if constexpr (BWD) {
-#pragma unroll
-    for (int r = 0; r < RB; ++r)
-#pragma unroll
-      for (int c = 0; c < RB / 2; ++c) acc[r][c] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int q = 0; q < XPER; ++q)
-#pragma unroll
-      for (int e = 0; e < 10; ++e) xacc[q][e] = 0.f;
-  }
   float bits_acc = 0.f;
+  bool ok = true;
 
-  for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
-    const int2 td = a.tiles[tile];
-    const int l = td.x;
-    const int w = a.g.w[l];
-    const int n_l = a.g.h[l] * w;
-    const int pw = a.g.pw[l];
-    // zero-bordered plane: every causal neighbour is inside the allocation, outside the
-    // grid it reads the zero border
-    bool valid[LPT];
-    float h[LPT][N], yq[LPT];
+  // the context of the CTA's next tile is loaded while the current one is computed
+  float nh[N], nyq = 0.f;
+  bool nvalid = false;
+  int2 ntd = make_int2(0, 0);
+  if (blockIdx.x < a.n_tiles) {
+    ntd = a.tiles[blockIdx.x];
+    nvalid = gather_context<N>(a, ntd, tid, nh, nyq);
+  }
+  for (int tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
+    const int2 td = ntd;
+    float h[N];
 #pragma unroll
-    for (int q = 0; q < LPT; ++q) {
-      const int i = td.y + tid + q * TT;
-      valid[q] = i < n_l;
-      int r = 0, c = 0;
-      if (valid[q]) { r = i / w; c = i - r * w; }
-      const float* ctr = a.yhat + a.g.poff[l] + (long long)(r + kCtxPad) * pw + c + kCtxPad;
-#pragma unroll
-      for (int k = 0; k < N; ++k) {
-        const int2 o = c_off[k];
-        h[q][k] = valid[q] ? __ldg(ctr + o.x * pw + o.y) : 0.f;
-      }
-      yq[q] = valid[q] ? __ldg(ctr) : 0.f;
+    for (int k = 0; k < N; ++k) h[k] = nh[k];
+    const float yq = nyq;
+    const bool valid = nvalid;
+    if (tile + (int)gridDim.x < a.n_tiles) {
+      ntd = a.tiles[tile + gridDim.x];
+      nvalid = gather_context<N>(a, ntd, tid, nh, nyq);
     }
 
     // forward: h <- h + relu(W h + b), NL times
-    uint32_t mask[LPT][NL];
+    uint32_t mask[NL];
 #pragma unroll
     for (int L = 0; L < NL; ++L) {
-      if constexpr (BWD) {
+      store_row<N>(s_in + L * LS + tid * S, h);
+      float z[NP];
+      if (!layer_mma(h, L, false, z)) { ok = false; break; }
+      uint32_t mk = 0;
 #pragma unroll
-        for (int q = 0; q < LPT; ++q) store_row<N>(s_in + L * LS + (tid + q * TT) * S, h[q]);
+      for (int o = 0; o < N; ++o) {
+        const float zo = z[o] + c_armb[L * LW + N * N + o];
+        mk |= (zo > 0.f ? 1u : 0u) << o;
+        h[o] += fmaxf(zo, 0.f);
       }
-      // packed FP32 pairs: (z[2m], z[2m+1]) += (W[2m][k], W[2m+1][k]) * (h[k], h[k]); the
-      // forward bank stores every layer's weights in those pairs, input k innermost, so
-      // consecutive multiply-adds use adjacent weights
-      float2 zp[LPT][N / 2];
-      {
-        float2 hd[LPT][N];
-#pragma unroll
-        for (int q = 0; q < LPT; ++q)
-#pragma unroll
-          for (int k = 0; k < N; ++k) hd[q][k] = make_float2(h[q][k], h[q][k]);
-        const float2* wp = reinterpret_cast<const float2*>(c_arm + L * LW);
-#pragma unroll
-        for (int m = 0; m < N / 2; ++m)
-#pragma unroll
-          for (int q = 0; q < LPT; ++q) zp[q][m] = wp[N * N / 2 + m];   // bias pair
-#pragma unroll
-        for (int m = 0; m < N / 2; ++m)
-#pragma unroll
-          for (int k = 0; k < N; ++k)
-#pragma unroll
-            for (int q = 0; q < LPT; ++q) zp[q][m] = __ffma2_rn(wp[m * N + k], hd[q][k], zp[q][m]);
-      }
-      float z[LPT][N];
-#pragma unroll
-      for (int q = 0; q < LPT; ++q)
-#pragma unroll
-        for (int m = 0; m < N / 2; ++m) { z[q][2 * m] = zp[q][m].x; z[q][2 * m + 1] = zp[q][m].y; }
-#pragma unroll
-      for (int q = 0; q < LPT; ++q) {
-        uint32_t mk = 0;
-#pragma unroll
-        for (int o = 0; o < N; ++o) {
-          mk |= (z[q][o] > 0.f ? 1u : 0u) << o;
-          h[q][o] += fmaxf(z[q][o], 0.f);
-        }
-        mask[q][L] = mk;
-      }
+      mask[L] = mk;
     }
-    LapOut lo[LPT];
+    if (!ok) break;
+    store_row<N>(s_ho + tid * S, h);
+    const float2 ms = output_layer<N, NL>(h);
+    LapOut lo = laplace_bits(yq, ms.x, ms.y);
+    if (!valid) lo.bits = lo.g_y = lo.g_mu = lo.g_s = 0.f;
+    bits_acc += lo.bits;
+
+    // backward: dh = W_out^T (d mu, d s), then dh += W_L^T (mask_L * dh) for L = NL-1 .. 0
+    reinterpret_cast<float2*>(s_do)[tid] = make_float2(lo.g_mu, lo.g_s);
+    float dh[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      dh[k] = fmaf(c_armb[OW + k], lo.g_mu, c_armb[OW + N + k] * lo.g_s);
+#pragma unroll
+    for (int L = NL - 1; L >= 0; --L) {
+      float dz[N];
+#pragma unroll
+      for (int o = 0; o < N; ++o) dz[o] = ((mask[L] >> o) & 1u) ? dh[o] : 0.f;
+      store_row<N>(s_dz + L * LS + tid * S, dz);
+      float t[NP];
+      if (!layer_mma(dz, L, true, t)) { ok = false; break; }
+#pragma unroll
+      for (int k = 0; k < N; ++k) dh[k] += t[k];
+    }
+    if (!ok) break;
+    if (valid) {
+      const long long qq = a.g.off[td.x] + td.y + tid;
+#pragma unroll
+      for (int k = 0; k < N; ++k) a.dctx[k * a.g.n_pad + qq] = dh[k];
+      a.gself[qq] = lo.g_y;
+    }
+    __syncthreads();
+
+    // weight gradients of the LinR layers: acc += sum_p dz_L[p][rows] (x) in_L[p][cols]
     {
-      float mu[LPT], s[LPT];
-      // (mu, s) as one packed pair; the forward bank stores W_out as (W_out[0][k], W_out[1][k])
-      const float2* wo = reinterpret_cast<const float2*>(c_arm + OW);
-#pragma unroll
-      for (int q = 0; q < LPT; ++q) {
-        if constexpr (BWD) store_row<N>(s_ho + (tid + q * TT) * S, h[q]);
-        float2 ms = make_float2(c_arm[OB], c_arm[OB + 1]);
-#pragma unroll
-        for (int k = 0; k < N; ++k) ms = __ffma2_rn(wo[k], make_float2(h[q][k], h[q][k]), ms);
-        mu[q] = ms.x;
-        s[q] = ms.y;
-      }
-#pragma unroll
-      for (int q = 0; q < LPT; ++q) {
-        lo[q] = laplace_bits(yq[q], mu[q], s[q]);
-        if (!valid[q]) lo[q].bits = lo[q].g_y = lo[q].g_mu = lo[q].g_s = 0.f;
-        bits_acc += lo[q].bits;
-      }
-    }
-
-    if constexpr (BWD) {
-      // packed pairs over inputs: (dh[k], dh[k+1]) += (W[o][k], W[o][k+1]) * (dz[o], dz[o]),
-      // read from the row-major copy of the weights (adjacent along k)
-      float2 dhp[LPT][N / 2];
-#pragma unroll
-      for (int q = 0; q < LPT; ++q) {
-        reinterpret_cast<float2*>(s_do)[tid + q * TT] = make_float2(lo[q].g_mu, lo[q].g_s);
-        const float2* w0 = reinterpret_cast<const float2*>(c_armb + OW);
-        const float2* w1 = reinterpret_cast<const float2*>(c_armb + OW + N);
-        const float2 gm = make_float2(lo[q].g_mu, lo[q].g_mu), gs = make_float2(lo[q].g_s, lo[q].g_s);
-#pragma unroll
-        for (int j = 0; j < N / 2; ++j) dhp[q][j] = __ffma2_rn(w0[j], gm, __fmul2_rn(w1[j], gs));
-      }
-#pragma unroll
-      for (int L = NL - 1; L >= 0; --L) {
-        float2 dzd[LPT][N];
-#pragma unroll
-        for (int q = 0; q < LPT; ++q) {
-          float dz[N];
-#pragma unroll
-          for (int o = 0; o < N; ++o) {
-            const float dv = (o & 1) ? dhp[q][o >> 1].y : dhp[q][o >> 1].x;
-            dz[o] = ((mask[q][L] >> o) & 1u) ? dv : 0.f;
-            dzd[q][o] = make_float2(dz[o], dz[o]);
-          }
-          store_row<N>(s_dz + L * LS + (tid + q * TT) * S, dz);
-        }
-        const float2* wr = reinterpret_cast<const float2*>(c_armb + L * LW);
-#pragma unroll
-        for (int o = 0; o < N; ++o)
-#pragma unroll
-          for (int j = 0; j < N / 2; ++j)
-#pragma unroll
-            for (int q = 0; q < LPT; ++q)
-              dhp[q][j] = __ffma2_rn(wr[o * (N / 2) + j], dzd[q][o], dhp[q][j]);
-      }
-      float dh[LPT][N];
-#pragma unroll
-      for (int q = 0; q < LPT; ++q)
-#pragma unroll
-        for (int j = 0; j < N / 2; ++j) { dh[q][2 * j] = dhp[q][j].x; dh[q][2 * j + 1] = dhp[q][j].y; }
-#pragma unroll
-      for (int q = 0; q < LPT; ++q) {
-        if (valid[q]) {
-          const long long qq = a.g.off[l] + td.y + tid + q * TT;
-#pragma unroll
-          for (int k = 0; k < N; ++k) a.dctx[k * a.g.n_pad + qq] = dh[q][k];
-          a.gself[qq] = lo[q].g_y;
-        }
-      }
-      __syncthreads();
-
-      // weight gradients of the LinR layers: acc += sum_p dz_L[p][rows] (x) in_L[p][cols]
-      {
-        const float* A = s_dz + uL * LS + urb * RB;
-        const float* B = s_in + uL * LS + ucb * RB;
+      const float* A = s_dz + uL * LS + urb * RB;
+      const float* B = s_in + uL * LS + ucb * RB;
 #pragma unroll 2
-        for (int p = grp; p < T; p += G) {
-          float av[RB], bv[RB];
-          load_row<RB>(av, A + p * S);
-          load_row<RB>(bv, B + p * S);
+      for (int p = grp; p < T; p += G) {
+        float av[RB], bv[RB];
+        load_row<RB>(av, A + p * S);
+        load_row<RB>(bv, B + p * S);
 #pragma unroll
-          for (int rr = 0; rr < RB; ++rr) {
-            const float2 ad = make_float2(av[rr], av[rr]);
+        for (int rr = 0; rr < RB; ++rr) {
+          const float2 ad = make_float2(av[rr], av[rr]);
 #pragma unroll
-            for (int cc = 0; cc < RB / 2; ++cc)
-              acc[rr][cc] = __ffma2_rn(ad, make_float2(bv[2 * cc], bv[2 * cc + 1]), acc[rr][cc]);
-          }
+          for (int cc = 0; cc < RB / 2; ++cc)
+            acc[rr][cc] = __ffma2_rn(ad, make_float2(bv[2 * cc], bv[2 * cc + 1]), acc[rr][cc]);
         }
       }
-      // biases and the output layer, in chunks of four columns
-#pragma unroll
-      for (int qi = 0; qi < XPER; ++qi) {
-        const int q = unit + qi * NBLK;
-        if (q < NCH_B) {
-          const int L = q / (N / 4), i0 = (q % (N / 4)) * 4;
-          const float* A = s_dz + L * LS + i0;
-          for (int p = grp; p < T; p += G) {
-            const float4 t = *reinterpret_cast<const float4*>(A + p * S);
-            xacc[qi][0] += t.x; xacc[qi][1] += t.y; xacc[qi][2] += t.z; xacc[qi][3] += t.w;
-          }
-        } else if (q < NCH) {
-          const int j0 = (q - NCH_B) * 4;
-          for (int p = grp; p < T; p += G) {
-            const float4 t = *reinterpret_cast<const float4*>(s_ho + p * S + j0);
-            const float2 d = reinterpret_cast<const float2*>(s_do)[p];
-            xacc[qi][0] = fmaf(d.x, t.x, xacc[qi][0]); xacc[qi][1] = fmaf(d.x, t.y, xacc[qi][1]);
-            xacc[qi][2] = fmaf(d.x, t.z, xacc[qi][2]); xacc[qi][3] = fmaf(d.x, t.w, xacc[qi][3]);
-            xacc[qi][4] = fmaf(d.y, t.x, xacc[qi][4]); xacc[qi][5] = fmaf(d.y, t.y, xacc[qi][5]);
-            xacc[qi][6] = fmaf(d.y, t.z, xacc[qi][6]); xacc[qi][7] = fmaf(d.y, t.w, xacc[qi][7]);
-            xacc[qi][8] += d.x; xacc[qi][9] += d.y;
-          }
-        }
-      }
-      __syncthreads();
     }
+    // biases and the output layer, in chunks of four columns
+#pragma unroll
+    for (int qi = 0; qi < XPER; ++qi) {
+      const int q = unit + qi * NBLK;
+      if (q < NCH_B) {
+        const int L = q / (N / 4), i0 = (q % (N / 4)) * 4;
+        const float* A = s_dz + L * LS + i0;
+        for (int p = grp; p < T; p += G) {
+          const float4 t = *reinterpret_cast<const float4*>(A + p * S);
+          xacc[qi][0] += t.x; xacc[qi][1] += t.y; xacc[qi][2] += t.z; xacc[qi][3] += t.w;
+        }
+      } else if (q < NCH) {
+        const int j0 = (q - NCH_B) * 4;
+        for (int p = grp; p < T; p += G) {
+          const float4 t = *reinterpret_cast<const float4*>(s_ho + p * S + j0);
+          const float2 d = reinterpret_cast<const float2*>(s_do)[p];
+          xacc[qi][0] = fmaf(d.x, t.x, xacc[qi][0]); xacc[qi][1] = fmaf(d.x, t.y, xacc[qi][1]);
+          xacc[qi][2] = fmaf(d.x, t.z, xacc[qi][2]); xacc[qi][3] = fmaf(d.x, t.w, xacc[qi][3]);
+          xacc[qi][4] = fmaf(d.y, t.x, xacc[qi][4]); xacc[qi][5] = fmaf(d.y, t.y, xacc[qi][5]);
+          xacc[qi][6] = fmaf(d.y, t.z, xacc[qi][6]); xacc[qi][7] = fmaf(d.y, t.w, xacc[qi][7]);
+          xacc[qi][8] += d.x; xacc[qi][9] += d.y;
+        }
+      }
+    }
+    __syncthreads();
   }
+
+  if (!ok) {
+    // a tensor-core wait gave up: report, give the MMAs in flight another bounded wait,
+    // free the tensor memory and stop
+    if (tid == 0) atomicExch(a.fault, 1);
+    mbar_wait(mbar, phase ^ 1u, kTcWaitCycles);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc_dealloc(tmem, Sh::TMEM_COLS);
+    return;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc_dealloc(tmem, Sh::TMEM_COLS);
 
   // rate partial of this CTA
   {
     float v = bits_acc;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __shared__ float s_bits[TT / 32];
-    if ((tid & 31) == 0) s_bits[tid >> 5] = v;
+    __shared__ float s_bits[T / 32];
+    if ((tid & 31) == 0) s_bits[warp] = v;
     __syncthreads();
     if (tid == 0) {
       float t = 0.f;
 #pragma unroll
-      for (int k = 0; k < TT / 32; ++k) t += s_bits[k];
+      for (int k = 0; k < T / 32; ++k) t += s_bits[k];
       a.part_bits[blockIdx.x] = t;
     }
   }
-
-  if constexpr (BWD) {
-    // every (group, parameter) slot is written exactly once, then summed over groups
-    float* red = sm;
-    float* mine = red + grp * NP;
+  // every (group, parameter) slot is written exactly once, then summed over groups
+  float* red = reinterpret_cast<float*>(smem);
+  float* mine = red + grp * NPA;
 #pragma unroll
-    for (int rr = 0; rr < RB; ++rr)
+  for (int rr = 0; rr < RB; ++rr)
 #pragma unroll
-      for (int cc = 0; cc < RB; ++cc)
-        mine[uL * LW + (urb * RB + rr) * N + ucb * RB + cc] =
-            (cc & 1) ? acc[rr][cc >> 1].y : acc[rr][cc >> 1].x;
+    for (int cc = 0; cc < RB; ++cc)
+      mine[uL * LW + (urb * RB + rr) * N + ucb * RB + cc] =
+          (cc & 1) ? acc[rr][cc >> 1].y : acc[rr][cc >> 1].x;
 #pragma unroll
-    for (int qi = 0; qi < XPER; ++qi) {
-      const int q = unit + qi * NBLK;
-      if (q < NCH_B) {
-        const int L = q / (N / 4), i0 = (q % (N / 4)) * 4;
+  for (int qi = 0; qi < XPER; ++qi) {
+    const int q = unit + qi * NBLK;
+    if (q < NCH_B) {
+      const int L = q / (N / 4), i0 = (q % (N / 4)) * 4;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) mine[L * LW + N * N + i0 + e] = xacc[qi][e];
-      } else if (q < NCH) {
-        const int j0 = (q - NCH_B) * 4;
+      for (int e = 0; e < 4; ++e) mine[L * LW + N * N + i0 + e] = xacc[qi][e];
+    } else if (q < NCH) {
+      const int j0 = (q - NCH_B) * 4;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          mine[OW + j0 + e] = xacc[qi][e];
-          mine[OW + N + j0 + e] = xacc[qi][4 + e];
-        }
-        if (j0 == 0) { mine[OB] = xacc[qi][8]; mine[OB + 1] = xacc[qi][9]; }
+      for (int e = 0; e < 4; ++e) {
+        mine[OW + j0 + e] = xacc[qi][e];
+        mine[OW + N + j0 + e] = xacc[qi][4 + e];
       }
+      if (j0 == 0) { mine[OB] = xacc[qi][8]; mine[OB + 1] = xacc[qi][9]; }
     }
-    __syncthreads();
-    for (int j = tid; j < NP; j += TT) {
-      float t = 0.f;
+  }
+  __syncthreads();
+  for (int j = tid; j < NPA; j += T) {
+    float t = 0.f;
 #pragma unroll
-      for (int g = 0; g < G; ++g) t += red[g * NP + j];
-      a.part_grad[(long long)blockIdx.x * NP + j] = t;
-    }
+    for (int g = 0; g < G; ++g) t += red[g * NPA + j];
+    a.part_grad[(long long)blockIdx.x * NPA + j] = t;
   }
 }
 
-// latents per thread of the instantiated ARM kernels
 template <int N, int NL>
-struct ArmLpt {
-  static constexpr int value = 1;
-};
-
-template <int N, int NL, bool BWD>
-static cudaError_t launch_t(const ArmArgs& a, int grid, cudaStream_t st) {
-  constexpr int LPT = ArmLpt<N, NL>::value;
-  using Sh = ArmShape<N, NL, LPT>;
-  const size_t smem = BWD ? (size_t)Sh::smem_floats * sizeof(float) : 0;
-  k_arm<N, NL, BWD, LPT><<<grid, kArmTile / LPT, smem, st>>>(a);
+static cudaError_t launch_t(bool bwd, const ArmArgs& a, int grid, cudaStream_t st) {
+  if (bwd) {
+    k_arm_tc<N, NL><<<grid, kArmTile, ArmTcShape<N, NL>::BYTES, st>>>(a);
+  } else {
+    k_arm_fwd<N, NL><<<grid, kArmTile, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
 template <int N, int NL>
 static cudaError_t prepare_t() {
-  constexpr int LPT = ArmLpt<N, NL>::value;
-  return cudaFuncSetAttribute(k_arm<N, NL, true, LPT>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(ArmShape<N, NL, LPT>::smem_floats * sizeof(float)));
+  return cudaFuncSetAttribute(k_arm_tc<N, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              ArmTcShape<N, NL>::BYTES);
 }
 
 template <int N, int NL>
 static size_t smem_t(bool bwd) {
-  return bwd ? (size_t)ArmShape<N, NL, ArmLpt<N, NL>::value>::smem_floats * sizeof(float) : 0;
+  return bwd ? (size_t)ArmTcShape<N, NL>::BYTES : 0;
 }
 
 #define CC_ARM_DISPATCH(FN, ...)                                              \
@@ -429,18 +518,13 @@ static size_t smem_t(bool bwd) {
     default: break;                                                           \
   }
 
-template <int N, int NL>
-static cudaError_t launch_nl(bool bwd, const ArmArgs& k, int grid, cudaStream_t st) {
-  return bwd ? launch_t<N, NL, true>(k, grid, st) : launch_t<N, NL, false>(k, grid, st);
-}
-
 cudaError_t arm_launch(const Arch& a, bool backward, const float* yhat, const Geo& g,
                        const int2* tiles, int n_tiles, int grid, float* dctx, float* gself,
-                       float* part_grad, float* part_bits, cudaStream_t st) {
+                       float* part_grad, float* part_bits, int* fault, cudaStream_t st) {
   ArmArgs k;
   k.yhat = yhat; k.dctx = dctx; k.gself = gself; k.part_grad = part_grad;
-  k.part_bits = part_bits; k.tiles = tiles; k.n_tiles = n_tiles; k.g = g;
-  CC_ARM_DISPATCH(launch_nl, backward, k, grid, st);
+  k.part_bits = part_bits; k.tiles = tiles; k.n_tiles = n_tiles; k.fault = fault; k.g = g;
+  CC_ARM_DISPATCH(launch_t, backward, k, grid, st);
   return cudaErrorInvalidValue;
 }
 
@@ -454,9 +538,12 @@ size_t arm_smem_bytes(const Arch& a, bool backward) {
   return 0;
 }
 
+// two CTAs of the tensor-core kernel fit an SM (shared memory); the forward-only kernel
+// runs on the same grid
 int arm_blocks_per_sm(const Arch& a, bool backward) {
+  (void)a;
   (void)backward;
-  return a.N >= 16 ? ArmOcc<24>::blocks : ArmOcc<8>::blocks;
+  return 2;
 }
 
 __global__ void k_arm_image(const float* __restrict__ params, int n_arm,

@@ -315,7 +315,7 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
   };
   if (fork) CKE(record_on_side(c->ev_a0));
   CKE(arm_launch(a, backward, c->yhat_bord, c->geo, c->tiles, c->n_tiles, c->grid_arm, c->dctx,
-                 c->gself, c->part_arm, c->part_bits, sa));
+                 c->gself, c->part_arm, c->part_bits, &c->sc->fault, sa));
   if (fork) CKE(record_on_side(c->ev_a1));
   // the context gather follows the ARM on its stream; timed per phase it runs after the
   // upsampling adjoint instead, so that the phase events stay in stream order
@@ -496,6 +496,10 @@ int init_common(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
 int sync_copy_scalars(cc_ctx* c, IterScalars* h) {
   CK(cudaMemcpyAsync(h, c->sc, sizeof(IterScalars), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
+  if (h->fault) {
+    set_error_text("a tensor-core wait of the ARM kernel gave up; results are invalid");
+    return CC_ECUDA;
+  }
   return CC_OK;
 }
 

@@ -9,7 +9,7 @@
 namespace cc {
 
 constexpr int kLevels = 7;        // L of Sec. II "Decoding" item i (fixed by Table 1 "7-C")
-constexpr int kArmTile = 384;     // latents per ARM tile (= threads per ARM block)
+constexpr int kArmTile = 128;     // latents per ARM tile (= threads per ARM block)
 constexpr int kPixTile = 256;     // pixels per synthesis block
 constexpr int kLogCap = 4096;     // per-iteration loss log entries kept on the device
 
@@ -125,7 +125,7 @@ struct IterScalars {
   int t;              // index of the current iteration (0-based)
   float inv_bc1;      // Adam 1 / (1 - beta1^(t+1)) of the current update
   float inv_sqrt_bc2; // Adam 1 / sqrt(1 - beta2^(t+1))
-  int pad;
+  int fault;          // set when a bounded tensor-core wait of the ARM kernel gave up
   double D, R, loss;
   double b1t, b2t;    // beta1^t, beta2^t, carried by repeated multiplication
 };
@@ -140,7 +140,7 @@ cudaError_t arm_upload(const float* d_params, int n_arm, const int2* d_offsets, 
 size_t arm_image_bytes();
 cudaError_t arm_launch(const Arch& a, bool backward, const float* yhat, const Geo& g,
                        const int2* tiles, int n_tiles, int grid, float* dctx, float* gself,
-                       float* part_grad, float* part_bits, cudaStream_t st);
+                       float* part_grad, float* part_bits, int* fault, cudaStream_t st);
 int arm_blocks_per_sm(const Arch& a, bool backward);
 cudaError_t arm_prepare(const Arch& a);   // kernel attributes; call once before capture
 size_t arm_smem_bytes(const Arch& a, bool backward);
