@@ -25,6 +25,8 @@
 #include "cc_laplace.cuh"
 #include "cc_tc.cuh"
 
+#include <cudaTypedefs.h>
+
 namespace cc {
 
 constexpr int kMaxN = 24;
@@ -86,18 +88,23 @@ __device__ __forceinline__ void store_row(float* p, const float (&v)[N]) {
     *reinterpret_cast<float4*>(p + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
 }
 
-// The N causal neighbours of latent td.y + tid of the tile and the latent itself, read
-// from the zero-bordered plane (every neighbour is inside the allocation; outside the grid
-// it reads the zero border).  Returns whether the latent exists.
+// Latent (y, x) of thread tid in tile td = (level, y0 << 16 | x0): rows of kArmTileX.
+__device__ __forceinline__ void tile_latent(int2 td, int tid, int& y, int& x) {
+  y = (td.y >> 16) + tid / kArmTileX;
+  x = (td.y & 0xFFFF) + tid % kArmTileX;
+}
+
+// The N causal neighbours of the thread's latent and the latent itself, read from the
+// zero-bordered plane (every neighbour is inside the allocation; outside the grid it reads
+// the zero border).  Returns whether the latent exists.
 template <int N>
 __device__ __forceinline__ bool gather_context(const ArmArgs& a, int2 td, int tid,
                                                float (&h)[N], float& yq) {
   const int l = td.x;
-  const int w = a.g.w[l];
-  const int i = td.y + tid;
-  const bool valid = i < a.g.h[l] * w;
-  int r = 0, c = 0;
-  if (valid) { r = i / w; c = i - r * w; }
+  int r, c;
+  tile_latent(td, tid, r, c);
+  const bool valid = r < a.g.h[l] && c < a.g.w[l];
+  if (!valid) { r = 0; c = 0; }
   const int pw = a.g.pw[l];
   const float* ctr = a.yhat + a.g.poff[l] + (long long)(r + kCtxPad) * pw + c + kCtxPad;
 #pragma unroll
@@ -206,7 +213,7 @@ struct ArmTcShape {
 constexpr long long kTcWaitCycles = 1ll << 30;
 
 template <int N, int NL>
-__global__ void __launch_bounds__(kArmTile, 2) k_arm_tc(ArmArgs a) {
+__global__ void __launch_bounds__(kArmTile, 2) k_arm_tc(ArmArgs a, const __grid_constant__ ArmMaps maps) {
   pdl_wait();
   pdl_trigger();
   using Sh = ArmTcShape<N, NL>;
@@ -228,6 +235,12 @@ __global__ void __launch_bounds__(kArmTile, 2) k_arm_tc(ArmArgs a) {
   float* s_do = s_ho + T * S;        // [T][2]     (d bits/d mu, d bits/d s)
   __shared__ __align__(8) uint64_t s_mbar;
   __shared__ uint32_t s_tmem;
+  // causal context of a tile, loaded by TMA (double-buffered): rows y0 - kCtxPad .. y0 + 3,
+  // columns x0 - kCtxPad .. x0 + 35 of the level (zeros outside it)
+  constexpr int HR = kArmTileY + kCtxPad, HC = kArmTileX + 2 * kCtxPad;
+  constexpr uint32_t HALO_BYTES = HR * HC * 4;
+  __shared__ __align__(128) float s_halo[2][HR * HC];
+  __shared__ __align__(8) uint64_t s_tbar[2];
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -245,7 +258,11 @@ __global__ void __launch_bounds__(kArmTile, 2) k_arm_tc(ArmArgs a) {
     *reinterpret_cast<float*>(base + 2 * Sh::W_BYTES + off) = th;
     *reinterpret_cast<float*>(base + 3 * Sh::W_BYTES + off) = wt - th;
   }
-  if (tid == 0) mbar_init(smem_u32(&s_mbar), 1);
+  if (tid == 0) {
+    mbar_init(smem_u32(&s_mbar), 1);
+    mbar_init(smem_u32(&s_tbar[0]), 1);
+    mbar_init(smem_u32(&s_tbar[1]), 1);
+  }
   if (warp == 0) tc_alloc(smem_u32(&s_tmem), Sh::TMEM_COLS);
   fence_async_smem();
   tc_fence_before();
@@ -308,25 +325,38 @@ __global__ void __launch_bounds__(kArmTile, 2) k_arm_tc(ArmArgs a) {
   float bits_acc = 0.f;
   bool ok = true;
 
-  // the context of the CTA's next tile is loaded while the current one is computed
-  float nh[N], nyq = 0.f;
-  bool nvalid = false;
-  int2 ntd = make_int2(0, 0);
-  if (blockIdx.x < a.n_tiles) {
-    ntd = a.tiles[blockIdx.x];
-    nvalid = gather_context<N>(a, ntd, tid, nh, nyq);
-  }
-  for (int tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
-    const int2 td = ntd;
+  // TMA of a tile's context into halo buffer `buf` (thread 0): the buffer's earlier
+  // readers are ordered before the asynchronous write by a barrier and this fence
+  auto issue = [&](int t, int buf) {
+    const int2 tq = a.tiles[t];
+    fence_async_smem();
+    const uint32_t bar = smem_u32(&s_tbar[buf]);
+    mbar_expect_tx(bar, HALO_BYTES);
+    tma_load_2d(smem_u32(&s_halo[buf][0]), &maps.m[tq.x], tq.y & 0xFFFF, tq.y >> 16, bar);
+  };
+  if (tid == 0 && (int)blockIdx.x < a.n_tiles) issue(blockIdx.x, 0);
+  int it = 0;
+  bool pending = (int)blockIdx.x < a.n_tiles;   // a load in flight into buffer it & 1
+  for (int tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x, ++it) {
+    const int buf = it & 1;
+    // the next tile's context goes to the other buffer, read during the previous tile
+    const bool more = tile + (int)gridDim.x < a.n_tiles;
+    if (tid == 0 && more) issue(tile + gridDim.x, buf ^ 1);
+    const bool hok = mbar_wait(smem_u32(&s_tbar[buf]), (uint32_t)(it >> 1) & 1u, kTcWaitCycles);
+    if (__syncthreads_or(hok ? 0 : 1)) { ok = false; break; }
+    pending = more;
+    const int2 td = a.tiles[tile];
+    int ly, lx;
+    tile_latent(td, tid, ly, lx);
+    const bool valid = ly < a.g.h[td.x] && lx < a.g.w[td.x];
+    const float* hb = &s_halo[buf][(tid / kArmTileX + kCtxPad) * HC + tid % kArmTileX + kCtxPad];
     float h[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) h[k] = nh[k];
-    const float yq = nyq;
-    const bool valid = nvalid;
-    if (tile + (int)gridDim.x < a.n_tiles) {
-      ntd = a.tiles[tile + gridDim.x];
-      nvalid = gather_context<N>(a, ntd, tid, nh, nyq);
+    for (int k = 0; k < N; ++k) {
+      const int2 o = c_off[k];
+      h[k] = valid ? hb[o.x * HC + o.y] : 0.f;
     }
+    const float yq = valid ? hb[0] : 0.f;
 
     // forward: h <- h + relu(W h + b), NL times
     uint32_t mask[NL];
@@ -370,7 +400,7 @@ __global__ void __launch_bounds__(kArmTile, 2) k_arm_tc(ArmArgs a) {
     }
     if (!ok) break;
     if (valid) {
-      const long long qq = a.g.off[td.x] + td.y + tid;
+      const long long qq = a.g.off[td.x] + (long long)ly * a.g.w[td.x] + lx;
 #pragma unroll
       for (int k = 0; k < N; ++k) a.dctx[k * a.g.n_pad + qq] = dh[k];
       a.gself[qq] = lo.g_y;
@@ -427,6 +457,8 @@ __global__ void __launch_bounds__(kArmTile, 2) k_arm_tc(ArmArgs a) {
     // free the tensor memory and stop
     if (tid == 0) atomicExch(a.fault, 1);
     mbar_wait(mbar, phase ^ 1u, kTcWaitCycles);
+    if (pending)   // the context load still in flight
+      mbar_wait(smem_u32(&s_tbar[(it + 1) & 1]), (uint32_t)((it + 1) >> 1) & 1u, kTcWaitCycles);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tc_dealloc(tmem, Sh::TMEM_COLS);
@@ -487,9 +519,10 @@ __global__ void __launch_bounds__(kArmTile, 2) k_arm_tc(ArmArgs a) {
 }
 
 template <int N, int NL>
-static cudaError_t launch_t(bool bwd, const ArmArgs& a, int grid, cudaStream_t st) {
+static cudaError_t launch_t(bool bwd, const ArmArgs& a, const ArmMaps& maps, int grid,
+                            cudaStream_t st) {
   if (bwd) {
-    k_arm_tc<N, NL><<<grid, kArmTile, ArmTcShape<N, NL>::BYTES, st>>>(a);
+    k_arm_tc<N, NL><<<grid, kArmTile, ArmTcShape<N, NL>::BYTES, st>>>(a, maps);
   } else {
     k_arm_fwd<N, NL><<<grid, kArmTile, 0, st>>>(a);
   }
@@ -519,13 +552,40 @@ static size_t smem_t(bool bwd) {
   }
 
 cudaError_t arm_launch(const Arch& a, bool backward, const float* yhat, const Geo& g,
-                       const int2* tiles, int n_tiles, int grid, float* dctx, float* gself,
-                       float* part_grad, float* part_bits, int* fault, cudaStream_t st) {
+                       const ArmMaps& maps, const int2* tiles, int n_tiles, int grid,
+                       float* dctx, float* gself, float* part_grad, float* part_bits,
+                       int* fault, cudaStream_t st) {
   ArmArgs k;
   k.yhat = yhat; k.dctx = dctx; k.gself = gself; k.part_grad = part_grad;
   k.part_bits = part_bits; k.tiles = tiles; k.n_tiles = n_tiles; k.fault = fault; k.g = g;
-  CC_ARM_DISPATCH(launch_t, backward, k, grid, st);
+  CC_ARM_DISPATCH(launch_t, backward, k, maps, grid, st);
   return cudaErrorInvalidValue;
+}
+
+cudaError_t arm_make_maps(const Geo& g, const float* yhat_bord, ArmMaps* out) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorSymbolNotFound;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  for (int l = 0; l < kLevels; ++l) {
+    const cuuint64_t dims[2] = {(cuuint64_t)g.pw[l], (cuuint64_t)(g.h[l] + kCtxPad)};
+    const cuuint64_t strides[1] = {(cuuint64_t)g.pw[l] * sizeof(float)};
+    const cuuint32_t box[2] = {kArmTileX + 2 * kCtxPad, kArmTileY + kCtxPad};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(&out->m[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                              const_cast<float*>(yhat_bord + g.poff[l]), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t arm_prepare(const Arch& a) {

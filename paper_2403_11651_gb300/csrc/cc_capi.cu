@@ -115,7 +115,7 @@ Geo geo_of(int H, int W) {
   g.n_pad = off;
   off = 0;
   for (int l = 0; l < kLevels; ++l) {
-    g.pw[l] = g.w[l] + 2 * kCtxPad;
+    g.pw[l] = (g.w[l] + 2 * kCtxPad + 3) & ~3;   // 16-byte rows (tensor-map stride)
     g.poff[l] = off;
     off = align32(off + (long long)(g.h[l] + kCtxPad) * g.pw[l]);
   }
@@ -164,6 +164,7 @@ struct cc_ctx {
   std::vector<int2> h_tiles, h_offs;
   int n_tiles = 0, grid_arm = 0, grid_syn = 0, grid_tiles = 0, slices = 16, n_virtual = 0;
   SectionTable tab;
+  ArmMaps maps;   // tensor maps of the zero-bordered y_hat planes (ARM context tiles)
   cudaGraphExec_t g1 = nullptr, g16 = nullptr;
   int iter = 0;
   int kernels_per_iter = 0;
@@ -235,8 +236,11 @@ int setup(cc_ctx* c, const cc_config* cfg, int H, int W) {
   c->HW = H * W;
   c->ste_start = (int)std::llround((double)cfg->total_iters * (1.0 - (double)cfg->ste_frac));
   c->h_tiles.clear();
+  // ARM tiles: blocks of kArmTileY x kArmTileX latents of one level, (level, y0 << 16 | x0)
   for (int l = 0; l < kLevels; ++l)
-    for (int s = 0; s < c->geo.h[l] * c->geo.w[l]; s += kArmTile) c->h_tiles.push_back(make_int2(l, s));
+    for (int y0 = 0; y0 < c->geo.h[l]; y0 += kArmTileY)
+      for (int x0 = 0; x0 < c->geo.w[l]; x0 += kArmTileX)
+        c->h_tiles.push_back(make_int2(l, (y0 << 16) | x0));
   c->n_tiles = (int)c->h_tiles.size();
   const int sms = sm_count();
   if (sms <= 0) return fail_cuda(cudaErrorNoDevice, "cudaDeviceGetAttribute");
@@ -314,8 +318,8 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
                : cudaEventRecord(e, sa);
   };
   if (fork) CKE(record_on_side(c->ev_a0));
-  CKE(arm_launch(a, backward, c->yhat_bord, c->geo, c->tiles, c->n_tiles, c->grid_arm, c->dctx,
-                 c->gself, c->part_arm, c->part_bits, &c->sc->fault, sa));
+  CKE(arm_launch(a, backward, c->yhat_bord, c->geo, c->maps, c->tiles, c->n_tiles, c->grid_arm,
+                 c->dctx, c->gself, c->part_arm, c->part_bits, &c->sc->fault, sa));
   if (fork) CKE(record_on_side(c->ev_a1));
   // the context gather follows the ARM on its stream; timed per phase it runs after the
   // upsampling adjoint instead, so that the phase events stay in stream order
@@ -453,6 +457,10 @@ int init_common(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
   c->bytes = need;
   plan(c, (char*)c->mem);
   build_sections(c);
+  if (cudaError_t me = arm_make_maps(c->geo, c->yhat_bord, &c->maps)) {
+    cc_free(c);
+    return fail_cuda(me, "cuTensorMapEncodeTiled");
+  }
   auto bail = [&](int code) { cc_free(c); return code; };
   cudaError_t ce = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
   if (ce != cudaSuccess) return bail(fail_cuda(ce, "cudaStreamCreate"));

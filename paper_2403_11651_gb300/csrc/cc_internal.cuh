@@ -2,6 +2,7 @@
 // Everything here is host/device plumbing; the arithmetic lives in the .cu files.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (types only; the encoder is reached through the runtime)
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
@@ -10,6 +11,7 @@ namespace cc {
 
 constexpr int kLevels = 7;        // L of Sec. II "Decoding" item i (fixed by Table 1 "7-C")
 constexpr int kArmTile = 128;     // latents per ARM tile (= threads per ARM block)
+constexpr int kArmTileY = 4, kArmTileX = 32;   // an ARM tile: 4 rows x 32 latents of a level
 constexpr int kPixTile = 256;     // pixels per synthesis block
 constexpr int kLogCap = 4096;     // per-iteration loss log entries kept on the device
 
@@ -138,9 +140,17 @@ IterScalars iter_scalars_at(int t);
 cudaError_t arm_upload(const float* d_params, int n_arm, const int2* d_offsets, int N,
                        void* d_image, cudaStream_t st);
 size_t arm_image_bytes();
+// One tensor map per level over the zero-bordered y_hat plane (width pw, h + kCtxPad rows),
+// box of (kArmTileY + kCtxPad) rows x (kArmTileX + 2 kCtxPad) floats: the causal context
+// of one ARM tile; reads outside the plane return zeros.
+struct ArmMaps {
+  CUtensorMap m[kLevels];
+};
+cudaError_t arm_make_maps(const Geo& g, const float* yhat_bord, ArmMaps* out);
 cudaError_t arm_launch(const Arch& a, bool backward, const float* yhat, const Geo& g,
-                       const int2* tiles, int n_tiles, int grid, float* dctx, float* gself,
-                       float* part_grad, float* part_bits, int* fault, cudaStream_t st);
+                       const ArmMaps& maps, const int2* tiles, int n_tiles, int grid,
+                       float* dctx, float* gself, float* part_grad, float* part_bits,
+                       int* fault, cudaStream_t st);
 int arm_blocks_per_sm(const Arch& a, bool backward);
 cudaError_t arm_prepare(const Arch& a);   // kernel attributes; call once before capture
 size_t arm_smem_bytes(const Arch& a, bool backward);

@@ -138,6 +138,24 @@ __device__ __forceinline__ void tc_ld_row<16>(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// TMA: announce `bytes` for the current phase of the mbarrier (one arrival)
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes)
+               : "memory");
+}
+
+// TMA: load the box of the 2D tensor map whose first element is at (x, y) (x counts
+// elements of the contiguous dimension) into shared memory at dst; completes the
+// transaction bytes on mbar.  x times the element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y,
+                                            uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];"
+      :: "r"(dst), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+
 // the TF32 part of x: its low 13 mantissa bits cleared (exactly representable in TF32, so
 // the tensor cores read it unchanged); x - tf32_hi(x) is exact in FP32 and is the low part
 __device__ __forceinline__ float tf32_hi(float x) {
