@@ -343,13 +343,15 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
     CKE(param_update(c->lay, a, c->part2, c->slices, c->params, c->mp, c->vp,
                      grad_out ? grad_out + c->geo.n_lat : nullptr, apply, c->cfg.lr, c->sc, s));
     CKE(latent_update(c->geo, c->gsyn, c->gself, (float)((double)c->cfg.lam / (double)c->HW),
-                      c->y, c->my, c->vy, grad_out, apply, c->cfg.lr, c->sc, s));
-  } else if (fork) {
-    CKE(cudaStreamWaitEvent(s, c->ev_join, 0));
+                      c->y, c->my, c->vy, grad_out, apply, c->cfg.lr, c->sc, c->part_d,
+                      c->grid_tiles, c->part_bits, c->grid_arm, 1.0 / (3.0 * (double)HW),
+                      1.0 / (double)HW, (double)c->cfg.lam, c->log, advance, s));
+  } else {
+    if (fork) CKE(cudaStreamWaitEvent(s, c->ev_join, 0));
+    CKE(finish_iteration(c->part_d, c->grid_tiles, c->part_bits, c->grid_arm,
+                         1.0 / (3.0 * (double)HW), 1.0 / (double)HW, (double)c->cfg.lam, c->sc,
+                         c->log, advance, s, false));
   }
-  CKE(finish_iteration(c->part_d, c->grid_tiles, c->part_bits, c->grid_arm,
-                       1.0 / (3.0 * (double)HW), 1.0 / (double)HW, (double)c->cfg.lam, c->sc,
-                       c->log, advance, s, backward));
   return mark(7);
 }
 

@@ -130,6 +130,8 @@ struct IterScalars {
   int fault;          // set when a bounded tensor-core wait of the ARM kernel gave up
   double D, R, loss;
   double b1t, b2t;    // beta1^t, beta2^t, carried by repeated multiplication
+  unsigned ticket;    // blocks of the latent update done (reset by the last one)
+  int pad2;
 };
 // IterScalars of iteration t, computed on the host (context set-up, state restore).
 IterScalars iter_scalars_at(int t);
@@ -198,9 +200,12 @@ cudaError_t param_update(const Layout& lay, const Arch& a, const float* part2, i
                          float lr, const IterScalars* sc, cudaStream_t st);
 // Total latent gradient dD/dy_hat + lambda / (HW) * dR/dy_hat (grate: the rate gradient
 // after ctx_gather) and Adam on the latents.
+// ... and finishes the pass as finish_iteration does (its last block).
 cudaError_t latent_update(const Geo& g, const float* gsyn, const float* grate, float rate_scale,
                           float* y, float* m, float* v, float* grad_out, bool apply, float lr,
-                          const IterScalars* sc, cudaStream_t st);
+                          IterScalars* sc, const float* part_d, int nd, const float* part_bits,
+                          int nb, double d_scale, double r_scale, double lam, double* log,
+                          bool advance, cudaStream_t st);
 cudaError_t finish_iteration(const float* part_d, int nd, const float* part_bits, int nb,
                              double d_scale, double r_scale, double lam, IterScalars* sc,
                              double* log, bool advance, cudaStream_t st,

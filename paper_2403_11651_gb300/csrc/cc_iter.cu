@@ -190,50 +190,12 @@ cudaError_t param_update(const Layout& lay, const Arch& a, const float* part2, i
 // Gradient of a latent: the synthesis path, plus lambda/(HW) times the rate terms in
 // which it appears, as the coded symbol (gself) and in the context of every latent p
 // whose causal neighbourhood contains it (dctx of p at the matching slot).
-__global__ void __launch_bounds__(256) k_latent_update(Geo g, const float* __restrict__ gsyn,
-                                                       const float* __restrict__ grate,
-                                                       float rate_scale, float* y, float* m,
-                                                       float* v, float* grad_out, int apply,
-                                                       float lr, const IterScalars* sc) {
-  pdl_wait();
-  pdl_trigger();
-  const int l = blockIdx.y;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.h[l] * g.w[l]) return;
-  const long long q = g.off[l] + i;
-  const float gt = __ldg(gsyn + q) + rate_scale * __ldg(grate + q);
-  if (grad_out) {
-    long long fo = 0;
-    for (int k = 0; k < l; ++k) fo += (long long)g.h[k] * g.w[k];
-    grad_out[fo + i] = gt;
-  }
-  if (apply) {
-    AdamStep st;
-    st.lr = lr;
-    st.inv_bc1 = sc->inv_bc1;
-    st.inv_sqrt_bc2 = sc->inv_sqrt_bc2;
-    float yv = y[q], mv = m[q], vv = v[q];
-    adam_apply(yv, mv, vv, gt, st);
-    y[q] = yv; m[q] = mv; v[q] = vv;
-  }
-}
-
-cudaError_t latent_update(const Geo& g, const float* gsyn, const float* grate, float rate_scale,
-                          float* y, float* m, float* v, float* grad_out, bool apply, float lr,
-                          const IterScalars* sc, cudaStream_t st) {
-  int maxn = 0;
-  for (int l = 0; l < kLevels; ++l) maxn = g.h[l] * g.w[l] > maxn ? g.h[l] * g.w[l] : maxn;
-  dim3 grid((maxn + 255) / 256, kLevels);
-  return launch_k(k_latent_update, grid, dim3(256), 0, st, g, gsyn, grate, rate_scale, y, m, v,
-                  grad_out, apply ? 1 : 0, lr, sc);
-}
-
-__global__ void __launch_bounds__(256) k_finish(const float* part_d, int nd,
-                                                const float* part_bits, int nb, double d_scale,
-                                                double r_scale, double lam, IterScalars* sc,
-                                                double* log, int advance) {
-  pdl_wait();
-  pdl_trigger();
+// D, R and the loss of the pass from the per-CTA partial sums (FP64, fixed order), the
+// loss log entry, and with `advance` the step to the next iteration (t and the Adam powers
+// and bias corrections of its update).  Run by one block of 256 threads.
+__device__ __forceinline__ void finish_block(const float* part_d, int nd, const float* part_bits,
+                                             int nb, double d_scale, double r_scale, double lam,
+                                             IterScalars* sc, double* log, int advance) {
   __shared__ double sd[256], sb[256];
   double a = 0.0, b = 0.0;
   for (int k = threadIdx.x; k < nd; k += 256) a += (double)part_d[k];
@@ -267,6 +229,82 @@ __global__ void __launch_bounds__(256) k_finish(const float* part_d, int nd,
       sc->inv_sqrt_bc2 = (float)(1.0 / sqrt(1.0 - b2 * 0.999));
     }
   }
+}
+
+__global__ void __launch_bounds__(256) k_finish(const float* part_d, int nd,
+                                                const float* part_bits, int nb, double d_scale,
+                                                double r_scale, double lam, IterScalars* sc,
+                                                double* log, int advance) {
+  pdl_wait();
+  pdl_trigger();
+  finish_block(part_d, nd, part_bits, nb, d_scale, r_scale, lam, sc, log, advance);
+}
+
+// Also finishes the pass (finish_block): the last of its blocks to end, found with a ticket
+// in IterScalars, runs it once every block has updated its latents.
+struct FinishArgs {
+  const float* part_d;
+  int nd;
+  const float* part_bits;
+  int nb;
+  double d_scale, r_scale, lam;
+  double* log;
+  int advance;
+};
+
+__global__ void __launch_bounds__(256) k_latent_update(Geo g, const float* __restrict__ gsyn,
+                                                       const float* __restrict__ grate,
+                                                       float rate_scale, float* y, float* m,
+                                                       float* v, float* grad_out, int apply,
+                                                       float lr, IterScalars* sc, FinishArgs fa) {
+  pdl_wait();
+  pdl_trigger();
+  // one thread per element of the latent-shaped buffers; alignment gaps between planes skip
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int l = 0;
+#pragma unroll
+  for (int k = 1; k < kLevels; ++k) l = q >= g.off[k] ? k : l;
+  const long long i = q - g.off[l];
+  if (q < g.n_pad && i < (long long)g.h[l] * g.w[l]) {
+    const float gt = __ldg(gsyn + q) + rate_scale * __ldg(grate + q);
+    if (grad_out) {
+      long long fo = 0;
+      for (int k = 0; k < l; ++k) fo += (long long)g.h[k] * g.w[k];
+      grad_out[fo + i] = gt;
+    }
+    if (apply) {
+      AdamStep st;
+      st.lr = lr;
+      st.inv_bc1 = sc->inv_bc1;
+      st.inv_sqrt_bc2 = sc->inv_sqrt_bc2;
+      float yv = y[q], mv = m[q], vv = v[q];
+      adam_apply(yv, mv, vv, gt, st);
+      y[q] = yv; m[q] = mv; v[q] = vv;
+    }
+  }
+  __shared__ bool s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&sc->ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (s_last) {
+    finish_block(fa.part_d, fa.nd, fa.part_bits, fa.nb, fa.d_scale, fa.r_scale, fa.lam, sc,
+                 fa.log, fa.advance);
+    if (threadIdx.x == 0) sc->ticket = 0u;
+  }
+}
+
+cudaError_t latent_update(const Geo& g, const float* gsyn, const float* grate, float rate_scale,
+                          float* y, float* m, float* v, float* grad_out, bool apply, float lr,
+                          IterScalars* sc, const float* part_d, int nd, const float* part_bits,
+                          int nb, double d_scale, double r_scale, double lam, double* log,
+                          bool advance, cudaStream_t st) {
+  FinishArgs fa;
+  fa.part_d = part_d; fa.nd = nd; fa.part_bits = part_bits; fa.nb = nb;
+  fa.d_scale = d_scale; fa.r_scale = r_scale; fa.lam = lam; fa.log = log;
+  fa.advance = advance ? 1 : 0;
+  const int blocks = (int)((g.n_pad + 255) / 256);
+  return launch_k(k_latent_update, dim3(blocks), dim3(256), 0, st, g, gsyn, grate, rate_scale, y,
+                  m, v, grad_out, apply ? 1 : 0, lr, sc, fa);
 }
 
 cudaError_t finish_iteration(const float* part_d, int nd, const float* part_bits, int nb,
