@@ -635,14 +635,24 @@ __global__ void k_arm_image(const float* __restrict__ params, int n_arm,
 
 size_t arm_image_bytes() { return sizeof(ArmBank); }
 
-cudaError_t arm_upload(const float* d_params, int n_arm, const int2* d_offsets, int N,
-                       void* d_image, cudaStream_t st) {
+cudaError_t arm_build_image(const float* d_params, int n_arm, const int2* d_offsets, int N,
+                            void* d_image, cudaStream_t st) {
   const int NL = (n_arm - 2 * N - 2) / (N * N + N);
   k_arm_image<<<1, 256, 0, st>>>(d_params, n_arm, d_offsets, N, NL, (ArmBank*)d_image);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t arm_copy_bank(const void* d_image, cudaStream_t st) {
   return cudaMemcpyToSymbolAsync(c_armbank, d_image, sizeof(ArmBank), 0,
                                  cudaMemcpyDeviceToDevice, st);
 }
+
+cudaError_t arm_upload(const float* d_params, int n_arm, const int2* d_offsets, int N,
+                       void* d_image, cudaStream_t st) {
+  cudaError_t e = arm_build_image(d_params, n_arm, d_offsets, N, d_image, st);
+  return e != cudaSuccess ? e : arm_copy_bank(d_image, st);
+}
+
+int arm_image_weight_floats() { return 2 * kArmBankFloats; }
 
 }  // namespace cc

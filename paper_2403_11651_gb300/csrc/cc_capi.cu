@@ -158,6 +158,7 @@ struct cc_ctx {
   uint8_t* img_u8;
   int2 *tiles, *offs;
   void *arm_image, *syn_image;   // constant-bank images built on the device
+  int4* slot_map;                // parameter -> image slots (ImageSlots)
   IterScalars* sc;
   double* log;
   UpPlan up;
@@ -212,6 +213,7 @@ size_t plan(cc_ctx* c, char* base) {
   c->img_u8 = (uint8_t*)take(3 * HW);
   c->tiles = (int2*)take((size_t)c->n_tiles * sizeof(int2));
   c->offs = (int2*)take(24 * sizeof(int2));
+  c->slot_map = (int4*)take((size_t)c->lay.total * sizeof(int4));
   c->arm_image = take(arm_image_bytes());
   c->syn_image = take(syn_image_bytes());
   c->sc = (IterScalars*)take(sizeof(IterScalars));
@@ -285,6 +287,64 @@ void build_sections(cc_ctx* c) {
   t.n = n;
 }
 
+ImageSlots image_slots(cc_ctx* c) {
+  ImageSlots sl;
+  sl.map = c->slot_map;
+  sl.arm_image = (float*)c->arm_image;
+  sl.syn_image = (float*)c->syn_image;
+  return sl;
+}
+
+// Rebuild both bank images from the parameters (after the host wrote them).
+cudaError_t rebuild_images(cc_ctx* c, cudaStream_t st) {
+  cudaError_t e = arm_build_image(c->params, c->lay.n_arm, c->offs, c->arch.N, c->arm_image, st);
+  return e != cudaSuccess ? e : syn_build_image(c->params, c->lay, c->arch, c->syn_image, st);
+}
+
+// The parameter slots of the images: build both images from the index parameters
+// p[j] = j + 1 (a scratch buffer) and read back where each index landed.  The image
+// builders copy parameters without arithmetic, so every slot holds exactly one index.
+int build_slot_map(cc_ctx* c) {
+  const int total = c->lay.total;
+  std::vector<float> idx(total);
+  for (int j = 0; j < total; ++j) idx[j] = (float)(j + 1);
+  float* scratch = c->grad_scratch;
+  CK(cudaMemcpyAsync(scratch, idx.data(), (size_t)total * sizeof(float), cudaMemcpyHostToDevice,
+                     c->st));
+  CK(arm_build_image(scratch, c->lay.n_arm, c->offs, c->arch.N, c->arm_image, c->st));
+  CK(syn_build_image(scratch, c->lay, c->arch, c->syn_image, c->st));
+  const int na = arm_image_weight_floats(), ns = syn_image_weight_floats();
+  std::vector<float> ia(na), is(ns);
+  CK(cudaMemcpyAsync(ia.data(), c->arm_image, (size_t)na * sizeof(float), cudaMemcpyDeviceToHost,
+                     c->st));
+  CK(cudaMemcpyAsync(is.data(), c->syn_image, (size_t)ns * sizeof(float), cudaMemcpyDeviceToHost,
+                     c->st));
+  CK(cudaStreamSynchronize(c->st));
+  std::vector<int4> map(total, make_int4(-1, -1, -1, -1));
+  auto add = [&](const std::vector<float>& img, bool arm) -> bool {
+    for (size_t p = 0; p < img.size(); ++p) {
+      const float v = img[p];
+      if (!(v > 0.5f)) continue;
+      const int j = (int)(v + 0.5f) - 1;
+      if (j < 0 || j >= total) return false;
+      int& a = arm ? map[j].x : map[j].z;
+      int& b = arm ? map[j].y : map[j].w;
+      if (a < 0) a = (int)p;
+      else if (b < 0) b = (int)p;
+      else return false;   // more than two slots: not a copy layout
+    }
+    return true;
+  };
+  if (!add(ia, true) || !add(is, false)) {
+    set_error_text("bank image layout: a parameter has more than two slots");
+    return CC_EINVAL;
+  }
+  CK(cudaMemcpyAsync(c->slot_map, map.data(), (size_t)total * sizeof(int4), cudaMemcpyHostToDevice,
+                     c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return CC_OK;
+}
+
 // One pass of the hot path.  qmode: quantisation mode of k_quantize.  backward: run the
 // backward kernels (and the update when apply).  grad_out: device buffer receiving dL/dy
 // then dL/dparams, or nullptr.
@@ -299,8 +359,9 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
   const bool fork = ev == nullptr;
   cudaStream_t sa = fork ? c->side : s;
   CKE(mark(0));
-  CKE(arm_upload(c->params, c->lay.n_arm, c->offs, a.N, c->arm_image, s));
-  CKE(syn_upload(c->params, c->lay, a, c->syn_image, s));
+  // the bank images track the parameters (image_slots); copy them into the banks
+  CKE(arm_copy_bank(c->arm_image, s));
+  CKE(syn_copy_bank(c->syn_image, s));
   CKE(quantize_launch(c->geo, c->y, c->yhat, c->yhat_bord, c->noise, qmode, c->sc, c->ste_start, c->cfg.seed,
                       -1, s));
   CKE(mark(1));
@@ -341,7 +402,8 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
     else CKE(ctx_gather(c->geo, c->offs, a.N, c->gself, c->dctx, s));
     CKE(reduce_sections(c->tab, c->part2, c->n_virtual, c->slices, s));
     CKE(param_update(c->lay, a, c->part2, c->slices, c->params, c->mp, c->vp,
-                     grad_out ? grad_out + c->geo.n_lat : nullptr, apply, c->cfg.lr, c->sc, s));
+                     grad_out ? grad_out + c->geo.n_lat : nullptr, apply, c->cfg.lr, c->sc,
+                     image_slots(c), s));
     CKE(latent_update(c->geo, c->gsyn, c->gself, (float)((double)c->cfg.lam / (double)c->HW),
                       c->y, c->my, c->vy, grad_out, apply, c->cfg.lr, c->sc, c->part_d,
                       c->grid_tiles, c->part_bits, c->grid_arm, 1.0 / (3.0 * (double)HW),
@@ -498,6 +560,8 @@ int init_common(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
   if ((ce = cudaMemcpyAsync(c->offs, c->h_offs.data(), c->h_offs.size() * sizeof(int2),
                             cudaMemcpyHostToDevice, c->st)))
     return bail(fail_cuda(ce, "offsets copy"));
+  if (int me = build_slot_map(c)) return bail(me);
+  if ((ce = rebuild_images(c, c->st)) != cudaSuccess) return bail(fail_cuda(ce, "bank images"));
   if ((ce = cudaStreamSynchronize(c->st))) return bail(fail_cuda(ce, "init sync"));
   *out = c;
   return CC_OK;
@@ -508,7 +572,7 @@ int sync_copy_scalars(cc_ctx* c, IterScalars* h) {
   CK(cudaStreamSynchronize(c->st));
   if (h->fault) {
     set_error_text("a tensor-core wait of the ARM kernel gave up; results are invalid");
-    return CC_ECUDA;
+    return CC_ETIMEOUT;
   }
   return CC_OK;
 }
@@ -700,6 +764,7 @@ int cc_set_params(cc_ctx* c, const float* params) {
   CK(cudaSetDevice(c->dev));
   CK(cudaMemcpyAsync(c->params, params, (size_t)c->lay.total * sizeof(float), cudaMemcpyDefault,
                      c->st));
+  CK(rebuild_images(c, c->st));
   return CC_OK;
 }
 
@@ -823,6 +888,7 @@ int cc_set_state(cc_ctx* c, const void* buf, size_t nbytes) {
   int e;
   if ((e = copy_latents(c, c->y, f.data(), false))) return e;
   CK(cudaMemcpyAsync(c->params, f.data() + nl, np * sizeof(float), cudaMemcpyHostToDevice, c->st));
+  CK(rebuild_images(c, c->st));
   if ((e = copy_latents(c, c->my, f.data() + nl + np, false))) return e;
   if ((e = copy_latents(c, c->vy, f.data() + 2 * nl + np, false))) return e;
   CK(cudaMemcpyAsync(c->mp, f.data() + 3 * nl + np, np * sizeof(float), cudaMemcpyHostToDevice, c->st));

@@ -139,6 +139,17 @@ IterScalars iter_scalars_at(int t);
 // ---- launchers (each returns the cudaError_t of its launch) ----
 // ARM (cc_arm.cu)
 // Build the ARM constant-bank image in d_image (arm_image_bytes()) and copy it to the bank.
+// Bank images: built on the device from the flat parameters (build_image), copied into
+// the __constant__ bank before a pass (copy_bank); upload = both.  Every float of the
+// first *_image_weight_floats() of an image is a copy of one parameter (or zero padding).
+cudaError_t arm_build_image(const float* d_params, int n_arm, const int2* d_offsets, int N,
+                            void* d_image, cudaStream_t st);
+cudaError_t arm_copy_bank(const void* d_image, cudaStream_t st);
+int arm_image_weight_floats();
+cudaError_t syn_build_image(const float* d_params, const Layout& lay, const Arch& a,
+                            void* d_image, cudaStream_t st);
+cudaError_t syn_copy_bank(const void* d_image, cudaStream_t st);
+int syn_image_weight_floats();
 cudaError_t arm_upload(const float* d_params, int n_arm, const int2* d_offsets, int N,
                        void* d_image, cudaStream_t st);
 size_t arm_image_bytes();
@@ -195,9 +206,17 @@ cudaError_t ctx_gather(const Geo& g, const int2* d_offsets, int N, float* gself,
                        const float* dctx, cudaStream_t st);
 cudaError_t reduce_sections(const SectionTable& tab, float* part2, int n_virtual, int slices,
                             cudaStream_t st);
+// Parameter slots of the bank images: per parameter up to two float indices into the ARM
+// image and two into the synthesis image (-1: none).  param_update writes every updated
+// value to its slots, so that the images stay current between passes.
+struct ImageSlots {
+  const int4* map;
+  float* arm_image;
+  float* syn_image;
+};
 cudaError_t param_update(const Layout& lay, const Arch& a, const float* part2, int slices,
                          float* params, float* m, float* v, float* grad_out, bool apply,
-                         float lr, const IterScalars* sc, cudaStream_t st);
+                         float lr, const IterScalars* sc, const ImageSlots& slots, cudaStream_t st);
 // Total latent gradient dD/dy_hat + lambda / (HW) * dR/dy_hat (grate: the rate gradient
 // after ctx_gather) and Adam on the latents.
 // ... and finishes the pass as finish_iteration does (its last block).

@@ -137,7 +137,8 @@ struct VirtualMap {
 __global__ void __launch_bounds__(128) k_param_update(VirtualMap vm, const float* part2,
                                                       int slices, float* params, float* m,
                                                       float* v, float* grad_out, int apply,
-                                                      float lr, IterScalars* sc, int total) {
+                                                      float lr, IterScalars* sc, int total,
+                                                      ImageSlots slots) {
   pdl_wait();
   pdl_trigger();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -170,12 +171,22 @@ __global__ void __launch_bounds__(128) k_param_update(VirtualMap vm, const float
     g += t;
   }
   if (grad_out) grad_out[j] = g;
-  if (apply) adam_apply(params[j], m[j], v[j], g, st);
+  if (apply) {
+    float p = params[j];
+    adam_apply(p, m[j], v[j], g, st);
+    params[j] = p;
+    const int4 d = slots.map[j];
+    if (d.x >= 0) slots.arm_image[d.x] = p;
+    if (d.y >= 0) slots.arm_image[d.y] = p;
+    if (d.z >= 0) slots.syn_image[d.z] = p;
+    if (d.w >= 0) slots.syn_image[d.w] = p;
+  }
 }
 
 cudaError_t param_update(const Layout& lay, const Arch& a, const float* part2, int slices,
                          float* params, float* m, float* v, float* grad_out, bool apply,
-                         float lr, const IterScalars* sc, cudaStream_t st) {
+                         float lr, const IterScalars* sc, const ImageSlots& slots,
+                         cudaStream_t st) {
   VirtualMap vm;
   vm.n_arm = lay.n_arm; vm.up0 = lay.up0; vm.syn0 = lay.syn0;
   vm.n1x1 = 11 * a.C + 3; vm.nconv = a.NR * 84; vm.K2 = a.K * a.K; vm.n_up = lay.n_up;
@@ -184,7 +195,7 @@ cudaError_t param_update(const Layout& lay, const Arch& a, const float* part2, i
   vm.n_virtual = vm.vup + (kLevels - 1) * vm.K2;
   return launch_k(k_param_update, dim3((lay.total + 127) / 128), dim3(128), 0, st, vm, part2,
                   slices, params, m, v, grad_out, apply ? 1 : 0, lr,
-                  const_cast<IterScalars*>(sc), lay.total);
+                  const_cast<IterScalars*>(sc), lay.total, slots);
 }
 
 // Gradient of a latent: the synthesis path, plus lambda/(HW) times the rate terms in

@@ -1147,14 +1147,24 @@ __global__ void k_syn_image(const float* __restrict__ syn, int C, int NR,
 
 size_t syn_image_bytes() { return sizeof(SynBank); }
 
-cudaError_t syn_upload(const float* d_params, const Layout& lay, const Arch& a, void* d_image,
-                       cudaStream_t st) {
+cudaError_t syn_build_image(const float* d_params, const Layout& lay, const Arch& a,
+                            void* d_image, cudaStream_t st) {
   k_syn_image<<<1, 256, 0, st>>>(d_params + lay.syn0, a.C, a.NR, d_params + lay.up0,
                                  lay.n_up * a.K * a.K, (SynBank*)d_image);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t syn_copy_bank(const void* d_image, cudaStream_t st) {
   return cudaMemcpyToSymbolAsync(c_synbank, d_image, sizeof(SynBank), 0,
                                  cudaMemcpyDeviceToDevice, st);
 }
+
+cudaError_t syn_upload(const float* d_params, const Layout& lay, const Arch& a, void* d_image,
+                       cudaStream_t st) {
+  cudaError_t e = syn_build_image(d_params, lay, a, d_image, st);
+  return e != cudaSuccess ? e : syn_copy_bank(d_image, st);
+}
+
+int syn_image_weight_floats() { return (int)(sizeof(SynBank) / sizeof(float)); }
 
 }  // namespace cc
