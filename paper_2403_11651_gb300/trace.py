@@ -69,7 +69,7 @@ def main():
         cc.cc_free(ctx)
     recs = sorted((buf[i].t, names.get(buf[i].hash, hex(buf[i].hash)), buf[i].gx, buf[i].gy,
                    buf[i].bx) for i in range(min(n, 8192)))
-    starts = [i for i, r in enumerate(recs) if r[1] == "k_arm_image"]
+    starts = [i for i, r in enumerate(recs) if r[1] == "k_quantize"]
     print(f"{a.config} {H}x{W}: {n} kernel records, {len(starts)} iterations")
     for idx, (s0, s1) in enumerate(zip(starts, starts[1:])):
         if idx != 1 and not a.all:
