@@ -33,9 +33,9 @@ UNIT = "Mpixel-iter/s"
 PAPER_DERIVED_MPXIT = 22.5   # 512x768, 2300-MAC, 102 950 iterations in ~30 min (Sec. V, Fig. 5)
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one launch of the ARM kernel on this workload, from the ncu
-# capture summarised in profiles/k_arm_512x768_full.md; None when the kernel has changed
+# capture summarised in profiles/k_arm_tc_512x768.md; None when the kernel has changed
 # since the counters were taken
-ARM_DRAM_BYTES_PER_LAUNCH = None
+ARM_DRAM_BYTES_PER_LAUNCH = 2242048 + 579840
 
 
 def dist_env():

@@ -14,6 +14,7 @@ ARCHS = {
     "c1": (8, 2, 8, 1, 8, 2),
     "c2": (24, 2, 8, 1, 40, 2),
     "t300": (8, 1, 4, 0, 8, 1),
+    "t545": (8, 2, 4, 0, 16, 2),
     "t1079": (16, 2, 4, 0, 16, 2),
 }
 

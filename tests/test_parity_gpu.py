@@ -49,7 +49,7 @@ def test_noise_bit_exact(H, W):
         p.close()
 
 
-@pytest.mark.parametrize("arch", ["c1", "c2", "t300", "t1079"])
+@pytest.mark.parametrize("arch", ["c1", "c2", "t300", "t545", "t1079"])
 @pytest.mark.parametrize("H,W", SIZES)
 def test_forward_and_gradients(arch, H, W):
     p = Pair(config_dict(arch, lam=1e-2), H, W, seed=3, random_state=True)
