@@ -32,7 +32,11 @@ listed with its reason in the design notes of the repository):
 * 3x3 convolutions read with replicate padding.
 * D = mean of the 3HW squared errors; R = total bits / (H W) (bits per pixel).
 * Quantisation proxy: y_hat = y + u with uniform noise u, or y_hat = rint(y) with a
-  straight-through gradient in the last part of training.
+  straight-through gradient in the last part of training.  With a soft-rounding
+  temperature T > 0 (C3's proxy, to which Sec. II "Encoding" refers), the noise phase uses
+  y_hat = s_T(s_T(y) + u) with the soft rounding
+  s_T(x) = floor(x) + 1/2 + tanh((x - floor(x) - 1/2) / T) / (2 tanh(1 / (2T))),
+  differentiated through both soft roundings.
 * Adam: beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected, one learning rate for all.
 """
 from __future__ import annotations
@@ -72,6 +76,7 @@ class Train:
     total_iters: int = 10000
     ste_frac: float = 0.0    # last fraction of iterations with straight-through rounding
     seed: int = 0
+    soft_temp: float = 0.0   # C3 soft-rounding temperature of the noise phase; 0: y + u
 
     @property
     def ste_start(self) -> int:
@@ -161,10 +166,20 @@ def params_from_numpy(named: dict, arch: Arch, requires_grad=True) -> dict:
 # Quantisation proxy (Sec. II "Encoding")
 # --------------------------------------------------------------------------------------
 
-def quantize(y: torch.Tensor, u, hard: bool) -> torch.Tensor:
-    """Noise: y + u.  Hard: rint(y) (round half to even) with the identity as gradient."""
+def soft_round(x: torch.Tensor, T: float) -> torch.Tensor:
+    """C3's soft rounding with temperature T: integers and half-integers are fixed points,
+    it tends to rounding as T -> 0 and to the identity as T grows."""
+    f = torch.floor(x)
+    return f + 0.5 + 0.5 * torch.tanh((x - f - 0.5) / T) / math.tanh(0.5 / T)
+
+
+def quantize(y: torch.Tensor, u, hard: bool, soft_temp: float = 0.0) -> torch.Tensor:
+    """Noise: y + u, or s_T(s_T(y) + u) with a soft-rounding temperature T = soft_temp > 0.
+    Hard: rint(y) (round half to even) with the identity as gradient."""
     if hard:
         return y + (torch.round(y) - y).detach()
+    if soft_temp > 0.0:
+        return soft_round(soft_round(y, soft_temp) + u, soft_temp)
     return y + u
 
 
@@ -299,11 +314,12 @@ def synthesis(feat: torch.Tensor, P: dict, arch: Arch) -> torch.Tensor:
 # Loss, eq. (1)
 # --------------------------------------------------------------------------------------
 
-def forward(x, y_levels, P, arch: Arch, lam: float, u_levels=None, hard=False):
+def forward(x, y_levels, P, arch: Arch, lam: float, u_levels=None, hard=False,
+            soft_temp: float = 0.0):
     """Returns (loss, D, R_bpp, x_hat, y_hat levels).  x: [3, H, W] float64 in [0, 1]."""
     H, W = x.shape[1], x.shape[2]
     shapes = level_shapes(H, W, arch.levels)
-    yhat = [quantize(y_levels[l], None if hard else u_levels[l], hard)
+    yhat = [quantize(y_levels[l], None if hard else u_levels[l], hard, soft_temp)
             for l in range(arch.levels)]
     R = total_bits(yhat, P, arch) / (H * W)
     xhat = synthesis(upsample_all(yhat, P, arch, shapes), P, arch)
@@ -312,7 +328,7 @@ def forward(x, y_levels, P, arch: Arch, lam: float, u_levels=None, hard=False):
 
 
 @torch.no_grad()
-def decision_margins(x, y_levels, P, arch: Arch, u_levels=None, hard=False):
+def decision_margins(x, y_levels, P, arch: Arch, u_levels=None, hard=False, soft_temp=0.0):
     """Distance of every discrete decision of the forward pass to its tie.
 
     Where a decision sits within rounding error of its tie (a ReLU pre-activation near 0,
@@ -324,7 +340,7 @@ def decision_margins(x, y_levels, P, arch: Arch, u_levels=None, hard=False):
     """
     H, W = x.shape[1], x.shape[2]
     shapes = level_shapes(H, W, arch.levels)
-    yhat = [torch.round(y) if hard else y + u for y, u in
+    yhat = [torch.round(y) if hard else quantize(y, u, False, soft_temp) for y, u in
             zip(y_levels, u_levels if u_levels is not None else [None] * arch.levels)]
     offs = causal_offsets(arch.arm_ctx)
     arm = []
@@ -390,7 +406,7 @@ class OracleEncoder:
         if u_levels is None and not hard:
             u_levels = self.noise(self.t)
         loss, D, R, _, _ = forward(self.x, self.y, self.P, self.arch, self.train.lam,
-                                   u_levels, hard)
+                                   u_levels, hard, self.train.soft_temp)
         grads = torch.autograd.grad(loss, self.tensors)
         return float(loss.detach()), float(D.detach()), float(R.detach()), [g.detach() for g in grads]
 
@@ -415,7 +431,8 @@ class OracleEncoder:
     def rd_cost(self, hard: bool = True):
         """(D, R_bpp, D + lambda R) with rint latents and no noise (or the current noise)."""
         u = None if hard else self.noise(self.t)
-        loss, D, R, _, _ = forward(self.x, self.y, self.P, self.arch, self.train.lam, u, hard)
+        loss, D, R, _, _ = forward(self.x, self.y, self.P, self.arch, self.train.lam, u, hard,
+                                   self.train.soft_temp)
         return float(D), float(R), float(loss)
 
     @torch.no_grad()

@@ -452,3 +452,83 @@ def test_training_reduces_rd_cost():
     for _ in range(39):
         last = enc.step()[0]
     assert last < 0.5 * first
+
+
+# ---------------------------------------------------------------- C3 soft-rounding proxy
+
+def test_soft_round_fixed_points_and_symmetry():
+    """Integers and half-integers are fixed points; s_T(-x) = -s_T(x); strictly increasing."""
+    for T in (0.05, 0.3, 1.0, 4.0):
+        k = torch.arange(-6, 7, dtype=torch.float64)
+        assert torch.max(torch.abs(oc.soft_round(k, T) - k)) < 1e-12
+        assert torch.max(torch.abs(oc.soft_round(k + 0.5, T) - (k + 0.5))) < 1e-12
+        x = torch.linspace(-4.9, 4.9, 2001, dtype=torch.float64)
+        assert torch.max(torch.abs(oc.soft_round(-x, T) + oc.soft_round(x, T))) < 1e-12
+        assert bool(torch.all(torch.diff(oc.soft_round(x, T)) > 0))
+
+
+def test_soft_round_continuous_across_integers():
+    for T in (0.1, 0.3, 2.0):
+        for n in (-2.0, 0.0, 3.0):
+            lo = oc.soft_round(torch.tensor(n - 1e-9, dtype=torch.float64), T)
+            hi = oc.soft_round(torch.tensor(n + 1e-9, dtype=torch.float64), T)
+            assert abs(float(hi - lo)) < 1e-6
+
+
+def test_soft_round_limits():
+    """T -> 0: rounding (away from the half-integers); large T: the identity."""
+    x = torch.tensor([-2.3, -1.2, -0.1, 0.2, 0.7, 1.4, 2.95], dtype=torch.float64)
+    assert torch.equal(oc.soft_round(x, 1e-3), torch.round(x))
+    assert torch.max(torch.abs(oc.soft_round(x, 1e3) - x)) < 1e-6
+
+
+def test_soft_proxy_gradient_central_differences():
+    """d/dy of s_T(s_T(y) + u) by autograd matches central differences of the proxy."""
+    rng = np.random.default_rng(5)
+    for T in (0.1, 0.3, 1.0):
+        y = torch.tensor(rng.normal(0, 2, 200), dtype=torch.float64, requires_grad=True)
+        u = torch.tensor(rng.uniform(-0.5, 0.5, 200), dtype=torch.float64)
+        (g,) = torch.autograd.grad(oc.quantize(y, u, False, T).sum(), y)
+        eps = 1e-6
+        with torch.no_grad():
+            fd = (oc.quantize(y + eps, u, False, T) - oc.quantize(y - eps, u, False, T)) / (2 * eps)
+        # relative error, with an absolute floor where the derivative is tiny (flat steps)
+        assert torch.max(torch.abs(fd - g) / torch.clamp(torch.abs(g), min=1e-4)) < 1e-5
+
+
+def test_soft_proxy_loss_gradients_central_differences():
+    """The whole loss with the soft proxy: latent gradients against central differences."""
+    arch = oc.Arch(arm_ctx=8, syn_hidden=8)
+    enc = _small_encoder(arch)
+    enc.train = oc.Train(lam=enc.train.lam, total_iters=100, soft_temp=0.3)
+    u = enc.noise(0)
+    _, _, _, grads = enc.loss_and_grads(u)
+    rng = np.random.default_rng(21)
+    checked = 0
+    for _ in range(200):
+        l = int(rng.integers(0, len(enc.y)))
+        t = enc.y[l]
+        flat = t.detach().view(-1)
+        j = int(rng.integers(0, flat.numel()))
+        g = float(grads[l].view(-1)[j])
+        old = float(flat[j])
+
+        def loss_at():
+            with torch.no_grad():
+                return float(oc.forward(enc.x, enc.y, enc.P, arch, enc.train.lam, u, False, 0.3)[0])
+
+        def fd(eps):
+            flat[j] = old + eps
+            lp = loss_at()
+            flat[j] = old - eps
+            lm = loss_at()
+            flat[j] = old
+            return (lp - lm) / (2 * eps)
+
+        tol = 2.5e-5 * max(abs(g), 1e-4)
+        f1, f2 = fd(1e-4), fd(5e-5)
+        if abs(f1 - f2) > tol:   # a kink between the two steps
+            continue
+        checked += 1
+        assert abs(f1 - g) <= 1e-4 * max(abs(g), 1e-4), (l, j, g, f1)
+    assert checked > 150
