@@ -74,6 +74,10 @@ typedef struct {
     int total_iters;   /* schedule length; decides where straight-through rounding starts */
     float ste_frac;    /* last fraction of total_iters using rint + straight-through     */
     uint64_t seed;     /* key of the Philox4x32-10 quantisation noise                    */
+    float soft_temp;   /* 0: noise phase y_hat = y + u.  T > 0: C3's soft-rounding proxy
+                        * y_hat = s_T(s_T(y) + u), s_T(x) = floor(x) + 1/2 +
+                        * tanh((x - floor(x) - 1/2)/T) / (2 tanh(1/(2T))), differentiated
+                        * through both soft roundings (Sec. II "Encoding" refers to C3)    */
 } cc_config;
 
 /* Number of decoder parameters of a configuration (Table 1 "Param" column). */

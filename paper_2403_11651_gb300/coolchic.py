@@ -35,7 +35,8 @@ class cc_config(ctypes.Structure):
     _fields_ = [("levels", c_int), ("arm_ctx", c_int), ("arm_layers", c_int),
                 ("up_kernel", c_int), ("up_per_level", c_int), ("syn_hidden", c_int),
                 ("syn_res3x3", c_int), ("lam", c_float), ("lr", c_float),
-                ("total_iters", c_int), ("ste_frac", c_float), ("seed", c_uint64)]
+                ("total_iters", c_int), ("ste_frac", c_float), ("seed", c_uint64),
+                ("soft_temp", c_float)]
 
 
 _LIB = None
@@ -143,7 +144,8 @@ def make_config(d: dict, seed: int | None = None, lam: float | None = None) -> c
                      up_per_level=int(d["up_per_level"]), syn_hidden=d["syn_hidden"],
                      syn_res3x3=d["syn_res3x3"], lam=d["lam"] if lam is None else lam,
                      lr=d["lr"], total_iters=d["total_iters"], ste_frac=d["ste_frac"],
-                     seed=(d.get("seed", 0) if seed is None else seed))
+                     seed=(d.get("seed", 0) if seed is None else seed),
+                     soft_temp=float(d.get("soft_temp", 0.0)))
 
 
 def load_config(name: str) -> dict:

@@ -79,6 +79,7 @@ int validate(const cc_config* c) {
   if (c->syn_res3x3 != 1 && c->syn_res3x3 != 2) return CC_EINVAL;
   if (!(c->lam >= 0.f) || !(c->lr > 0.f) || c->total_iters < 0) return CC_EINVAL;
   if (!(c->ste_frac >= 0.f && c->ste_frac <= 1.f)) return CC_EINVAL;
+  if (!(c->soft_temp >= 0.f && c->soft_temp < 1e30f)) return CC_EINVAL;
   return CC_OK;
 }
 
@@ -151,6 +152,7 @@ struct cc_ctx {
   void* mem = nullptr;
   size_t bytes = 0;
   float *x, *y, *my, *vy, *yhat, *yhat_bord, *gsyn, *gself, *dctx, *noise;
+  float* dq;   // d y_hat / d y of the soft-rounding proxy
   float *params, *mp, *vp;
   float *hbuf, *dhbuf, *dz;
   float *part_arm, *part_bits, *part_d, *part_conv, *part_syn, *part_up, *part2;
@@ -194,6 +196,7 @@ size_t plan(cc_ctx* c, char* base) {
   c->gsyn = (float*)take(L);
   c->gself = (float*)take(L);
   c->noise = (float*)take(L);
+  c->dq = (float*)take(L);
   c->dctx = (float*)take((size_t)a.N * L);
   c->params = (float*)take((size_t)c->lay.total * sizeof(float));
   c->mp = (float*)take((size_t)c->lay.total * sizeof(float));
@@ -287,6 +290,14 @@ void build_sections(cc_ctx* c) {
   t.n = n;
 }
 
+// Whether a pass quantising with mode qmode used the soft-rounding proxy: 0 never (no
+// temperature, or rint), 1 always (given or drawn noise), 2 in the noise phase of the
+// schedule (decided on the device from the iteration index).
+int soft_mode(const cc_ctx* c, int qmode) {
+  if (!(c->cfg.soft_temp > 0.f) || qmode == 1) return 0;
+  return qmode == 0 ? 2 : 1;
+}
+
 ImageSlots image_slots(cc_ctx* c) {
   ImageSlots sl;
   sl.map = c->slot_map;
@@ -363,7 +374,7 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
   CKE(arm_copy_bank(c->arm_image, s));
   CKE(syn_copy_bank(c->syn_image, s));
   CKE(quantize_launch(c->geo, c->y, c->yhat, c->yhat_bord, c->noise, qmode, c->sc, c->ste_start, c->cfg.seed,
-                      -1, s));
+                      -1, c->cfg.soft_temp, c->dq, s));
   CKE(mark(1));
   if (fork) {
     CKE(cudaEventRecord(c->ev_fork, s));
@@ -407,7 +418,8 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
     CKE(latent_update(c->geo, c->gsyn, c->gself, (float)((double)c->cfg.lam / (double)c->HW),
                       c->y, c->my, c->vy, grad_out, apply, c->cfg.lr, c->sc, c->part_d,
                       c->grid_tiles, c->part_bits, c->grid_arm, 1.0 / (3.0 * (double)HW),
-                      1.0 / (double)HW, (double)c->cfg.lam, c->log, advance, s));
+                      1.0 / (double)HW, (double)c->cfg.lam, c->log, advance, c->dq,
+                      soft_mode(c, qmode), c->ste_start, s));
   } else {
     if (fork) CKE(cudaStreamWaitEvent(s, c->ev_join, 0));
     CKE(finish_iteration(c->part_d, c->grid_tiles, c->part_bits, c->grid_arm,
@@ -685,7 +697,7 @@ int cc_decode(cc_ctx* c, float* rgb_out_hwc) {
   const size_t HW = (size_t)c->HW;
   CK(syn_upload(c->params, c->lay, a, c->syn_image, c->st));
   CK(quantize_launch(c->geo, c->y, c->yhat, c->yhat_bord, c->noise, 1, c->sc, c->ste_start, c->cfg.seed, -1,
-                     c->st));
+                     0.f, nullptr, c->st));
   CK(up_forward(a, c->geo, c->yhat, c->up, c->grid_syn, c->st));
   CK(syn_forward(a, c->geo, c->yhat, c->up, c->x, c->hbuf, c->dhbuf + (size_t)a.NR * 3 * HW,
                  c->part_d, c->part_conv, c->grid_tiles, c->st));
@@ -830,7 +842,7 @@ int cc_noise(cc_ctx* c, int iter, float* out) {
   if (!c || !out || iter < 0) return CC_EINVAL;
   CK(cudaSetDevice(c->dev));
   CK(quantize_launch(c->geo, c->y, c->yhat, c->yhat_bord, c->noise, 4, c->sc, c->ste_start, c->cfg.seed, iter,
-                     c->st));
+                     0.f, nullptr, c->st));
   int e = copy_latents(c, c->yhat, out, true);
   if (e) return e;
   CK(cudaStreamSynchronize(c->st));

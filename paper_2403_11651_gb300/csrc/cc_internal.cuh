@@ -199,7 +199,8 @@ cudaError_t syn_prepare(const Arch& a);   // kernel attributes; call once before
 // iteration bookkeeping (cc_iter.cu)
 cudaError_t quantize_launch(const Geo& g, const float* y, float* yhat, float* yhat_bord,
                             const float* noise, int mode, const IterScalars* sc, int ste_start,
-                            uint64_t seed, int iter_override, cudaStream_t st);
+                            uint64_t seed, int iter_override, float soft_temp, float* dq,
+                            cudaStream_t st);
 // Context gradient of the rate: gself[q] += sum over the N context positions k of
 // dctx[k][q - offset_k] (the ARM's gradients with respect to its inputs), in place.
 cudaError_t ctx_gather(const Geo& g, const int2* d_offsets, int N, float* gself,
@@ -224,7 +225,8 @@ cudaError_t latent_update(const Geo& g, const float* gsyn, const float* grate, f
                           float* y, float* m, float* v, float* grad_out, bool apply, float lr,
                           IterScalars* sc, const float* part_d, int nd, const float* part_bits,
                           int nb, double d_scale, double r_scale, double lam, double* log,
-                          bool advance, cudaStream_t st);
+                          bool advance, const float* dq, int soft, int ste_start,
+                          cudaStream_t st);
 cudaError_t finish_iteration(const float* part_d, int nd, const float* part_bits, int nb,
                              double d_scale, double r_scale, double lam, IterScalars* sc,
                              double* log, bool advance, cudaStream_t st,

@@ -28,12 +28,23 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint2 k) {
 //        4 write the Philox noise itself.
 // Noise of latent i of level l at iteration t: word (i mod 4) of
 // Philox4x32-10(counter (i div 4, l, t, 0), key (seed lo, seed hi)), u = (w >> 8) 2^-24 - 1/2.
+// C3 soft rounding with temperature T (inv_t = 1/T, k = 1 / (2 tanh(1/(2T)))):
+// s(x) = floor(x) + 1/2 + k tanh((x - floor(x) - 1/2) / T) and its derivative
+// s'(x) = k (1 - tanh^2(...)) / T.
+__device__ __forceinline__ float soft_round(float x, float inv_t, float k, float& ds) {
+  const float f = floorf(x);
+  const float th = tanhf((x - f - 0.5f) * inv_t);
+  ds = k * (1.f - th * th) * inv_t;
+  return f + 0.5f + k * th;
+}
+
 __global__ void __launch_bounds__(256) k_quantize(Geo g, const float* __restrict__ y,
                                                   float* __restrict__ yhat,
                                                   float* __restrict__ yhat_bord,
                                                   const float* __restrict__ noise, int mode,
                                                   const IterScalars* sc, int ste_start,
-                                                  uint2 key, int iter_override) {
+                                                  uint2 key, int iter_override, float soft_temp,
+                                                  float* __restrict__ dq) {
   pdl_wait();
   pdl_trigger();
   const int l = blockIdx.y;
@@ -55,11 +66,21 @@ __global__ void __launch_bounds__(256) k_quantize(Geo g, const float* __restrict
     float out;
     if (m == 1) {
       out = rintf(yv);
-    } else if (m == 2) {
-      out = yv + noise[base + i];
+    } else if (m == 4) {
+      out = (float)(words[e] >> 8) * 5.9604644775390625e-08f - 0.5f;
     } else {
-      const float u = (float)(words[e] >> 8) * 5.9604644775390625e-08f - 0.5f;
-      out = m == 4 ? u : yv + u;
+      const float u = m == 2 ? noise[base + i]
+                             : (float)(words[e] >> 8) * 5.9604644775390625e-08f - 0.5f;
+      if (soft_temp > 0.f) {
+        // y_hat = s(s(y) + u), d y_hat / d y = s'(s(y) + u) s'(y)
+        const float inv_t = 1.f / soft_temp, k = 0.5f / tanhf(0.5f * inv_t);
+        float d1, d2;
+        const float s1 = soft_round(yv, inv_t, k, d1);
+        out = soft_round(s1 + u, inv_t, k, d2);
+        dq[base + i] = d2 * d1;
+      } else {
+        out = yv + u;
+      }
     }
     yhat[base + i] = out;
     if (yhat_bord) {
@@ -71,14 +92,15 @@ __global__ void __launch_bounds__(256) k_quantize(Geo g, const float* __restrict
 
 cudaError_t quantize_launch(const Geo& g, const float* y, float* yhat, float* yhat_bord,
                             const float* noise, int mode, const IterScalars* sc, int ste_start,
-                            uint64_t seed, int iter_override, cudaStream_t st) {
+                            uint64_t seed, int iter_override, float soft_temp, float* dq,
+                            cudaStream_t st) {
   int maxn = 0;
   for (int l = 0; l < kLevels; ++l) maxn = g.h[l] * g.w[l] > maxn ? g.h[l] * g.w[l] : maxn;
   const int groups = (maxn + 3) / 4;
   dim3 grid((groups + 255) / 256, kLevels);
   const uint2 key = make_uint2((uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32));
   k_quantize<<<grid, 256, 0, st>>>(g, y, yhat, yhat_bord, noise, mode, sc, ste_start, key,
-                                   iter_override);
+                                   iter_override, dq ? soft_temp : 0.f, dq);
   return cudaGetLastError();
 }
 
@@ -267,7 +289,9 @@ __global__ void __launch_bounds__(256) k_latent_update(Geo g, const float* __res
                                                        const float* __restrict__ grate,
                                                        float rate_scale, float* y, float* m,
                                                        float* v, float* grad_out, int apply,
-                                                       float lr, IterScalars* sc, FinishArgs fa) {
+                                                       float lr, IterScalars* sc, FinishArgs fa,
+                                                       const float* __restrict__ dq, int soft,
+                                                       int ste_start) {
   pdl_wait();
   pdl_trigger();
   // one thread per element of the latent-shaped buffers; alignment gaps between planes skip
@@ -277,7 +301,9 @@ __global__ void __launch_bounds__(256) k_latent_update(Geo g, const float* __res
   for (int k = 1; k < kLevels; ++k) l = q >= g.off[k] ? k : l;
   const long long i = q - g.off[l];
   if (q < g.n_pad && i < (long long)g.h[l] * g.w[l]) {
-    const float gt = __ldg(gsyn + q) + rate_scale * __ldg(grate + q);
+    float gt = __ldg(gsyn + q) + rate_scale * __ldg(grate + q);   // dL / d y_hat
+    // soft-rounding pass: dL/dy = dL/dy_hat * dy_hat/dy (1: always, 2: noise phase only)
+    if (soft == 1 || (soft == 2 && sc->t < ste_start)) gt *= __ldg(dq + q);
     if (grad_out) {
       long long fo = 0;
       for (int k = 0; k < l; ++k) fo += (long long)g.h[k] * g.w[k];
@@ -308,14 +334,15 @@ cudaError_t latent_update(const Geo& g, const float* gsyn, const float* grate, f
                           float* y, float* m, float* v, float* grad_out, bool apply, float lr,
                           IterScalars* sc, const float* part_d, int nd, const float* part_bits,
                           int nb, double d_scale, double r_scale, double lam, double* log,
-                          bool advance, cudaStream_t st) {
+                          bool advance, const float* dq, int soft, int ste_start,
+                          cudaStream_t st) {
   FinishArgs fa;
   fa.part_d = part_d; fa.nd = nd; fa.part_bits = part_bits; fa.nb = nb;
   fa.d_scale = d_scale; fa.r_scale = r_scale; fa.lam = lam; fa.log = log;
   fa.advance = advance ? 1 : 0;
   const int blocks = (int)((g.n_pad + 255) / 256);
   return launch_k(k_latent_update, dim3(blocks), dim3(256), 0, st, g, gsyn, grate, rate_scale, y,
-                  m, v, grad_out, apply ? 1 : 0, lr, sc, fa);
+                  m, v, grad_out, apply ? 1 : 0, lr, sc, fa, dq, soft, ste_start);
 }
 
 cudaError_t finish_iteration(const float* part_d, int nd, const float* part_bits, int nb,

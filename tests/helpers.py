@@ -19,11 +19,11 @@ ARCHS = {
 }
 
 
-def config_dict(arch: str, lam=1e-3, lr=1e-2, total_iters=100, ste_frac=0.0):
+def config_dict(arch: str, lam=1e-3, lr=1e-2, total_iters=100, ste_frac=0.0, soft_temp=0.0):
     n, nl, k, pl, c, nr = ARCHS[arch]
     return dict(levels=7, arm_ctx=n, arm_layers=nl, up_kernel=k, up_per_level=bool(pl),
                 syn_hidden=c, syn_res3x3=nr, lam=lam, lr=lr, total_iters=total_iters,
-                ste_frac=ste_frac)
+                ste_frac=ste_frac, soft_temp=soft_temp)
 
 
 def oracle_arch(d: dict) -> oc.Arch:
@@ -53,7 +53,8 @@ class Pair:
         self.oracle = oc.OracleEncoder(
             self.rgb, oracle_arch(d),
             oc.Train(lam=d["lam"], lr=d["lr"], total_iters=d["total_iters"],
-                     ste_frac=d["ste_frac"], seed=seed), self.init)
+                     ste_frac=d["ste_frac"], seed=seed, soft_temp=d.get("soft_temp", 0.0)),
+            self.init)
         if random_state:
             y = [rng.normal(0, state_scale, s).astype(np.float32) for s in cc.level_shapes(H, W)]
             self.set_latents(y)
@@ -106,20 +107,24 @@ def margins(pair, noise_levels=None, hard=False):
     u = None if noise_levels is None else [torch.tensor(np.asarray(a, np.float64))
                                            for a in noise_levels]
     return oc.decision_margins(enc.x, [t.detach() for t in enc.y],
-                               {k: v.detach() for k, v in enc.P.items()}, enc.arch, u, hard)
+                               {k: v.detach() for k, v in enc.P.items()}, enc.arch, u, hard,
+                               enc.train.soft_temp)
 
 
 def assert_latents_close_with_ties(got, ref, level, arm_margin, syn_margin, offsets, rtol,
-                                   delta=1e-5):
+                                   delta=1e-5, max_outliers=None):
     """Element-wise tolerance on one latent level, except at latents whose gradient depends
     on a decision within `delta` of its tie in the oracle (an ARM decision of the latent
     itself or of a latent whose context holds it, or a synthesis ReLU in its pixel
-    footprint).  Such exemptions must stay rare."""
+    footprint).  Such exemptions must stay rare: at most max_outliers (default
+    max(4, 1e-4 of the level)); one ARM tie reaches the latent and the N latents whose
+    context holds it."""
     got = np.asarray(got, np.float64)
     ref = np.asarray(ref, np.float64)
     scale = float(np.max(np.abs(ref)))
     bad = np.argwhere(np.abs(got - ref) > rtol * scale)
-    assert len(bad) <= max(4, 1e-4 * ref.size), f"level {level}: {len(bad)} outliers"
+    cap = max(4, 1e-4 * ref.size) if max_outliers is None else max_outliers
+    assert len(bad) <= cap, f"level {level}: {len(bad)} outliers"
     h, w = ref.shape
     Hp, Wp = syn_margin.shape
     for r, c in bad:
