@@ -54,7 +54,8 @@ enum {
     CC_ECUDA = -3,        /* a CUDA runtime call failed (see cc_last_cuda_error) */
     CC_ETIMEOUT = -4,     /* a bounded device wait gave up */
     CC_ENONFINITE = -5,   /* the loss became NaN or infinite */
-    CC_ESTATE = -6        /* state blob of the wrong size, version or shape */
+    CC_ESTATE = -6,       /* state blob of the wrong size, version or shape */
+    CC_ESIZE = -7         /* output buffer too small; the size needed was returned  */
 };
 
 typedef struct cc_ctx cc_ctx;
@@ -212,6 +213,43 @@ const char* cc_strerror(int code);
 #define CC_NOALLOC_MAX_TILES 65536
 int cc_rate_bits_noalloc(const cc_config* cfg, const float* yhat_flat, int H, int W,
                          const float* params, void* cuda_stream, double* bits_out);
+
+/* Latent bitstream.  Sec. II "Encoding": once the encoder has converged, the latents are
+ * entropy coded with a range coder driven by the ARM's probability model p_psi; Sec. II
+ * "Decoding" (Fig. 2): the decoder reads the latent grids with that model, each latent
+ * conditioned on its already-decoded causal neighbours, then upsamples and synthesises.
+ * The decoder re-evaluates the ARM, so both sides run it in integer arithmetic:
+ *   - ARM weights and biases rounded (half to even) to multiples of 2^-8 (Q8; weights
+ *     clamped to +-2^20, biases to +-2^28 in Q8 units); inputs = integer latents x 256; a
+ *     layer z = ((sum W a) + 128) >> 8 + b in 64-bit integers, saturated to +-2^28; LinR
+ *     output a + max(z, 0), saturated; the output layer gives (mu, log-scale) in Q8;
+ *   - probabilities from 744 Laplace frequency tables (93 log-scale bins of width 1/8 from
+ *     ln 0.01, 8 bins of mu's fraction; symbols y - floor(mu) in [-64, 64] plus one escape
+ *     per tail, the excess as an order-0 Exp-Golomb code), built on the host;
+ *   - a 32-bit range coder with frequencies out of 2^16, one substream per latent row.
+ * Layout: "CCF1", H, W (u32 little endian), 8 architecture bytes (levels, N, LinR layers,
+ * k, per-level filters, C, 3x3 layers, 0), the Q8 ARM parameters (i32), the other
+ * parameters (f32) in flat parameter order, the byte count of every row substream
+ * (LEB128; levels 0..L-1, rows top to bottom), the substreams.
+ *
+ * cc_write_bitstream: codes rint(y) of the context's latents with its current
+ *   parameters.  out (host or device) receives *nbytes bytes; with out == NULL only
+ *   *nbytes is set; with capacity < *nbytes nothing is written and CC_ESIZE returned.
+ *   A quantised latent above 2^20 in magnitude gives CC_EINVAL.  Synchronises.
+ * cc_bitstream_info: configuration (architecture fields; lam, schedule and seed zero,
+ *   lr 1) and image size of a bitstream in host memory.
+ * cc_decode_bitstream: decodes a bitstream in host memory on the current device and
+ *   the given stream (cudaStream_t or NULL): the latent rows as a wavefront (row r
+ *   decodes position x at step x + lag r, lag 3 for N = 8 and 4 for N = 16 or 24; one
+ *   block per level, so ceil(W / lag) <= 1024), then the float32 upsampling and
+ *   synthesis.  Optional outputs (host or device): rgb_out_hwc (H x W x 3 floats, not
+ *   clamped, as cc_decode), latents_out (cc_latent_count int32, flat latent order),
+ *   latent_ms (device time of the latent decoding).  It holds a temporary context (the
+ *   memory of cc_init_image) for the call.  Synchronises. */
+int cc_write_bitstream(cc_ctx* ctx, uint8_t* out, size_t capacity, size_t* nbytes);
+int cc_bitstream_info(const uint8_t* bs, size_t nbytes, cc_config* cfg, int* H, int* W);
+int cc_decode_bitstream(const uint8_t* bs, size_t nbytes, void* cuda_stream,
+                        float* rgb_out_hwc, int32_t* latents_out, float* latent_ms);
 
 /* Text of the last error seen by the library in this thread ("" if none). */
 const char* cc_last_cuda_error(void);

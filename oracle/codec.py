@@ -299,18 +299,22 @@ def decode_symbol(dec: RangeDecoder, cum_row) -> int:
 # Substreams and bitstream
 # --------------------------------------------------------------------------------------
 
+def row_context(plane: np.ndarray, r: int, offsets) -> np.ndarray:
+    """[w, N] causal contexts of row r (only the rows the offsets reach are read)."""
+    r0 = max(0, r - max(-dy for dy, _ in offsets))
+    return context_int(plane[r0:r + 1], offsets)[r - r0]
+
+
 def encode_rows(plane: np.ndarray, Q: dict, arch: Arch, cum: np.ndarray, rows=None):
     """Substreams (bytes) of the given rows (default: all) of one level's integer plane."""
     offs = causal_offsets(arch.arm_ctx)
-    ctx = context_int(plane, offs)
-    mu_q, s_q = arm_fixed(ctx if rows is None else ctx[list(rows)], Q, arch)
-    t, m = table_index(mu_q, s_q)
-    rows = range(plane.shape[0]) if rows is None else rows
     out = []
-    for i, r in enumerate(rows):
+    for r in (range(plane.shape[0]) if rows is None else rows):
+        mu_q, s_q = arm_fixed(row_context(plane, r, offs), Q, arch)
+        t, m = table_index(mu_q, s_q)
         enc = RangeEncoder()
         for x in range(plane.shape[1]):
-            encode_symbol(enc, cum[t[i, x]], int(plane[r, x]) - int(m[i, x]))
+            encode_symbol(enc, cum[t[x]], int(plane[r, x]) - int(m[x]))
         out.append(enc.finish())
     return out
 

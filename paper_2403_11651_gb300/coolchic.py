@@ -19,6 +19,7 @@ import numpy as np
 from . import build as _build
 
 CC_OK, CC_EINVAL, CC_ENOMEM, CC_ECUDA, CC_ETIMEOUT, CC_ENONFINITE, CC_ESTATE = 0, -1, -2, -3, -4, -5, -6
+CC_ESIZE = -7
 LEVELS = 7
 
 
@@ -72,6 +73,9 @@ def _declare(lib):
         "cc_strerror": (ctypes.c_char_p, [c_int]),
         "cc_last_cuda_error": (ctypes.c_char_p, []),
         "cc_arm_kernel_ms": (c_int, [P, POINTER(ctypes.c_float)]),
+        "cc_write_bitstream": (c_int, [P, P, c_size_t, POINTER(c_size_t)]),
+        "cc_bitstream_info": (c_int, [P, c_size_t, P, POINTER(c_int), POINTER(c_int)]),
+        "cc_decode_bitstream": (c_int, [P, c_size_t, P, P, P, POINTER(ctypes.c_float)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -364,6 +368,42 @@ def cc_rate_bits_noalloc(cfg: cc_config, yhat_flat, H: int, W: int, params, stre
     return out.value
 
 
+def cc_write_bitstream(ctx) -> bytes:
+    """Range-coded bitstream of rint(y) and the decoder parameters of the context."""
+    n = c_size_t()
+    _check(_lib().cc_write_bitstream(ctx, None, 0, ctypes.byref(n)), "cc_write_bitstream")
+    buf = ctypes.create_string_buffer(max(1, n.value))
+    _check(_lib().cc_write_bitstream(ctx, buf, n.value, ctypes.byref(n)), "cc_write_bitstream")
+    return buf.raw[:n.value]
+
+
+def cc_bitstream_info(bs: bytes):
+    """(cc_config with the architecture fields, H, W) of a bitstream."""
+    cfg, H, W = cc_config(), c_int(), c_int()
+    buf = ctypes.create_string_buffer(bs, len(bs))
+    _check(_lib().cc_bitstream_info(buf, len(bs), ctypes.byref(cfg), ctypes.byref(H),
+                                    ctypes.byref(W)), "cc_bitstream_info")
+    return cfg, H.value, W.value
+
+
+def cc_decode_bitstream(bs: bytes, rgb_out=None, latents_out=None, stream=None, want_rgb=True,
+                        want_latents=True):
+    """Decode a bitstream: (image H x W x 3 float32 or None, int32 latents or None, ms of
+    the latent decoding)."""
+    cfg, H, W = cc_bitstream_info(bs)
+    if want_rgb and rgb_out is None:
+        rgb_out = np.empty((H, W, 3), np.float32)
+    if want_latents and latents_out is None:
+        latents_out = np.empty(cc_latent_count(cfg, H, W), np.int32)
+    ms = ctypes.c_float()
+    buf = ctypes.create_string_buffer(bs, len(bs))
+    _check(_lib().cc_decode_bitstream(buf, len(bs), _stream_handle(stream),
+                                      _ptr(rgb_out) if want_rgb else None,
+                                      _ptr(latents_out) if want_latents else None,
+                                      ctypes.byref(ms)), "cc_decode_bitstream")
+    return (rgb_out if want_rgb else None), (latents_out if want_latents else None), ms.value
+
+
 def cc_free(ctx):
     if ctx:
         _lib().cc_free(ctx)
@@ -378,4 +418,5 @@ EXPORTED = ["cc_param_count", "cc_latent_count", "cc_workspace_size", "cc_init_i
             "cc_get_grads", "cc_forward_backward", "cc_get_losses", "cc_iteration", "cc_noise",
             "cc_set_latents", "cc_get_latents", "cc_set_params", "cc_get_params",
             "cc_profile_phases", "cc_graph_kernel_count", "cc_arm_kernel_ms", "cc_rate_bits_noalloc",
-            "cc_get_state", "cc_set_state", "cc_free", "cc_strerror", "cc_last_cuda_error"]
+            "cc_get_state", "cc_set_state", "cc_write_bitstream", "cc_bitstream_info",
+            "cc_decode_bitstream", "cc_free", "cc_strerror", "cc_last_cuda_error"]

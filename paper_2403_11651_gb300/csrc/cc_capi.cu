@@ -913,6 +913,228 @@ int cc_set_state(cc_ctx* c, const void* buf, size_t nbytes) {
   return CC_OK;
 }
 
+// ---- latent bitstream -------------------------------------------------------------------
+
+}  // extern "C"
+
+namespace {
+
+constexpr uint8_t kBsMagic[4] = {'C', 'C', 'F', '1'};
+constexpr int kBsFixed = 20;   // magic, H, W, 8 architecture bytes
+
+// device buffer released on scope exit
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() { if (p) cudaFree(p); }
+  cudaError_t alloc(size_t n) { return cudaMalloc(&p, n ? n : 1); }
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+void put_u32(std::vector<uint8_t>& v, uint32_t x) {
+  for (int i = 0; i < 4; ++i) v.push_back((uint8_t)(x >> (8 * i)));
+}
+uint32_t get_u32(const uint8_t* p) {
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+void put_leb128(std::vector<uint8_t>& v, uint32_t x) {
+  do {
+    const uint8_t b = x & 0x7F;
+    x >>= 7;
+    v.push_back(b | (x ? 0x80 : 0));
+  } while (x);
+}
+bool get_leb128(const uint8_t* bs, size_t n, size_t& pos, uint32_t& x) {
+  x = 0;
+  for (int shift = 0; shift < 35; shift += 7) {
+    if (pos >= n) return false;
+    const uint8_t b = bs[pos++];
+    x |= (uint32_t)(b & 0x7F) << shift;
+    if (!(b & 0x80)) return true;
+  }
+  return false;
+}
+
+int set_msg(int code, const char* msg) {
+  cc::set_error_text(msg);
+  return code;
+}
+
+int parse_fixed(const uint8_t* bs, size_t n, cc_config* cfg, int* H, int* W) {
+  if (!bs || n < (size_t)kBsFixed || std::memcmp(bs, kBsMagic, 4) != 0)
+    return set_msg(CC_EINVAL, "not a latent bitstream (magic)");
+  const uint32_t h = get_u32(bs + 4), w = get_u32(bs + 8);
+  if (h < 1 || w < 1 || h > 16384 || w > 16384) return set_msg(CC_EINVAL, "bitstream image size");
+  cc_config c;
+  std::memset(&c, 0, sizeof(c));
+  c.levels = bs[12]; c.arm_ctx = bs[13]; c.arm_layers = bs[14]; c.up_kernel = bs[15];
+  c.up_per_level = bs[16]; c.syn_hidden = bs[17]; c.syn_res3x3 = bs[18];
+  c.lam = 0.f; c.lr = 1.f; c.total_iters = 0; c.ste_frac = 0.f; c.seed = 0; c.soft_temp = 0.f;
+  if (validate(&c) != CC_OK) return set_msg(CC_EINVAL, "bitstream architecture");
+  *cfg = c;
+  *H = (int)h;
+  *W = (int)w;
+  return CC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cc_write_bitstream(cc_ctx* c, uint8_t* out, size_t capacity, size_t* nbytes) {
+  if (!c || !nbytes) return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  const Arch& a = c->arch;
+  cudaStream_t st = c->st;
+  std::vector<float> p((size_t)c->lay.total);
+  CK(cudaMemcpyAsync(p.data(), c->params, p.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<int32_t> q((size_t)c->lay.n_arm);
+  if (!codec_quantize_arm(p.data(), a.N, a.NL, q.data()))
+    return set_msg(CC_ENONFINITE, "non-finite ARM parameter");
+  const CodecGeo cg = codec_geo(c->geo);
+  const std::vector<uint16_t>& tab = codec_tables();
+  DevBuf d_tab, d_sym, d_rows, d_len, d_flag, d_off, d_out;
+  CK(d_tab.alloc(codec_table_bytes()));
+  CK(d_sym.alloc((size_t)cg.n_lat * sizeof(int2)));
+  CK(d_rows.alloc((size_t)cg.buf_bytes));
+  CK(d_len.alloc((size_t)cg.rows * sizeof(int)));
+  CK(d_flag.alloc(sizeof(int)));
+  CK(d_off.alloc((size_t)cg.rows * sizeof(long long)));
+  CK(cudaMemcpyAsync(d_tab.p, tab.data(), codec_table_bytes(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(d_flag.p, 0, sizeof(int), st));
+  CK(codec_upload_arm(q.data(), (int)q.size(), st));
+  CK(codec_symbols(cg, c->geo, c->y, c->offs, a.N, a.NL, d_sym.as<int2>(), d_flag.as<int>(), st));
+  CK(codec_encode_rows(cg, d_sym.as<int2>(), d_tab.as<uint16_t>(), d_rows.as<uint8_t>(),
+                       d_len.as<int>(), d_flag.as<int>(), st));
+  std::vector<int> len((size_t)cg.rows);
+  int flag = 0;
+  CK(cudaMemcpyAsync(len.data(), d_len.p, len.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&flag, d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (flag & 1) return set_msg(CC_EINVAL, "a quantised latent exceeds 2^20 in magnitude");
+  if (flag & 2) return set_msg(CC_ECUDA, "substream overran its buffer");
+
+  std::vector<uint8_t> hdr(kBsMagic, kBsMagic + 4);
+  put_u32(hdr, (uint32_t)c->geo.H);
+  put_u32(hdr, (uint32_t)c->geo.W);
+  const uint8_t ab[8] = {(uint8_t)kLevels, (uint8_t)a.N, (uint8_t)a.NL, (uint8_t)a.K,
+                         (uint8_t)a.per_level, (uint8_t)a.C, (uint8_t)a.NR, 0};
+  hdr.insert(hdr.end(), ab, ab + 8);
+  for (int32_t v : q) put_u32(hdr, (uint32_t)v);
+  for (int k = c->lay.n_arm; k < c->lay.total; ++k) {
+    uint32_t u;
+    std::memcpy(&u, &p[(size_t)k], 4);
+    put_u32(hdr, u);
+  }
+  std::vector<long long> off((size_t)cg.rows);
+  long long body = 0;
+  for (int r = 0; r < cg.rows; ++r) {
+    put_leb128(hdr, (uint32_t)len[(size_t)r]);
+    off[(size_t)r] = body;
+    body += len[(size_t)r];
+  }
+  const size_t total = hdr.size() + (size_t)body;
+  *nbytes = total;
+  if (!out) return CC_OK;
+  if (capacity < total) return set_msg(CC_ESIZE, "output buffer smaller than the bitstream");
+  CK(d_out.alloc((size_t)body));
+  CK(cudaMemcpyAsync(d_off.p, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
+  CK(codec_pack(cg, d_rows.as<uint8_t>(), d_off.as<long long>(), d_len.as<int>(),
+                d_out.as<uint8_t>(), st));
+  CK(cudaMemcpyAsync(out, hdr.data(), hdr.size(), cudaMemcpyDefault, st));
+  CK(cudaMemcpyAsync(out + hdr.size(), d_out.p, (size_t)body, cudaMemcpyDefault, st));
+  CK(cudaStreamSynchronize(st));
+  return CC_OK;
+}
+
+int cc_bitstream_info(const uint8_t* bs, size_t nbytes, cc_config* cfg, int* H, int* W) {
+  if (!cfg || !H || !W) return CC_EINVAL;
+  return parse_fixed(bs, nbytes, cfg, H, W);
+}
+
+int cc_decode_bitstream(const uint8_t* bs, size_t nbytes, void* cuda_stream, float* rgb_out_hwc,
+                        int32_t* latents_out, float* latent_ms) {
+  cc_config cfg;
+  int H = 0, W = 0;
+  int e = parse_fixed(bs, nbytes, &cfg, &H, &W);
+  if (e) return e;
+  const Arch a = arch_of(&cfg);
+  const Layout lay = layout_of(a);
+  size_t pos = kBsFixed;
+  if (nbytes - pos < (size_t)lay.total * 4) return set_msg(CC_EINVAL, "truncated bitstream (parameters)");
+  std::vector<int32_t> q((size_t)lay.n_arm);
+  std::vector<float> params((size_t)lay.total);
+  for (int k = 0; k < lay.total; ++k, pos += 4) {
+    const uint32_t u = get_u32(bs + pos);
+    if (k < lay.n_arm) {
+      q[(size_t)k] = (int32_t)u;
+      params[(size_t)k] = (float)((double)(int32_t)u / 256.0);
+    } else {
+      std::memcpy(&params[(size_t)k], &u, 4);
+    }
+  }
+  const Geo g = geo_of(H, W);
+  const CodecGeo cg = codec_geo(g);
+  std::vector<long long> row_off((size_t)cg.rows);
+  std::vector<int> row_len((size_t)cg.rows);
+  long long body = 0;
+  for (int r = 0; r < cg.rows; ++r) {
+    uint32_t n = 0;
+    if (!get_leb128(bs, nbytes, pos, n)) return set_msg(CC_EINVAL, "truncated bitstream (lengths)");
+    if (n > (uint32_t)INT32_MAX) return set_msg(CC_EINVAL, "substream length");
+    row_off[(size_t)r] = body;
+    row_len[(size_t)r] = (int)n;
+    body += n;
+  }
+  if ((long long)(nbytes - pos) != body) return set_msg(CC_EINVAL, "bitstream length mismatch");
+  const std::vector<int2> offs = causal_offsets(a.N);
+  const int lag = codec_lag(offs.data(), a.N);
+  int active = 1;
+  for (int l = 0; l < kLevels; ++l) active = std::max(active, (g.w[l] + lag - 1) / lag);
+  if (active > 1024)
+    return set_msg(CC_EINVAL, "image too wide for the wavefront decoder (one block per level)");
+  const int threads = std::max(32, (active + 31) / 32 * 32);
+
+  std::vector<uint8_t> zeros((size_t)3 * H * W, 0);
+  cc_ctx* c = nullptr;
+  if ((e = init_common(&cfg, zeros.data(), H, W, params.data(), cuda_stream, nullptr, 0, &c)))
+    return e;
+  struct Guard { cc_ctx* c; ~Guard() { cc_free(c); } } guard{c};
+  cudaStream_t st = c->st;
+  const std::vector<uint16_t>& tab = codec_tables();
+  DevBuf d_tab, d_bytes, d_off, d_len, d_planes, d_flag;
+  CK(d_tab.alloc(codec_table_bytes()));
+  CK(d_bytes.alloc((size_t)body));
+  CK(d_off.alloc((size_t)cg.rows * sizeof(long long)));
+  CK(d_len.alloc((size_t)cg.rows * sizeof(int)));
+  CK(d_planes.alloc((size_t)cg.n_lat * sizeof(int)));
+  CK(d_flag.alloc(sizeof(int)));
+  CK(cudaMemcpyAsync(d_tab.p, tab.data(), codec_table_bytes(), cudaMemcpyHostToDevice, st));
+  if (body) CK(cudaMemcpyAsync(d_bytes.p, bs + pos, (size_t)body, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_off.p, row_off.data(), row_off.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_len.p, row_len.data(), row_len.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(d_flag.p, 0, sizeof(int), st));
+  CK(codec_upload_arm(q.data(), (int)q.size(), st));
+  CK(cudaEventRecord(c->ev_a0, st));
+  CK(codec_decode(cg, c->offs, a.N, a.NL, lag, d_tab.as<uint16_t>(), d_bytes.as<uint8_t>(),
+                  d_off.as<long long>(), d_len.as<int>(), d_planes.as<int>(), d_flag.as<int>(),
+                  threads, st));
+  CK(cudaEventRecord(c->ev_a1, st));
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (flag) return set_msg(CC_EINVAL, "corrupt substream (escape code too long)");
+  if (latent_ms) CK(cudaEventElapsedTime(latent_ms, c->ev_a0, c->ev_a1));
+  if (latents_out)
+    CK(cudaMemcpyAsync(latents_out, d_planes.p, (size_t)cg.n_lat * sizeof(int), cudaMemcpyDefault, st));
+  CK(codec_to_float(cg, c->geo, d_planes.as<int>(), c->y, st));
+  if (rgb_out_hwc) {
+    if ((e = cc_decode(c, rgb_out_hwc))) return e;
+  }
+  CK(cudaStreamSynchronize(st));
+  return CC_OK;
+}
+
 void cc_free(cc_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->dev);
@@ -939,6 +1161,7 @@ const char* cc_strerror(int code) {
     case CC_ETIMEOUT: return "bounded device wait timed out";
     case CC_ENONFINITE: return "non-finite loss";
     case CC_ESTATE: return "state blob does not match this context";
+    case CC_ESIZE: return "output buffer too small (the size needed was returned)";
     default: return "unknown error";
   }
 }

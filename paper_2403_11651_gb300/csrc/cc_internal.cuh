@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <vector>
 
 namespace cc {
 
@@ -235,5 +236,39 @@ cudaError_t image_to_planar(const uint8_t* rgb_hwc, float* x, int H, int W, cuda
 
 // Stores a message for cc_last_cuda_error() (thread-local).
 void set_error_text(const char* msg);
+
+
+// ---- latent bitstream (cc_codec.cu) ------------------------------------------------------
+
+// Flat geometry of the coded latents: levels in order, each row-major without padding;
+// rows of all levels numbered level by level (one range-coder substream per row).
+struct CodecGeo {
+  int h[kLevels], w[kLevels];
+  long long off[kLevels];     // first latent of each level
+  int row0[kLevels];          // first row number of each level
+  int cap[kLevels];           // bytes reserved for one row's substream while encoding
+  long long buf0[kLevels];    // first byte of each level's row buffers
+  long long n_lat, buf_bytes;
+  int rows;
+};
+CodecGeo codec_geo(const Geo& g);
+const std::vector<uint16_t>& codec_tables();
+size_t codec_table_bytes();
+bool codec_quantize_arm(const float* params, int N, int NL, int32_t* q);
+int codec_lag(const int2* offs, int N);
+int codec_max_arm_ints();
+cudaError_t codec_upload_arm(const int32_t* q, int n, cudaStream_t st);
+cudaError_t codec_symbols(const CodecGeo& cg, const Geo& g, const float* y, const int2* offs,
+                          int N, int NL, int2* sym, int* flag, cudaStream_t st);
+cudaError_t codec_encode_rows(const CodecGeo& cg, const int2* sym, const uint16_t* tab,
+                              uint8_t* rowbuf, int* row_len, int* flag, cudaStream_t st);
+cudaError_t codec_pack(const CodecGeo& cg, const uint8_t* rowbuf, const long long* dst_off,
+                       const int* row_len, uint8_t* out, cudaStream_t st);
+cudaError_t codec_decode(const CodecGeo& cg, const int2* offs, int N, int NL, int lag,
+                         const uint16_t* tab, const uint8_t* bytes, const long long* row_off,
+                         const int* row_len, int* planes, int* flag, int threads,
+                         cudaStream_t st);
+cudaError_t codec_to_float(const CodecGeo& cg, const Geo& g, const int* planes, float* y,
+                           cudaStream_t st);
 
 }  // namespace cc

@@ -79,7 +79,7 @@ def test_bad_sizes_rejected(lib):
 
 def test_strerror(lib):
     assert cc.cc_strerror(0) == "ok"
-    for code in (-1, -2, -3, -4, -5, -6):
+    for code in (-1, -2, -3, -4, -5, -6, -7):
         assert cc.cc_strerror(code) != "unknown error"
     assert cc.cc_strerror(-99) == "unknown error"
 
@@ -104,3 +104,31 @@ def test_config_files_load():
         d = cc.load_config(name)
         cfg = cc.make_config(d)
         assert cfg.levels == 7 and cfg.total_iters == d["total_iters"]
+
+
+@pytest.mark.parametrize("arch,H,W", [("c1", 37, 53), ("t1079", 5, 300)])
+def test_bitstream_header_parsed_on_host(lib, arch, H, W):
+    """cc_bitstream_info reads an oracle-written bitstream; damaged or truncated streams are
+    refused on the host, before any device work."""
+    from oracle import codec as C
+    from .helpers import oracle_arch
+    d = config_dict(arch)
+    a = oracle_arch(d)
+    rng = np.random.default_rng(0)
+    named = {n: rng.normal(0, 0.1, s).astype(np.float32) for n, s in oc.param_shapes(a)}
+    y = [np.rint(rng.laplace(0, 1.0, s)).astype(np.int64) for s in oc.level_shapes(H, W)]
+    bs = C.write_bitstream(H, W, a, named, y)
+    cfg, h, w = cc.cc_bitstream_info(bs)
+    assert (h, w) == (H, W)
+    got = (cfg.levels, cfg.arm_ctx, cfg.arm_layers, cfg.up_kernel, cfg.up_per_level,
+           cfg.syn_hidden, cfg.syn_res3x3)
+    assert got == (7, d["arm_ctx"], d["arm_layers"], d["up_kernel"], int(d["up_per_level"]),
+                   d["syn_hidden"], d["syn_res3x3"])
+    for bad in (b"XXXX" + bs[4:], bs[:-1], bs + b"\0", bs[:30]):
+        with pytest.raises(cc.CCError) as e:
+            cc.cc_decode_bitstream(bad)
+        assert e.value.code == cc.CC_EINVAL
+    wrong_arch = bytearray(bs)
+    wrong_arch[13] = 7          # N = 7 is not a supported context size
+    with pytest.raises(cc.CCError):
+        cc.cc_bitstream_info(bytes(wrong_arch))
