@@ -13,12 +13,13 @@ so encoder and decoder must agree on every probability to the last bit; the pape
 not say how (its C decoder is Sec. III-B "Fast C implementation").  Readings taken here,
 all of them integer-exact so that two implementations agree bit for bit:
 
-* ARM in fixed point with 8 fractional bits (Q8).  Weights and biases are rounded
-  (half to even) to multiples of 2^-8 and clamped to +-2^20 (weights) or +-2^28
-  (biases) in Q8 units.  Inputs are the integer latents times 256.  A layer computes, in
-  64-bit integers, z = ((sum_j W[o, j] a[j]) + 128) >> 8 + b[o] (arithmetic shift, i.e.
-  round half up of the Q16 sum), saturated to +-2^28; a LinR layer outputs
-  a[o] + max(z, 0), saturated to +-2^28; the output layer gives (mu_q, s_q) in Q8.
+* ARM in 32-bit fixed point with 8 fractional bits (Q8).  Weights are rounded (half to
+  even) to multiples of 2^-8 and clamped to +-2^11 in Q8 units (|w| <= 8), biases to
+  +-2^15 (|b| <= 128).  The context values are the integer latents clamped to [-128, 128]
+  times 256.  A layer computes z = ((sum_j W[o, j] a[j]) + 128) >> 8 + b[o] (arithmetic
+  shift, i.e. round half up of the Q16 sum), saturated to +-2^15; a LinR layer outputs
+  a[o] + max(z, 0), saturated to +-2^15; the output layer gives (mu_q, s_q) in Q8.  With
+  N <= 24 every sum is below 24 * 2^11 * 2^15 < 2^31: the whole ARM is exact in int32.
 * Probability tables.  The log-scale s_q selects one of NSCALE bins of width 1/8 starting
   at LOGB_LO_Q / 256 (= floor(256 ln 0.01) / 256), clamped to the first and last bin;
   mu_q splits into m = floor(mu_q / 256) and one of NMU = 8 fractional bins.  Table
@@ -54,8 +55,9 @@ import numpy as np
 from .coolchic import Arch, causal_offsets, param_shapes
 
 Q_FRAC = 8
-W_LIM = 1 << 20
-ACT_LIM = 1 << 28
+W_LIM = 1 << 11
+ACT_LIM = 1 << 15
+CTX_LIM = 128
 Y_LIM = 1 << 20
 PROB_BITS = 16
 TOTAL = 1 << PROB_BITS
@@ -91,13 +93,15 @@ def _sat(v):
 
 
 def _layer(a, W, b):
-    """((a W^T) + 128) >> 8 + b in int64 (exact: |a| <= 2^28, |W| <= 2^20, N <= 32)."""
-    return (((a @ W.T) + (1 << (Q_FRAC - 1))) >> Q_FRAC) + b
+    """((a W^T) + 128) >> 8 + b; the sum is checked to fit int32, as the format promises."""
+    acc = a @ W.T
+    assert np.abs(acc).max(initial=0) < 2 ** 31 - (1 << (Q_FRAC - 1))
+    return ((acc + (1 << (Q_FRAC - 1))) >> Q_FRAC) + b
 
 
 def arm_fixed(ctx_int: np.ndarray, Q: dict, arch: Arch):
-    """[..., N] integer contexts -> (mu_q, s_q), int64 in Q8."""
-    a = np.asarray(ctx_int, np.int64) << Q_FRAC
+    """[..., N] integer contexts -> (mu_q, s_q) in Q8 (int64 arrays holding int32 values)."""
+    a = np.clip(np.asarray(ctx_int, np.int64), -CTX_LIM, CTX_LIM) << Q_FRAC
     for i in range(arch.arm_layers):
         z = _sat(_layer(a, Q[f"arm.w{i}"], Q[f"arm.b{i}"]))
         a = _sat(a + np.maximum(z, 0))

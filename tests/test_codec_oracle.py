@@ -56,20 +56,46 @@ def test_fixed_arm_round_half_up():
 @pytest.mark.parametrize("n,layers", [(8, 2), (16, 1), (24, 2)])
 def test_fixed_arm_equals_float_arm_on_dyadic_grid(n, layers):
     """Weights and biases on the 1/4 grid, integer contexts: every partial product of up
-    to three layers lies on the 1/64 grid, so no fixed-point rounding happens and
-    mu_q / 256, s_q / 256 equal the float64 ARM (oracle.coolchic) exactly."""
+    to three layers lies on the 1/64 grid, so no fixed-point rounding happens and, with
+    activations kept below the +-128 saturation, mu_q / 256, s_q / 256 equal the float64
+    ARM (oracle.coolchic) exactly."""
     rng = np.random.default_rng(n * 10 + layers)
     arch = _arch(n, layers)
     named = {}
     for name, shape in oc.param_shapes(arch):
         if name.startswith("arm."):
-            named[name] = rng.integers(-4, 5, size=shape) / 4.0
-    ctx = rng.integers(-6, 7, size=(500, n))
+            named[name] = rng.integers(-2, 3, size=shape) / 4.0
+    ctx = rng.integers(-3, 4, size=(500, n))
     mu_q, s_q = C.arm_fixed(ctx, C.quantize_arm(named, arch), arch)
     P = {k: torch.tensor(v, dtype=oc.DT) for k, v in named.items()}
     mu, s = oc.arm_mlp(torch.tensor(ctx, dtype=oc.DT), P, arch)
+    h = torch.tensor(ctx, dtype=oc.DT)
+    for i in range(layers):      # no saturation anywhere
+        h = h + torch.relu(h @ P[f"arm.w{i}"].T + P[f"arm.b{i}"])
+        assert h.abs().max() < 128
     np.testing.assert_array_equal(mu_q / 256.0, mu.numpy())
     np.testing.assert_array_equal(s_q / 256.0, s.numpy())
+
+
+def test_fixed_arm_context_clamp_and_int32_bound():
+    """Contexts beyond +-128 act as +-128; the largest weights and activations the format
+    allows keep every layer sum inside int32 (checked inside arm_fixed)."""
+    arch = _arch(24, 2)
+    rng = np.random.default_rng(9)
+    Q = {}
+    for name, shape in oc.param_shapes(arch):
+        if name.startswith("arm."):
+            lim = C.W_LIM if ".w" in name else C.ACT_LIM
+            Q[name] = rng.choice([-lim, lim], size=shape).astype(np.int64)
+    big = rng.choice([-10**6, 10**6, -129, 129, 500], size=(64, 24))
+    clamped = np.clip(big, -C.CTX_LIM, C.CTX_LIM)
+    a = C.arm_fixed(big, Q, arch)
+    b = C.arm_fixed(clamped, Q, arch)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    assert np.abs(a[0]).max() <= C.ACT_LIM and np.abs(a[1]).max() <= C.ACT_LIM
+    # the bound itself: N * W_LIM * ACT_LIM + rounding stays below 2^31
+    assert 24 * C.W_LIM * C.ACT_LIM + 128 < 2 ** 31
 
 
 def test_fixed_arm_close_to_float_arm():
@@ -90,10 +116,10 @@ def test_quantize_arm_clamps_and_rounds_half_even():
     arch = _arch(8, 1)
     named = {name: np.zeros(shape) for name, shape in oc.param_shapes(arch)
              if name.startswith("arm.")}
-    named["arm.w0"][0, 0] = 1e9
+    named["arm.w0"][0, 0] = 1e9          # -> +2^11 (|w| <= 8)
     named["arm.w0"][0, 1] = 0.5 / 256     # half -> 0 (even)
     named["arm.w0"][0, 2] = 1.5 / 256     # -> 2
-    named["arm.b0"][0] = -1e12
+    named["arm.b0"][0] = -1e12           # -> -2^15
     Q = C.quantize_arm(named, arch)
     assert Q["arm.w0"][0, 0] == C.W_LIM
     assert Q["arm.w0"][0, 1] == 0 and Q["arm.w0"][0, 2] == 2
