@@ -1002,7 +1002,7 @@ int cc_write_bitstream(cc_ctx* c, uint8_t* out, size_t capacity, size_t* nbytes)
   CK(d_off.alloc((size_t)cg.rows * sizeof(long long)));
   CK(cudaMemcpyAsync(d_tab.p, tab.data(), codec_table_bytes(), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(d_flag.p, 0, sizeof(int), st));
-  CK(codec_upload_arm(q.data(), (int)q.size(), st));
+  CK(codec_upload_arm(q.data(), a.N, a.NL, st));
   CK(codec_symbols(cg, c->geo, c->y, c->offs, a.N, a.NL, d_sym.as<int2>(), d_flag.as<int>(), st));
   CK(codec_encode_rows(cg, d_sym.as<int2>(), d_tab.as<uint16_t>(), d_rows.as<uint8_t>(),
                        d_len.as<int>(), d_flag.as<int>(), st));
@@ -1087,13 +1087,11 @@ int cc_decode_bitstream(const uint8_t* bs, size_t nbytes, void* cuda_stream, flo
     body += n;
   }
   if ((long long)(nbytes - pos) != body) return set_msg(CC_EINVAL, "bitstream length mismatch");
+  if (!codec_arm_in_range(q.data(), a.N, a.NL))
+    return set_msg(CC_EINVAL, "bitstream ARM parameters outside the fixed-point ranges");
   const std::vector<int2> offs = causal_offsets(a.N);
-  const int lag = codec_lag(offs.data(), a.N);
-  int active = 1;
-  for (int l = 0; l < kLevels; ++l) active = std::max(active, (g.w[l] + lag - 1) / lag);
-  if (active > 1024)
-    return set_msg(CC_EINVAL, "image too wide for the wavefront decoder (one block per level)");
-  const int threads = std::max(32, (active + 31) / 32 * 32);
+  if (!codec_offsets_match(offs.data(), a.N))
+    return set_msg(CC_ECUDA, "decoder context tables disagree with the causal offsets");
 
   std::vector<uint8_t> zeros((size_t)3 * H * W, 0);
   cc_ctx* c = nullptr;
@@ -1102,8 +1100,9 @@ int cc_decode_bitstream(const uint8_t* bs, size_t nbytes, void* cuda_stream, flo
   struct Guard { cc_ctx* c; ~Guard() { cc_free(c); } } guard{c};
   cudaStream_t st = c->st;
   const std::vector<uint16_t>& tab = codec_tables();
-  DevBuf d_tab, d_bytes, d_off, d_len, d_planes, d_flag;
+  DevBuf d_tab, d_bytes, d_off, d_len, d_planes, d_flag, d_prog;
   CK(d_tab.alloc(codec_table_bytes()));
+  CK(d_prog.alloc((size_t)cg.bands * sizeof(int)));
   CK(d_bytes.alloc((size_t)body));
   CK(d_off.alloc((size_t)cg.rows * sizeof(long long)));
   CK(d_len.alloc((size_t)cg.rows * sizeof(int)));
@@ -1114,15 +1113,16 @@ int cc_decode_bitstream(const uint8_t* bs, size_t nbytes, void* cuda_stream, flo
   CK(cudaMemcpyAsync(d_off.p, row_off.data(), row_off.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_len.p, row_len.data(), row_len.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(d_flag.p, 0, sizeof(int), st));
-  CK(codec_upload_arm(q.data(), (int)q.size(), st));
+  CK(codec_upload_arm(q.data(), a.N, a.NL, st));
   CK(cudaEventRecord(c->ev_a0, st));
-  CK(codec_decode(cg, c->offs, a.N, a.NL, lag, d_tab.as<uint16_t>(), d_bytes.as<uint8_t>(),
-                  d_off.as<long long>(), d_len.as<int>(), d_planes.as<int>(), d_flag.as<int>(),
-                  threads, st));
+  CK(codec_decode(cg, a.N, a.NL, d_tab.as<uint16_t>(), d_bytes.as<uint8_t>(),
+                  d_off.as<long long>(), d_len.as<int>(), d_planes.as<int>(), d_prog.as<int>(),
+                  d_flag.as<int>(), st));
   CK(cudaEventRecord(c->ev_a1, st));
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (flag & 8) return set_msg(CC_ETIMEOUT, "a decoding band waited too long on the band above");
   if (flag) return set_msg(CC_EINVAL, "corrupt substream (escape code too long)");
   if (latent_ms) CK(cudaEventElapsedTime(latent_ms, c->ev_a0, c->ev_a1));
   if (latents_out)

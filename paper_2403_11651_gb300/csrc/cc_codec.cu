@@ -9,11 +9,12 @@
 // arithmetic.
 //
 // Format (shared with the decoder, nothing float on the device):
-//   ARM:    weights and biases rounded half-to-even to Q8 (8 fractional bits), weights
-//           clamped to +-2^20, biases to +-2^28; inputs are integer latents times 256; a
-//           layer computes z = ((sum_j W[o, j] a[j]) + 128) >> 8 + b[o] in 64-bit integers,
-//           saturated to +-2^28; a LinR layer outputs a[o] + max(z, 0), saturated; the
-//           output layer gives (mu_q, s_q) in Q8.
+//   ARM:    32-bit fixed point with 8 fractional bits (Q8): weights rounded half-to-even
+//           and clamped to +-2^11 (|w| <= 8), biases to +-2^15; context = integer latents
+//           clamped to [-128, 128] times 256; a layer computes
+//           z = ((sum_j W[o, j] a[j]) + 128) >> 8 + b[o], saturated to +-2^15; a LinR
+//           layer outputs a[o] + max(z, 0), saturated; the output layer gives (mu_q, s_q).
+//           With N <= 24 every sum is below 24 * 2^26 < 2^31: exact in int32.
 //   tables: s_q picks one of 93 log-scale bins of width 1/8 from -1179/256 (floor of
 //           256 ln 0.01), clamped; mu_q = 256 m + 32 fi + rest; table (bin j, fi) is the
 //           Laplace law of mean (fi + 1/2)/8 and scale exp(-1179/256 + (j + 1/2)/8) over
@@ -27,6 +28,7 @@
 //           of the last interval with the most trailing zero bits, and trailing zero
 //           bytes are dropped (the decoder reads zeros past the end of a substream).
 //   streams: one substream per latent row, so that rows decode as a wavefront.
+#include <climits>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -38,8 +40,9 @@ namespace cc {
 namespace {
 
 constexpr int kQFrac = 8;
-constexpr long long kWLim = 1ll << 20;
-constexpr long long kActLim = 1ll << 28;
+constexpr int kWLim = 1 << 11;
+constexpr int kActLim = 1 << 15;
+constexpr int kCtxLim = 128;
 constexpr int kYLim = 1 << 20;
 constexpr int kA = 64;
 constexpr int kNsym = 2 * kA + 3;          // 131
@@ -54,50 +57,45 @@ constexpr int kMaxEgBits = 40;             // Exp-Golomb prefix bound (latents <
 
 __constant__ int c_qarm[kMaxQArm];
 
-__device__ __forceinline__ long long sat(long long v) {
-  return v < -kActLim ? -kActLim : (v > kActLim ? kActLim : v);
-}
+__device__ __forceinline__ int sat(int v) { return min(max(v, -kActLim), kActLim); }
 
-// (mu_q, s_q) of the fixed-point ARM for the integer context ctx
-template <int N>
-__device__ __forceinline__ void arm_fixed(const int (&ctx)[N], int NL, long long& mu,
-                                          long long& s) {
+// (mu_q, s_q) of the fixed-point ARM for the integer context ctx; weights in c_qarm
+template <int N, int NL>
+__device__ __forceinline__ void arm_fixed(const int (&ctx)[N], int& mu, int& s) {
   int a[N];
 #pragma unroll
-  for (int j = 0; j < N; ++j) a[j] = ctx[j] * (1 << kQFrac);
+  for (int j = 0; j < N; ++j) a[j] = min(max(ctx[j], -kCtxLim), kCtxLim) * (1 << kQFrac);
+#pragma unroll
   for (int i = 0; i < NL; ++i) {
-    const int* W = c_qarm + i * (N * N + N);
-    const int* b = W + N * N;
-    int z[N];
+    const int* Wt = c_qarm + i * (N * N + N);   // the bank holds W transposed: Wt[j N + o]
+    const int* b = Wt + N * N;
+    int acc[N];                 // all N sums advance together: N independent chains
 #pragma unroll
-    for (int o = 0; o < N; ++o) {
-      long long acc = 0;
+    for (int o = 0; o < N; ++o) acc[o] = 0;
 #pragma unroll
-      for (int j = 0; j < N; ++j) acc += (long long)W[o * N + j] * a[j];
-      const long long v = sat(((acc + 128) >> kQFrac) + b[o]);
-      z[o] = (int)(v > 0 ? v : 0);
-    }
+    for (int j = 0; j < N; ++j)
 #pragma unroll
-    for (int o = 0; o < N; ++o) a[o] = (int)sat((long long)a[o] + z[o]);
+      for (int o = 0; o < N; ++o) acc[o] += Wt[j * N + o] * a[j];
+#pragma unroll
+    for (int o = 0; o < N; ++o) a[o] = sat(a[o] + max(sat(((acc[o] + 128) >> kQFrac) + b[o]), 0));
   }
   const int* W = c_qarm + NL * (N * N + N);
   const int* b = W + 2 * N;
-  long long acc0 = 0, acc1 = 0;
+  int acc0 = 0, acc1 = 0;
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    acc0 += (long long)W[j] * a[j];
-    acc1 += (long long)W[N + j] * a[j];
+    acc0 += W[j] * a[j];
+    acc1 += W[N + j] * a[j];
   }
   mu = sat(((acc0 + 128) >> kQFrac) + b[0]);
   s = sat(((acc1 + 128) >> kQFrac) + b[1]);
 }
 
 // table number and integer part of mu
-__device__ __forceinline__ void table_of(long long mu, long long s, int& t, int& m) {
-  long long j = (s - kLogbLoQ) >> 5;
-  j = j < 0 ? 0 : (j > kNscale - 1 ? kNscale - 1 : j);
-  t = (int)j * kNmu + (int)((mu & 255) >> 5);
-  m = (int)(mu >> kQFrac);
+__device__ __forceinline__ void table_of(int mu, int s, int& t, int& m) {
+  const int j = min(max((s - kLogbLoQ) >> 5, 0), kNscale - 1);
+  t = j * kNmu + ((mu & 255) >> 5);
+  m = mu >> kQFrac;
 }
 
 __device__ __forceinline__ uint32_t cum_at(const uint16_t* row, int i) {
@@ -215,10 +213,10 @@ __device__ __forceinline__ int sym_index(int k) {
 // Encoder: fixed-point ARM of every latent (parallel), then one thread per row
 // ---------------------------------------------------------------------------------------
 
-template <int N>
+template <int N, int NL>
 __global__ void __launch_bounds__(256) k_codec_symbols(CodecGeo cg, Geo g,
                                                        const float* __restrict__ y,
-                                                       const int2* __restrict__ offs, int NL,
+                                                       const int2* __restrict__ offs,
                                                        int2* __restrict__ sym, int* flag) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= cg.n_lat) return;
@@ -242,9 +240,8 @@ __global__ void __launch_bounds__(256) k_codec_symbols(CodecGeo cg, Geo g,
     sym[q] = make_int2(0, 0);
     return;
   }
-  long long mu, s;
-  arm_fixed<N>(ctx, NL, mu, s);
-  int t, m;
+  int mu, s, t, m;
+  arm_fixed<N, NL>(ctx, mu, s);
   table_of(mu, s, t, m);
   sym[q] = make_int2((int)yv - m, t);
 }
@@ -292,59 +289,198 @@ __global__ void __launch_bounds__(256) k_codec_pack(CodecGeo cg, const uint8_t* 
 }
 
 // ---------------------------------------------------------------------------------------
-// Decoder: one block per level; row r decodes position x at step x + lag r, so that every
-// causal neighbour was decoded at an earlier step.  Rows are dealt to threads modulo the
-// block size, which is at least the number of rows active at one step (ceil(w / lag)):
-// a thread then holds one row's coder at a time.
+// Decoder.  The rows of a level form bands of 32; a warp decodes one band at a time, lane i
+// holding row r0 + i, which decodes position x at the band's local step x + lag i, so
+// that inside the band every causal neighbour was decoded at an earlier step (lag =
+// max over context offsets of ceil((dx + 1) / -dy)).  A band may run local step s once
+// its predecessor band (the 32 rows above) has completed s + 32 lag steps: then every
+// neighbour in those rows is decoded too.  Bands publish their completed step count every
+// 4 steps (release) and wait on their predecessor's (acquire, bounded).  All levels run
+// at once; warps take bands in increasing order, which keeps the waits acyclic, and the
+// cooperative launch keeps every warp resident.
 // ---------------------------------------------------------------------------------------
 
-template <int N>
-__global__ void __launch_bounds__(1024) k_codec_decode(CodecGeo cg, const int2* __restrict__ offs,
-                                                       int NL, int lag,
-                                                       const uint16_t* __restrict__ tab,
-                                                       const uint8_t* __restrict__ bytes,
-                                                       const long long* __restrict__ row_off,
-                                                       const int* __restrict__ row_len,
-                                                       int* planes, int* flag) {
+constexpr int kBandRows = 32;
+constexpr int kDecWarps = 4;                 // warps per block: one per scheduler
+constexpr int kMaxPolls = 1 << 22;           // bounded wait on the predecessor band
+constexpr int kRing = 64;                    // columns of the predecessor rows kept in smem
+constexpr int kFill = 16;                    // steps between ring refills
+
+// The causal offsets (dy, dx) of N = 8, 16, 24 in raster order (the N nearest causal
+// neighbours, ties by smaller |dy| then smaller dx) as compile-time tables: the decoder
+// keeps recent values in registers and needs each offset's register index statically.
+// The host checks them against the offsets the library builds at run time.
+template <int N> __host__ __device__ constexpr int off_dy(int j);
+template <int N> __host__ __device__ constexpr int off_dx(int j);
+template <> __host__ __device__ constexpr int off_dy<8>(int j) {
+  constexpr int t[8] = {-2, -1, -1, -1, -1, -1, 0, 0};
+  return t[j];
+}
+template <> __host__ __device__ constexpr int off_dx<8>(int j) {
+  constexpr int t[8] = {0, -2, -1, 0, 1, 2, -2, -1};
+  return t[j];
+}
+template <> __host__ __device__ constexpr int off_dy<16>(int j) {
+  constexpr int t[16] = {-3, -2, -2, -2, -2, -2, -1, -1, -1, -1, -1, -1, -1, 0, 0, 0};
+  return t[j];
+}
+template <> __host__ __device__ constexpr int off_dx<16>(int j) {
+  constexpr int t[16] = {0, -2, -1, 0, 1, 2, -3, -2, -1, 0, 1, 2, 3, -3, -2, -1};
+  return t[j];
+}
+template <> __host__ __device__ constexpr int off_dy<24>(int j) {
+  constexpr int t[24] = {-4, -3, -3, -3, -3, -3, -2, -2, -2, -2, -2, -2,
+                         -2, -1, -1, -1, -1, -1, -1, -1, 0, 0, 0, 0};
+  return t[j];
+}
+template <> __host__ __device__ constexpr int off_dx<24>(int j) {
+  constexpr int t[24] = {0, -2, -1, 0, 1, 2, -3, -2, -1, 0, 1, 2,
+                         3, -3, -2, -1, 0, 1, 2, 3, -4, -3, -2, -1};
+  return t[j];
+}
+// wavefront lag: max over dy < 0 of ceil((dx + 1) / -dy)
+template <int N> __host__ __device__ constexpr int lag_of() {
+  int lag = 1;
+  for (int j = 0; j < N; ++j)
+    if (off_dy<N>(j) < 0) {
+      const int d = -off_dy<N>(j), need = (off_dx<N>(j) + 1 + d - 1) / d;
+      lag = need > lag ? need : lag;
+    }
+  return lag;
+}
+// rows above the current one that the context reaches
+template <int N> __host__ __device__ constexpr int reach_of() {
+  int r = 0;
+  for (int j = 0; j < N; ++j) r = -off_dy<N>(j) > r ? -off_dy<N>(j) : r;
+  return r;
+}
+// register index, in the window of the row the offset points to, of the value it reads:
+// a lane's window entry k holds its row's value at (its position one step ago) - k
+template <int N> __host__ __device__ constexpr int win_idx(int j) {
+  return -lag_of<N>() * off_dy<N>(j) - 1 - off_dx<N>(j);
+}
+template <int N> __host__ __device__ constexpr int win_of() {
+  int m = 0;
+  for (int j = 0; j < N; ++j) m = win_idx<N>(j) > m ? win_idx<N>(j) : m;
+  return m + 1;
+}
+
+// ---------------------------------------------------------------------------------------
+// Decoder.  The rows of a level form bands of 32; a warp decodes one band at a time, lane i
+// holding row r0 + i, which decodes position x at the band's local step x + lag i: then
+// every causal neighbour inside the band was decoded at an earlier step.  Each lane keeps
+// its row's last win_of<N>() values in registers (0 before the row starts and after it
+// ends); a neighbour in row r0 + i + dy comes from lane i + dy's registers by a warp
+// shuffle.  Neighbours in the rows above the band come from a shared-memory ring of
+// those rows, refilled every kFill steps (from L2) once the band above has completed
+// enough steps; the band above publishes its completed step count every 4 steps
+// (release) and the refill waits for it (acquire, bounded).  All levels run at once;
+// warps take bands in increasing order, which keeps the waits acyclic, and the
+// cooperative launch keeps every warp resident.
+// ---------------------------------------------------------------------------------------
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <int N, int NL>
+__global__ void __launch_bounds__(kDecWarps * 32) k_codec_decode(
+    CodecGeo cg, const uint16_t* __restrict__ tab, const uint8_t* __restrict__ bytes,
+    const long long* __restrict__ row_off, const int* __restrict__ row_len, int* planes,
+    int* progress, int* flag) {
+  constexpr int LAG = lag_of<N>(), R = reach_of<N>(), WIN = win_of<N>();
   extern __shared__ __align__(16) uint16_t s_tab[];
-  __shared__ int2 s_offs[N];
+  __shared__ int s_ring[kDecWarps][R][kRing];
   for (int i = threadIdx.x; i < kNtab * kTabStride / 8; i += blockDim.x)
     reinterpret_cast<uint4*>(s_tab)[i] = reinterpret_cast<const uint4*>(tab)[i];
-  if (threadIdx.x < N) s_offs[threadIdx.x] = offs[threadIdx.x];
   __syncthreads();
 
-  const int l = blockIdx.x;
-  const int h = cg.h[l], w = cg.w[l];
-  int* plane = planes + cg.off[l];
-  const int T = blockDim.x, tid = threadIdx.x;
-  const long long steps = (long long)w + (long long)lag * (h - 1);
-  RcDec dec;
-  dec.init(bytes, 0);
-  bool bad = false;
-  for (long long st = 0; st < steps; ++st) {
-    const long long rmax_l = st / lag < h - 1 ? st / lag : h - 1;
-    const int rmax = (int)rmax_l;
-    if (tid <= rmax) {
-      const int r = rmax - (rmax - tid) % T;
-      const long long xl = st - (long long)lag * r;
-      if (xl < w) {
-        const int x = (int)xl;
-        const int grow = cg.row0[l] + r;
-        if (x == 0) dec.init(bytes + row_off[grow], row_len[grow]);
-        int ctx[N];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int (*ring)[kRing] = s_ring[wid];
+  const int tw = gridDim.x * kDecWarps;
+  for (int gb = blockIdx.x * kDecWarps + wid; gb < cg.bands; gb += tw) {
+    int l = 0;
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-          const int2 o = s_offs[j];
-          const int rr = r + o.x, xx = x + o.y;
-          ctx[j] = (rr >= 0 && xx >= 0 && xx < w) ? plane[(long long)rr * w + xx] : 0;
+    for (int k = 1; k < kLevels; ++k) l = gb >= cg.band0[k] ? k : l;
+    const int b = gb - cg.band0[l];
+    const int h = cg.h[l], w = cg.w[l];
+    const int r0 = kBandRows * b;
+    const int nr = min(kBandRows, h - r0);
+    const int r = r0 + lane;
+    int* plane = planes + cg.off[l];
+    const int nsteps = w + LAG * (nr - 1);
+    const int pred_steps = w + LAG * (kBandRows - 1);   // a predecessor band is full
+    int win[WIN];
+#pragma unroll
+    for (int k = 0; k < WIN; ++k) win[k] = 0;
+    RcDec dec;
+    dec.init(bytes, 0);
+    bool bad = false;
+    for (int st = 0; st < nsteps; ++st) {
+      if (st % kFill == 0) {                    // refill the ring of the rows above
+        if (b > 0) {
+          const int need = min(st + 2 * kFill + LAG * (kBandRows - 1), pred_steps);
+          int v = 0;
+          if (lane == 0) {
+            for (int tries = 0; tries < kMaxPolls; ++tries) {
+              v = ld_acquire(progress + gb - 1);
+              if (v >= need) break;
+              __nanosleep(64);
+            }
+          }
+          v = __shfl_sync(0xFFFFFFFFu, v, 0);
+          if (v < need) {                       // the band above stalled: give up
+            if (lane == 0) atomicOr(flag, 8);
+            return;
+          }
         }
-        long long mu, s;
-        arm_fixed<N>(ctx, NL, mu, s);
-        int t, m;
+        __syncwarp();
+#pragma unroll
+        for (int t = lane; t < 4 * kFill; t += 32) {
+          const int m = t / kFill + 1, rr = r0 - m;
+          if (m <= R) {
+            const int c = st + kFill + (t % kFill);
+            ring[m - 1][c % kRing] = (rr >= 0 && c < w) ? __ldcg(plane + (long long)rr * w + c) : 0;
+            if (st == 0) {
+              const int c0 = t % kFill;
+              ring[m - 1][c0] = (rr >= 0 && c0 < w) ? __ldcg(plane + (long long)rr * w + c0) : 0;
+            }
+          }
+        }
+        __syncwarp();
+      }
+      const int x = st - LAG * lane;
+      int ctx[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const int dy = off_dy<N>(j), dx = off_dx<N>(j);
+        int v;
+        if (dy == 0) {
+          v = win[-1 - dx];
+        } else {
+          v = __shfl_up_sync(0xFFFFFFFFu, win[win_idx<N>(j)], -dy);
+          if (lane + dy < 0) v = ring[-(lane + dy) - 1][(x + dx) & (kRing - 1)];
+        }
+        ctx[j] = (r + dy >= 0 && x + dx >= 0 && x + dx < w) ? v : 0;
+      }
+      int val = 0;
+      if (lane < nr && x >= 0 && x < w) {
+        if (x == 0) dec.init(bytes + row_off[cg.row0[l] + r], row_len[cg.row0[l] + r]);
+        int mu, s, t, m;
+        arm_fixed<N, NL>(ctx, mu, s);
         table_of(mu, s, t, m);
         const uint16_t* cr = s_tab + t * kTabStride;
         const uint32_t q = dec.target();
-        int lo = 0, hi = kNsym;            // largest idx with cum[idx] <= q
+        // largest idx with cum[idx] <= q: first the symbol k = 0 (the table's most
+        // probable region), then a binary search on the side q falls
+        int lo = kA + 1, hi = kA + 2;
+        if ((uint32_t)cr[lo] > q) { hi = lo; lo = 0; }
+        else if (q >= (uint32_t)cr[hi]) { lo = hi; hi = kNsym; }
         while (hi - lo > 1) {
           const int mid = (lo + hi) >> 1;
           if ((uint32_t)cr[mid] <= q) lo = mid; else hi = mid;
@@ -357,33 +493,50 @@ __global__ void __launch_bounds__(1024) k_codec_decode(CodecGeo cg, const int2* 
           if (!dec.excess(e)) bad = true;
           k = lo == 0 ? -kA - 1 - (int)e : kA + 1 + (int)e;
         }
-        plane[(long long)r * w + x] = m + k;
+        val = m + k;
+        plane[(long long)r * w + x] = val;
+      }
+#pragma unroll
+      for (int k = WIN - 1; k > 0; --k) win[k] = win[k - 1];
+      win[0] = val;
+      if ((st & 3) == 3 || st == nsteps - 1) {
+        __syncwarp();
+        if (lane == 0) st_release(progress + gb, st + 1);
       }
     }
-    __syncthreads();
+    if (bad) atomicOr(flag, 4);
   }
-  if (bad) atomicOr(flag, 4);
 }
 
 template <int N>
 cudaError_t symbols_t(const CodecGeo& cg, const Geo& g, const float* y, const int2* offs,
                       int NL, int2* sym, int* flag, cudaStream_t st) {
   const int blocks = (int)((cg.n_lat + 255) / 256);
-  k_codec_symbols<N><<<blocks, 256, 0, st>>>(cg, g, y, offs, NL, sym, flag);
+  if (NL == 1) k_codec_symbols<N, 1><<<blocks, 256, 0, st>>>(cg, g, y, offs, sym, flag);
+  else k_codec_symbols<N, 2><<<blocks, 256, 0, st>>>(cg, g, y, offs, sym, flag);
   return cudaGetLastError();
 }
 
-template <int N>
-cudaError_t decode_t(const CodecGeo& cg, const int2* offs, int NL, int lag, const uint16_t* tab,
-                     const uint8_t* bytes, const long long* row_off, const int* row_len,
-                     int* planes, int* flag, int threads, cudaStream_t st) {
+template <int N, int NL>
+cudaError_t decode_t(const CodecGeo& cg, const uint16_t* tab, const uint8_t* bytes,
+                     const long long* row_off, const int* row_len, int* planes, int* progress,
+                     int* flag, cudaStream_t st) {
   const size_t smem = (size_t)kNtab * kTabStride * sizeof(uint16_t);
-  cudaError_t e = cudaFuncSetAttribute(k_codec_decode<N>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = k_codec_decode<N, NL>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_codec_decode<N><<<kLevels, threads, smem, st>>>(cg, offs, NL, lag, tab, bytes, row_off,
-                                                    row_len, planes, flag);
-  return cudaGetLastError();
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDecWarps * 32, smem)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int want = (cg.bands + kDecWarps - 1) / kDecWarps;
+  const int grid = want < sms * per_sm ? want : sms * per_sm;
+  void* args[] = {(void*)&cg, (void*)&tab, (void*)&bytes, (void*)&row_off, (void*)&row_len,
+                  (void*)&planes, (void*)&progress, (void*)&flag};
+  return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kDecWarps * 32), args,
+                                     smem, st);
 }
 
 std::vector<uint16_t> g_tables;
@@ -432,7 +585,7 @@ const std::vector<uint16_t>& codec_tables() {
 size_t codec_table_bytes() { return (size_t)kNtab * kTabStride * sizeof(uint16_t); }
 
 bool codec_quantize_arm(const float* params, int N, int NL, int32_t* q) {
-  // Q8 rounding half to even; weights clamped to +-2^20, biases to +-2^28
+  // Q8 rounding half to even; weights clamped to +-2^11, biases to +-2^15
   auto quant = [](float p, long long lim, int32_t& out) {
     const double d = std::nearbyint((double)p * 256.0);
     if (!std::isfinite(d)) return false;
@@ -447,29 +600,53 @@ bool codec_quantize_arm(const float* params, int N, int NL, int32_t* q) {
   return ok;
 }
 
-int codec_lag(const int2* offs, int N) {
-  int lag = 1;
+bool codec_offsets_match(const int2* offs, int N) {
   for (int j = 0; j < N; ++j) {
-    const int dy = offs[j].x, dx = offs[j].y;
-    if (dy < 0) {
-      const int need = (dx + 1 + (-dy) - 1) / (-dy);   // ceil((dx + 1) / -dy), dx + 1 >= 0
-      lag = need > lag ? need : lag;
-    }
+    int dy = 0, dx = 0;
+    if (N == 8) { dy = off_dy<8>(j); dx = off_dx<8>(j); }
+    else if (N == 16) { dy = off_dy<16>(j); dx = off_dx<16>(j); }
+    else if (N == 24) { dy = off_dy<24>(j); dx = off_dx<24>(j); }
+    else return false;
+    if (offs[j].x != dy || offs[j].y != dx) return false;
   }
-  return lag;
+  return true;
+}
+
+bool codec_arm_in_range(const int32_t* q, int N, int NL) {
+  int k = 0;
+  for (int i = 0; i < NL; ++i)
+    for (int j = 0; j < N * N + N; ++j, ++k)
+      if (std::abs(q[k]) > (j < N * N ? kWLim : kActLim)) return false;
+  for (int j = 0; j < 2 * N + 2; ++j, ++k)
+    if (std::abs(q[k]) > (j < 2 * N ? kWLim : kActLim)) return false;
+  return true;
 }
 
 int codec_row_capacity(int w) { return 8 * w + 16; }
 
-cudaError_t codec_upload_arm(const int32_t* q, int n, cudaStream_t st) {
-  return cudaMemcpyToSymbolAsync(c_qarm, q, (size_t)n * sizeof(int32_t), 0,
-                                 cudaMemcpyHostToDevice, st);
+cudaError_t codec_upload_arm(const int32_t* q, int N, int NL, cudaStream_t st) {
+  // the constant bank holds each LinR weight matrix transposed (the device walks it along
+  // the outputs); biases and the output layer as in the flat order
+  static thread_local std::vector<int32_t> bank;
+  const int n = NL * (N * N + N) + 2 * N + 2;
+  bank.assign(q, q + n);
+  for (int i = 0; i < NL; ++i) {
+    const int32_t* W = q + i * (N * N + N);
+    int32_t* Wt = bank.data() + i * (N * N + N);
+    for (int o = 0; o < N; ++o)
+      for (int j = 0; j < N; ++j) Wt[j * N + o] = W[o * N + j];
+  }
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_qarm, bank.data(), (size_t)n * sizeof(int32_t), 0,
+                                          cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);   // the staging vector is reused by the next call
 }
 
 int codec_max_arm_ints() { return kMaxQArm; }
 
 cudaError_t codec_symbols(const CodecGeo& cg, const Geo& g, const float* y, const int2* offs,
                           int N, int NL, int2* sym, int* flag, cudaStream_t st) {
+  if (NL != 1 && NL != 2) return cudaErrorInvalidValue;
   switch (N) {
     case 8: return symbols_t<8>(cg, g, y, offs, NL, sym, flag, st);
     case 16: return symbols_t<16>(cg, g, y, offs, NL, sym, flag, st);
@@ -490,16 +667,18 @@ cudaError_t codec_pack(const CodecGeo& cg, const uint8_t* rowbuf, const long lon
   return cudaGetLastError();
 }
 
-cudaError_t codec_decode(const CodecGeo& cg, const int2* offs, int N, int NL, int lag,
-                         const uint16_t* tab, const uint8_t* bytes, const long long* row_off,
-                         const int* row_len, int* planes, int* flag, int threads,
-                         cudaStream_t st) {
-  switch (N) {
-    case 8: return decode_t<8>(cg, offs, NL, lag, tab, bytes, row_off, row_len, planes, flag, threads, st);
-    case 16: return decode_t<16>(cg, offs, NL, lag, tab, bytes, row_off, row_len, planes, flag, threads, st);
-    case 24: return decode_t<24>(cg, offs, NL, lag, tab, bytes, row_off, row_len, planes, flag, threads, st);
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t codec_decode(const CodecGeo& cg, int N, int NL, const uint16_t* tab,
+                         const uint8_t* bytes, const long long* row_off, const int* row_len,
+                         int* planes, int* progress, int* flag, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(progress, 0, (size_t)cg.bands * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+#define CC_DECODE_CASE(n, nl)                                                                 \
+  if (N == n && NL == nl)                                                                     \
+    return decode_t<n, nl>(cg, tab, bytes, row_off, row_len, planes, progress, flag, st);
+  CC_DECODE_CASE(8, 1) CC_DECODE_CASE(8, 2) CC_DECODE_CASE(16, 1) CC_DECODE_CASE(16, 2)
+  CC_DECODE_CASE(24, 1) CC_DECODE_CASE(24, 2)
+#undef CC_DECODE_CASE
+  return cudaErrorInvalidValue;
 }
 
 // integer latent planes (flat order) -> float latent buffer (padded layout)
@@ -522,7 +701,7 @@ cudaError_t codec_to_float(const CodecGeo& cg, const Geo& g, const int* planes, 
 CodecGeo codec_geo(const Geo& g) {
   CodecGeo cg;
   long long off = 0, buf = 0;
-  int rows = 0;
+  int rows = 0, bands = 0;
   for (int l = 0; l < kLevels; ++l) {
     cg.h[l] = g.h[l];
     cg.w[l] = g.w[l];
@@ -530,12 +709,15 @@ CodecGeo codec_geo(const Geo& g) {
     cg.row0[l] = rows;
     cg.cap[l] = codec_row_capacity(g.w[l]);
     cg.buf0[l] = buf;
+    cg.band0[l] = bands;
+    bands += (g.h[l] + kBandRows - 1) / kBandRows;
     off += (long long)g.h[l] * g.w[l];
     rows += g.h[l];
     buf += (long long)g.h[l] * cg.cap[l];
   }
   cg.n_lat = off;
   cg.rows = rows;
+  cg.bands = bands;
   cg.buf_bytes = buf;
   return cg;
 }

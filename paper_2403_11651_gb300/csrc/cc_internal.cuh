@@ -248,26 +248,27 @@ struct CodecGeo {
   int row0[kLevels];          // first row number of each level
   int cap[kLevels];           // bytes reserved for one row's substream while encoding
   long long buf0[kLevels];    // first byte of each level's row buffers
+  int band0[kLevels];         // first 32-row decoding band of each level
   long long n_lat, buf_bytes;
-  int rows;
+  int rows, bands;
 };
 CodecGeo codec_geo(const Geo& g);
 const std::vector<uint16_t>& codec_tables();
 size_t codec_table_bytes();
 bool codec_quantize_arm(const float* params, int N, int NL, int32_t* q);
-int codec_lag(const int2* offs, int N);
 int codec_max_arm_ints();
-cudaError_t codec_upload_arm(const int32_t* q, int n, cudaStream_t st);
+cudaError_t codec_upload_arm(const int32_t* q, int N, int NL, cudaStream_t st);
 cudaError_t codec_symbols(const CodecGeo& cg, const Geo& g, const float* y, const int2* offs,
                           int N, int NL, int2* sym, int* flag, cudaStream_t st);
 cudaError_t codec_encode_rows(const CodecGeo& cg, const int2* sym, const uint16_t* tab,
                               uint8_t* rowbuf, int* row_len, int* flag, cudaStream_t st);
 cudaError_t codec_pack(const CodecGeo& cg, const uint8_t* rowbuf, const long long* dst_off,
                        const int* row_len, uint8_t* out, cudaStream_t st);
-cudaError_t codec_decode(const CodecGeo& cg, const int2* offs, int N, int NL, int lag,
-                         const uint16_t* tab, const uint8_t* bytes, const long long* row_off,
-                         const int* row_len, int* planes, int* flag, int threads,
-                         cudaStream_t st);
+cudaError_t codec_decode(const CodecGeo& cg, int N, int NL, const uint16_t* tab,
+                         const uint8_t* bytes, const long long* row_off, const int* row_len,
+                         int* planes, int* progress, int* flag, cudaStream_t st);
+bool codec_offsets_match(const int2* offs, int N);
+bool codec_arm_in_range(const int32_t* q, int N, int NL);
 cudaError_t codec_to_float(const CodecGeo& cg, const Geo& g, const int* planes, float* y,
                            cudaStream_t st);
 

@@ -12,6 +12,9 @@ This module holds no arithmetic of the coding method itself: it only draws input
   k = 4, so that every polyphase component sums to one.
 * ``uniform_noise``: explicit quantisation noise in [-1/2, 1/2) on a 2^-24 grid, for the
   tests that pass noise in instead of drawing it from the counter-based generator.
+* ``synthetic_latents``: an integer latent pyramid for the bitstream benchmarks: level l
+  draws rounded Laplace values of scale 0.4 + 0.6 l (coarser levels carry larger values,
+  as in trained Cool-chic pyramids).
 
 Every value is exactly representable in float32, so both implementations start from
 bit-identical inputs.
@@ -28,6 +31,7 @@ __all__ = [
     "synthetic_image",
     "initial_parameters",
     "uniform_noise",
+    "synthetic_latents",
     "keys_cubic",
 ]
 
@@ -171,3 +175,10 @@ def uniform_noise(H: int, W: int, seed: int, levels: int = 7):
         k = rng.integers(0, 1 << 24, size=(h, w), dtype=np.int64)
         out.append((k.astype(np.float64) * 2.0 ** -24 - 0.5).astype(np.float32))
     return out
+
+
+def synthetic_latents(H: int, W: int, seed: int, levels: int = 7):
+    """Per-level int32 planes of rounded Laplace values, scale 0.4 + 0.6 l at level l."""
+    rng = np.random.Generator(np.random.PCG64(seed ^ 0x5A5A5A))
+    return [np.rint(rng.laplace(0.0, 0.4 + 0.6 * l, size=s)).astype(np.int32)
+            for l, s in enumerate(level_shapes(H, W, levels))]
