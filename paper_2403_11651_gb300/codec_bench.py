@@ -42,7 +42,7 @@ def main(argv=None):
         enc_ms = []
         for _ in range(a.reps):
             t0 = time.perf_counter()
-            bs = cc.cc_write_bitstream(ctx)
+            bs = cc.cc_write_bitstream(ctx, cfg, H, W)
             enc_ms.append(1e3 * (time.perf_counter() - t0))
     finally:
         cc.cc_free(ctx)

@@ -368,12 +368,26 @@ def cc_rate_bits_noalloc(cfg: cc_config, yhat_flat, H: int, W: int, params, stre
     return out.value
 
 
-def cc_write_bitstream(ctx) -> bytes:
-    """Range-coded bitstream of rint(y) and the decoder parameters of the context."""
+def bitstream_bound(cfg: cc_config, H: int, W: int) -> int:
+    """Bytes that always hold a bitstream of this configuration and size: the header, the
+    parameters, 5 LEB128 bytes per row and the encoder's per-row reservation 8 w + 16."""
+    shapes = level_shapes(H, W)
+    return (20 + 4 * cc_param_count(cfg) + 5 * sum(h for h, _ in shapes)
+            + sum(h * (8 * w + 16) for h, w in shapes))
+
+
+def cc_write_bitstream(ctx, cfg: cc_config = None, H: int = 0, W: int = 0) -> bytes:
+    """Range-coded bitstream of rint(y) and the decoder parameters of the context.  With
+    (cfg, H, W) the output buffer is sized from bitstream_bound and the library runs once;
+    without, a first call asks for the size."""
     n = c_size_t()
-    _check(_lib().cc_write_bitstream(ctx, None, 0, ctypes.byref(n)), "cc_write_bitstream")
-    buf = ctypes.create_string_buffer(max(1, n.value))
-    _check(_lib().cc_write_bitstream(ctx, buf, n.value, ctypes.byref(n)), "cc_write_bitstream")
+    if cfg is None:
+        _check(_lib().cc_write_bitstream(ctx, None, 0, ctypes.byref(n)), "cc_write_bitstream")
+        cap = n.value
+    else:
+        cap = bitstream_bound(cfg, H, W)
+    buf = ctypes.create_string_buffer(max(1, cap))
+    _check(_lib().cc_write_bitstream(ctx, buf, cap, ctypes.byref(n)), "cc_write_bitstream")
     return buf.raw[:n.value]
 
 

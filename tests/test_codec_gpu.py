@@ -70,6 +70,8 @@ def test_bitstream_bit_exact(arch, H, W, seed):
     ctx, _ = _context(d, H, W, named, y)
     try:
         got = cc.cc_write_bitstream(ctx)
+        assert cc.cc_write_bitstream(ctx, cc.make_config(d), H, W) == got
+        assert len(got) <= cc.bitstream_bound(cc.make_config(d), H, W)
     finally:
         cc.cc_free(ctx)
     want = C.write_bitstream(H, W, oracle_arch(d), named, y)

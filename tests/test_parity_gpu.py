@@ -199,7 +199,15 @@ def test_c2_full_size_gradients():
 
 
 def test_c2_final_rd_cost_golden(golden_dir):
-    """10 000 iterations (last 20 % straight-through) against the stored oracle run."""
+    """10 000 iterations (last 20 % straight-through) against the stored oracle run.
+
+    FP32 and FP64 runs of 10^4 Adam steps decorrelate (the loss moves by ~3 % between
+    samples 100 iterations apart in the stored run); what must agree is where they end up.
+    Tolerances from measured spreads: the GPU's final hard cost over six noise seeds from
+    the same initial state has a standard deviation of 1.6 % of its mean, so the final
+    hard cost must lie within 3 of those (5 %); the mean training loss over the oracle's
+    21 stored samples from iteration 8000 on (per-sample spread 3.1 %, so ~0.7 % on a
+    mean) must agree within 2 %."""
     path = os.path.join(golden_dir, "c2_lam1e-3.json")
     if not os.path.exists(path):
         pytest.skip("stored oracle run not present")
@@ -213,9 +221,15 @@ def test_c2_final_rd_cost_golden(golden_dir):
     try:
         cc.cc_encode_iters(ctx, ref["iters"])
         D, R, cost = cc.cc_rd_cost(ctx, True)
-        assert _rel(cost, ref["final_hard"]["cost"]) < 1e-2, (cost, ref["final_hard"])
+        first = ref["iters"] - 2000
+        log = cc.cc_get_losses(ctx, first, 2000)           # rows: D, R, loss
     finally:
         cc.cc_free(ctx)
+    traj = np.array(ref["trajectory"])
+    late = traj[traj[:, 0] >= first]
+    gpu_mean = log[late[:, 0].astype(int) - first, 2].mean()
+    assert _rel(gpu_mean, late[:, 1].mean()) < 0.02, (gpu_mean, late[:, 1].mean())
+    assert _rel(cost, ref["final_hard"]["cost"]) < 0.05, (cost, ref["final_hard"])
 
 
 def test_deterministic_and_resume():
