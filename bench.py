@@ -295,7 +295,24 @@ def run_ours(a, cfgd):
     torch.cuda.synchronize(dev)
     full_s = ev0.elapsed_time(ev1) / 1e3
     final = cc.cc_rd_cost(ctx2, True)
+    # the latent bitstream of the trained image: GPU encode, then GPU decode (each timed
+    # on its second call; the first builds the frequency tables and allocates)
+    for _ in range(2):
+        t0 = time.perf_counter()
+        bs = cc.cc_write_bitstream(ctx2, cfg, H, W)
+        enc_ms = 1e3 * (time.perf_counter() - t0)
+    y_int = np.rint(cc.cc_get_latents(ctx2, n_lat)).astype(np.int32)
     cc.cc_free(ctx2)
+    for _ in range(2):
+        t0 = time.perf_counter()
+        _, lat, lat_ms = cc.cc_decode_bitstream(bs)
+        dec_ms = 1e3 * (time.perf_counter() - t0)
+    codec = {"workload": f"{H}x{W} after the full schedule", "bytes": len(bs),
+             "bpp": 8.0 * len(bs) / (H * W), "model_rate_bpp": final[1],
+             "encode_ms": enc_ms, "latent_decode_ms": lat_ms,
+             "decode_ms": dec_ms, "latents_exact": bool(np.array_equal(lat, y_int)),
+             "note": "decode_ms: whole cc_decode_bitstream call (context set-up, upload, "
+                     "wavefront latent decode, upsampling and synthesis, image to host)"}
 
     pk, src = peaks()
     props = torch.cuda.get_device_properties(dev)
@@ -330,6 +347,7 @@ def run_ours(a, cfgd):
         "time_to_final_rd_s": {"iters": cfgd["total_iters"], "seconds": full_s,
                                "final_hard_rd": {"D": final[0], "R_bpp": final[1],
                                                  "cost": final[2]}},
+        "bitstream": codec,
     }
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         v, n, dt, cores = oracle_rate(cfgd, 15.0, H, W)
