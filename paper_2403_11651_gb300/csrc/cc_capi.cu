@@ -147,6 +147,7 @@ struct cc_ctx {
   cudaStream_t cap = nullptr;
   cudaStream_t side = nullptr;        // ARM branch of a pass, concurrent with the synthesis
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_arm = nullptr, ev_chain = nullptr;   // ARM done (side) / chain done (main)
   cudaEvent_t ev_a0 = nullptr, ev_a1 = nullptr;   // timing of the ARM kernel in forked passes
   bool own_mem = false;
   void* mem = nullptr;
@@ -393,10 +394,11 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
   CKE(arm_launch(a, backward, c->yhat_bord, c->geo, c->maps, c->tiles, c->n_tiles, c->grid_arm,
                  c->dctx, c->gself, c->part_arm, c->part_bits, &c->sc->fault, sa));
   if (fork) CKE(record_on_side(c->ev_a1));
+  if (fork) CKE(cudaEventRecord(c->ev_arm, sa));
   // the context gather follows the ARM on its stream; timed per phase it runs after the
   // upsampling adjoint instead, so that the phase events stay in stream order
   if (backward && fork) CKE(ctx_gather(c->geo, c->offs, a.N, c->gself, c->dctx, sa));
-  if (fork) CKE(cudaEventRecord(c->ev_join, sa));
+  if (fork && !backward) CKE(cudaEventRecord(c->ev_join, sa));
   CKE(mark(2));
   CKE(up_forward(a, c->geo, c->yhat, c->up, c->grid_syn, s));
   CKE(mark(3));
@@ -409,17 +411,38 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
     CKE(mark(5));
     CKE(up_backward(a, c->geo, c->yhat, c->up, c->gsyn, c->part_up, c->grid_syn, s));
     CKE(mark(6));
-    if (fork) CKE(cudaStreamWaitEvent(s, c->ev_join, 0));
-    else CKE(ctx_gather(c->geo, c->offs, a.N, c->gself, c->dctx, s));
+    PassFinish pf;
+    pf.part_d = c->part_d; pf.nd = c->grid_tiles; pf.part_bits = c->part_bits;
+    pf.nb = c->grid_arm; pf.d_scale = 1.0 / (3.0 * (double)HW); pf.r_scale = 1.0 / (double)HW;
+    pf.lam = (double)c->cfg.lam; pf.log = c->log;
+    // the parameter update (after the reduction of the partial sums) and the latent update
+    // are independent; forked, they run at once and the last block of either finishes
+    // the pass
+    const unsigned tickets = latent_update_blocks(c->geo) + param_update_blocks(c->lay);
+    const float rate_scale = (float)((double)c->cfg.lam / (double)c->HW);
+    auto latents = [&](cudaStream_t q) {
+      return latent_update(c->geo, c->gsyn, c->gself, rate_scale, c->y, c->my, c->vy, grad_out,
+                           apply, c->cfg.lr, c->sc, pf, tickets, advance, c->dq,
+                           soft_mode(c, qmode), c->ste_start, q);
+    };
+    if (fork) {
+      CKE(cudaEventRecord(c->ev_chain, s));
+      CKE(cudaStreamWaitEvent(sa, c->ev_chain, 0));
+      CKE(latents(sa));
+      CKE(cudaStreamWaitEvent(s, c->ev_arm, 0));
+    } else {
+      CKE(ctx_gather(c->geo, c->offs, a.N, c->gself, c->dctx, s));
+    }
     CKE(reduce_sections(c->tab, c->part2, c->n_virtual, c->slices, s));
     CKE(param_update(c->lay, a, c->part2, c->slices, c->params, c->mp, c->vp,
                      grad_out ? grad_out + c->geo.n_lat : nullptr, apply, c->cfg.lr, c->sc,
-                     image_slots(c), s));
-    CKE(latent_update(c->geo, c->gsyn, c->gself, (float)((double)c->cfg.lam / (double)c->HW),
-                      c->y, c->my, c->vy, grad_out, apply, c->cfg.lr, c->sc, c->part_d,
-                      c->grid_tiles, c->part_bits, c->grid_arm, 1.0 / (3.0 * (double)HW),
-                      1.0 / (double)HW, (double)c->cfg.lam, c->log, advance, c->dq,
-                      soft_mode(c, qmode), c->ste_start, s));
+                     image_slots(c), &pf, tickets, advance, s));
+    if (fork) {
+      CKE(cudaEventRecord(c->ev_join, sa));
+      CKE(cudaStreamWaitEvent(s, c->ev_join, 0));
+    } else {
+      CKE(latents(s));
+    }
   } else {
     if (fork) CKE(cudaStreamWaitEvent(s, c->ev_join, 0));
     CKE(finish_iteration(c->part_d, c->grid_tiles, c->part_bits, c->grid_arm,
@@ -544,6 +567,8 @@ int init_common(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
     return bail(fail_cuda(ce, "cudaStreamCreate"));
   if ((ce = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
       (ce = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess ||
+      (ce = cudaEventCreateWithFlags(&c->ev_arm, cudaEventDisableTiming)) != cudaSuccess ||
+      (ce = cudaEventCreateWithFlags(&c->ev_chain, cudaEventDisableTiming)) != cudaSuccess ||
       (ce = cudaEventCreate(&c->ev_a0)) != cudaSuccess ||
       (ce = cudaEventCreate(&c->ev_a1)) != cudaSuccess)
     return bail(fail_cuda(ce, "cudaEventCreate"));
@@ -1146,6 +1171,8 @@ void cc_free(cc_ctx* c) {
   if (c->side) cudaStreamDestroy(c->side);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_arm) cudaEventDestroy(c->ev_arm);
+  if (c->ev_chain) cudaEventDestroy(c->ev_chain);
   if (c->ev_a0) cudaEventDestroy(c->ev_a0);
   if (c->ev_a1) cudaEventDestroy(c->ev_a1);
   if (c->own_mem && c->mem) cudaFree(c->mem);

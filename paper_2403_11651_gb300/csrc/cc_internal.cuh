@@ -216,18 +216,31 @@ struct ImageSlots {
   float* arm_image;
   float* syn_image;
 };
+// What finishing a pass reads: the per-CTA partial sums of D and of the bits, their
+// scales, lambda and the loss log (finish_iteration).
+struct PassFinish {
+  const float* part_d;
+  int nd;
+  const float* part_bits;
+  int nb;
+  double d_scale, r_scale, lam;
+  double* log;
+};
+// The pass is finished by the last block to end among the latent update's blocks and, if
+// it takes part (pf != nullptr), the parameter update's: tickets = the sum of their block
+// counts (latent_update_blocks, param_update_blocks).
+unsigned param_update_blocks(const Layout& lay);
+unsigned latent_update_blocks(const Geo& g);
 cudaError_t param_update(const Layout& lay, const Arch& a, const float* part2, int slices,
                          float* params, float* m, float* v, float* grad_out, bool apply,
-                         float lr, const IterScalars* sc, const ImageSlots& slots, cudaStream_t st);
+                         float lr, const IterScalars* sc, const ImageSlots& slots,
+                         const PassFinish* pf, unsigned tickets, bool advance, cudaStream_t st);
 // Total latent gradient dD/dy_hat + lambda / (HW) * dR/dy_hat (grate: the rate gradient
 // after ctx_gather) and Adam on the latents.
-// ... and finishes the pass as finish_iteration does (its last block).
 cudaError_t latent_update(const Geo& g, const float* gsyn, const float* grate, float rate_scale,
                           float* y, float* m, float* v, float* grad_out, bool apply, float lr,
-                          IterScalars* sc, const float* part_d, int nd, const float* part_bits,
-                          int nb, double d_scale, double r_scale, double lam, double* log,
-                          bool advance, const float* dq, int soft, int ste_start,
-                          cudaStream_t st);
+                          IterScalars* sc, const PassFinish& pf, unsigned tickets, bool advance,
+                          const float* dq, int soft, int ste_start, cudaStream_t st);
 cudaError_t finish_iteration(const float* part_d, int nd, const float* part_bits, int nb,
                              double d_scale, double r_scale, double lam, IterScalars* sc,
                              double* log, bool advance, cudaStream_t st,

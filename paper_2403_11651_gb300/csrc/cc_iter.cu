@@ -150,21 +150,91 @@ __device__ __forceinline__ void adam_apply(float& p, float& m, float& v, float g
   p -= a.lr * (m * a.inv_bc1) / (sqrtf(v) * a.inv_sqrt_bc2 + 1e-8f);
 }
 
+// D, R and the loss of the pass from the per-CTA partial sums (FP64, fixed order), the
+// loss log entry, and with `advance` the step to the next iteration (t and the Adam powers
+// and bias corrections of its update).  Run by one block of any power-of-two size up to
+// 256: the sums run over 256 virtual lanes in a fixed order, so the result does not
+// depend on which kernel's block finishes the pass.
+__device__ __forceinline__ void finish_block(const float* part_d, int nd, const float* part_bits,
+                                             int nb, double d_scale, double r_scale, double lam,
+                                             IterScalars* sc, double* log, int advance) {
+  __shared__ double sd[256], sb[256];
+  for (int v = threadIdx.x; v < 256; v += blockDim.x) {
+    double a = 0.0, b = 0.0;
+    for (int k = v; k < nd; k += 256) a += (double)part_d[k];
+    for (int k = v; k < nb; k += 256) b += (double)part_bits[k];
+    sd[v] = a;
+    sb[v] = b;
+  }
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    for (int v = threadIdx.x; v < s; v += blockDim.x) {
+      sd[v] += sd[v + s];
+      sb[v] += sb[v + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double D = sd[0] * d_scale, R = sb[0] * r_scale;
+    sc->D = D;
+    sc->R = R;
+    sc->loss = D + lam * R;
+    const int t = sc->t;
+    double* e = log + 3 * (long long)(t % kLogCap);
+    e[0] = D;
+    e[1] = R;
+    e[2] = D + lam * R;
+    if (advance) {
+      const double b1 = sc->b1t * 0.9, b2 = sc->b2t * 0.999;   // beta^(t+1)
+      sc->t = t + 1;
+      sc->b1t = b1;
+      sc->b2t = b2;
+      sc->inv_bc1 = (float)(1.0 / (1.0 - b1 * 0.9));             // step t + 2
+      sc->inv_sqrt_bc2 = (float)(1.0 / sqrt(1.0 - b2 * 0.999));
+    }
+  }
+}
+
+// The pass ends with the latent update and the parameter update, which may run on two
+// streams at once; the last of their blocks to end (a ticket in IterScalars counting the
+// blocks of both) finishes the pass (finish_block), after every block has read the
+// iteration's scalars.
+struct FinishArgs {
+  const float* part_d;
+  int nd;
+  const float* part_bits;
+  int nb;
+  double d_scale, r_scale, lam;
+  double* log;
+  int advance;
+  unsigned tickets;   // blocks that take a ticket: the latent update's, plus the parameter
+                      // update's when it shares the finish
+};
+
+__device__ __forceinline__ void finish_if_last(IterScalars* sc, const FinishArgs& fa) {
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&sc->ticket, 1u) == fa.tickets - 1;
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    finish_block(fa.part_d, fa.nd, fa.part_bits, fa.nb, fa.d_scale, fa.r_scale, fa.lam, sc,
+                 fa.log, fa.advance);
+    if (threadIdx.x == 0) sc->ticket = 0u;
+  }
+}
+
 struct VirtualMap {
   int n_arm, up0, syn0, n1x1, nconv, K2, n_up, per_level;
   int vsyn, vconv, vup, n_virtual;
 };
 
-// Adam bias corrections of this iteration are read from IterScalars (set when t advanced).
-__global__ void __launch_bounds__(128) k_param_update(VirtualMap vm, const float* part2,
-                                                      int slices, float* params, float* m,
-                                                      float* v, float* grad_out, int apply,
-                                                      float lr, IterScalars* sc, int total,
-                                                      ImageSlots slots) {
-  pdl_wait();
-  pdl_trigger();
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= total) return;
+__device__ __forceinline__ void param_update_one(const VirtualMap& vm, const float* part2,
+                                                 int slices, float* params, float* m, float* v,
+                                                 float* grad_out, int apply, float lr,
+                                                 const IterScalars* sc, int j,
+                                                 const ImageSlots& slots) {
   AdamStep st;
   st.lr = lr;
   st.inv_bc1 = sc->inv_bc1;
@@ -205,9 +275,36 @@ __global__ void __launch_bounds__(128) k_param_update(VirtualMap vm, const float
   }
 }
 
+// Adam bias corrections of this iteration are read from IterScalars (set when t advanced).
+__global__ void __launch_bounds__(128) k_param_update(VirtualMap vm, const float* part2,
+                                                      int slices, float* params, float* m,
+                                                      float* v, float* grad_out, int apply,
+                                                      float lr, IterScalars* sc, int total,
+                                                      ImageSlots slots, FinishArgs fa) {
+  pdl_wait();
+  pdl_trigger();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < total) param_update_one(vm, part2, slices, params, m, v, grad_out, apply, lr, sc, j,
+                                  slots);
+  if (fa.tickets) finish_if_last(sc, fa);
+}
+
+FinishArgs finish_args(const PassFinish& pf, bool advance, unsigned tickets) {
+  FinishArgs fa;
+  fa.part_d = pf.part_d; fa.nd = pf.nd; fa.part_bits = pf.part_bits; fa.nb = pf.nb;
+  fa.d_scale = pf.d_scale; fa.r_scale = pf.r_scale; fa.lam = pf.lam; fa.log = pf.log;
+  fa.advance = advance ? 1 : 0;
+  fa.tickets = tickets;
+  return fa;
+}
+
+unsigned param_update_blocks(const Layout& lay) { return (unsigned)((lay.total + 127) / 128); }
+unsigned latent_update_blocks(const Geo& g) { return (unsigned)((g.n_pad + 255) / 256); }
+
 cudaError_t param_update(const Layout& lay, const Arch& a, const float* part2, int slices,
                          float* params, float* m, float* v, float* grad_out, bool apply,
                          float lr, const IterScalars* sc, const ImageSlots& slots,
+                         const PassFinish* pf, unsigned tickets, bool advance,
                          cudaStream_t st) {
   VirtualMap vm;
   vm.n_arm = lay.n_arm; vm.up0 = lay.up0; vm.syn0 = lay.syn0;
@@ -215,53 +312,10 @@ cudaError_t param_update(const Layout& lay, const Arch& a, const float* part2, i
   vm.per_level = a.per_level;
   vm.vsyn = lay.n_arm; vm.vconv = vm.vsyn + vm.n1x1; vm.vup = vm.vconv + vm.nconv;
   vm.n_virtual = vm.vup + (kLevels - 1) * vm.K2;
-  return launch_k(k_param_update, dim3((lay.total + 127) / 128), dim3(128), 0, st, vm, part2,
+  const FinishArgs fa = pf ? finish_args(*pf, advance, tickets) : FinishArgs{};
+  return launch_k(k_param_update, dim3(param_update_blocks(lay)), dim3(128), 0, st, vm, part2,
                   slices, params, m, v, grad_out, apply ? 1 : 0, lr,
-                  const_cast<IterScalars*>(sc), lay.total, slots);
-}
-
-// Gradient of a latent: the synthesis path, plus lambda/(HW) times the rate terms in
-// which it appears, as the coded symbol (gself) and in the context of every latent p
-// whose causal neighbourhood contains it (dctx of p at the matching slot).
-// D, R and the loss of the pass from the per-CTA partial sums (FP64, fixed order), the
-// loss log entry, and with `advance` the step to the next iteration (t and the Adam powers
-// and bias corrections of its update).  Run by one block of 256 threads.
-__device__ __forceinline__ void finish_block(const float* part_d, int nd, const float* part_bits,
-                                             int nb, double d_scale, double r_scale, double lam,
-                                             IterScalars* sc, double* log, int advance) {
-  __shared__ double sd[256], sb[256];
-  double a = 0.0, b = 0.0;
-  for (int k = threadIdx.x; k < nd; k += 256) a += (double)part_d[k];
-  for (int k = threadIdx.x; k < nb; k += 256) b += (double)part_bits[k];
-  sd[threadIdx.x] = a;
-  sb[threadIdx.x] = b;
-  __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) {
-      sd[threadIdx.x] += sd[threadIdx.x + s];
-      sb[threadIdx.x] += sb[threadIdx.x + s];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const double D = sd[0] * d_scale, R = sb[0] * r_scale;
-    sc->D = D;
-    sc->R = R;
-    sc->loss = D + lam * R;
-    const int t = sc->t;
-    double* e = log + 3 * (long long)(t % kLogCap);
-    e[0] = D;
-    e[1] = R;
-    e[2] = D + lam * R;
-    if (advance) {
-      const double b1 = sc->b1t * 0.9, b2 = sc->b2t * 0.999;   // beta^(t+1)
-      sc->t = t + 1;
-      sc->b1t = b1;
-      sc->b2t = b2;
-      sc->inv_bc1 = (float)(1.0 / (1.0 - b1 * 0.9));             // step t + 2
-      sc->inv_sqrt_bc2 = (float)(1.0 / sqrt(1.0 - b2 * 0.999));
-    }
-  }
+                  const_cast<IterScalars*>(sc), lay.total, slots, fa);
 }
 
 __global__ void __launch_bounds__(256) k_finish(const float* part_d, int nd,
@@ -273,18 +327,9 @@ __global__ void __launch_bounds__(256) k_finish(const float* part_d, int nd,
   finish_block(part_d, nd, part_bits, nb, d_scale, r_scale, lam, sc, log, advance);
 }
 
-// Also finishes the pass (finish_block): the last of its blocks to end, found with a ticket
-// in IterScalars, runs it once every block has updated its latents.
-struct FinishArgs {
-  const float* part_d;
-  int nd;
-  const float* part_bits;
-  int nb;
-  double d_scale, r_scale, lam;
-  double* log;
-  int advance;
-};
-
+// Gradient of a latent: the synthesis path, plus lambda/(HW) times the rate terms in
+// which it appears, as the coded symbol (gself) and in the context of every latent p
+// whose causal neighbourhood contains it (dctx of p at the matching slot).
 __global__ void __launch_bounds__(256) k_latent_update(Geo g, const float* __restrict__ gsyn,
                                                        const float* __restrict__ grate,
                                                        float rate_scale, float* y, float* m,
@@ -319,30 +364,17 @@ __global__ void __launch_bounds__(256) k_latent_update(Geo g, const float* __res
       y[q] = yv; m[q] = mv; v[q] = vv;
     }
   }
-  __shared__ bool s_last;
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(&sc->ticket, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (s_last) {
-    finish_block(fa.part_d, fa.nd, fa.part_bits, fa.nb, fa.d_scale, fa.r_scale, fa.lam, sc,
-                 fa.log, fa.advance);
-    if (threadIdx.x == 0) sc->ticket = 0u;
-  }
+  finish_if_last(sc, fa);
 }
 
 cudaError_t latent_update(const Geo& g, const float* gsyn, const float* grate, float rate_scale,
                           float* y, float* m, float* v, float* grad_out, bool apply, float lr,
-                          IterScalars* sc, const float* part_d, int nd, const float* part_bits,
-                          int nb, double d_scale, double r_scale, double lam, double* log,
-                          bool advance, const float* dq, int soft, int ste_start,
-                          cudaStream_t st) {
-  FinishArgs fa;
-  fa.part_d = part_d; fa.nd = nd; fa.part_bits = part_bits; fa.nb = nb;
-  fa.d_scale = d_scale; fa.r_scale = r_scale; fa.lam = lam; fa.log = log;
-  fa.advance = advance ? 1 : 0;
-  const int blocks = (int)((g.n_pad + 255) / 256);
-  return launch_k(k_latent_update, dim3(blocks), dim3(256), 0, st, g, gsyn, grate, rate_scale, y,
-                  m, v, grad_out, apply ? 1 : 0, lr, sc, fa, dq, soft, ste_start);
+                          IterScalars* sc, const PassFinish& pf, unsigned tickets, bool advance,
+                          const float* dq, int soft, int ste_start, cudaStream_t st) {
+  const FinishArgs fa = finish_args(pf, advance, tickets);
+  return launch_k(k_latent_update, dim3(latent_update_blocks(g)), dim3(256), 0, st, g, gsyn,
+                  grate, rate_scale, y, m, v, grad_out, apply ? 1 : 0, lr, sc, fa, dq, soft,
+                  ste_start);
 }
 
 cudaError_t finish_iteration(const float* part_d, int nd, const float* part_bits, int nb,
