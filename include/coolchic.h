@@ -106,8 +106,12 @@ int cc_init_image_ws(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
                      const float* init_params, void* cuda_stream,
                      void* device_workspace, size_t ws_bytes, cc_ctx** out);
 
-/* Replace the image of a context by another one of the same size (host or device);
- * asynchronous on the context stream. */
+/* Replace the image of a context by another one of the same size (host or device).
+ * Asynchronous: the copy is issued on a stream of the context's own, where it overlaps the
+ * iterations already issued (it waits only for the previous image's conversion); the
+ * conversion to the float planes the iterations read follows on the context stream.  The
+ * caller keeps rgb_hwc unchanged until the context stream has passed this call; from
+ * page-locked host memory the copy does not block the host. */
 int cc_set_image(cc_ctx* ctx, const uint8_t* rgb_hwc);
 
 /* Run n_iters overfitting iterations (forward, backward, Adam), asynchronously on the
@@ -142,6 +146,14 @@ int cc_forward_backward(cc_ctx* ctx, const float* noise_override, int hard,
 /* D, R_bpp and loss of iterations first .. first+count-1 (3 doubles each, host or
  * device).  Only the last 4096 iterations are kept.  Synchronises. */
 int cc_get_losses(cc_ctx* ctx, int first, int count, double* out);
+
+/* The same entries copied asynchronously: the copy is enqueued on the context stream
+ * behind the iterations already issued and the call returns at once (no check for
+ * non-finite values).  out: device or page-locked host memory (pageable host memory makes
+ * the copy synchronous); valid to read once the stream has passed the copy (an event
+ * recorded after this call, or a stream synchronisation).  Lets a training loop read each
+ * step's loss without waiting for the step to finish. */
+int cc_get_losses_async(cc_ctx* ctx, int first, int count, double* out);
 
 /* Overwrite / read the latents y (n_latents floats, flat latent order) or the parameters
  * (cc_param_count floats, flat parameter order); host or device buffers.  The setters are

@@ -58,6 +58,7 @@ def _declare(lib):
         "cc_get_grads": (c_int, [P, P, P]),
         "cc_forward_backward": (c_int, [P, P, c_int, P, POINTER(c_double), POINTER(c_double)]),
         "cc_get_losses": (c_int, [P, c_int, c_int, P]),
+        "cc_get_losses_async": (c_int, [P, c_int, c_int, P]),
         "cc_iteration": (c_int, [P, POINTER(c_int)]),
         "cc_set_latents": (c_int, [P, P]),
         "cc_get_latents": (c_int, [P, P]),
@@ -288,6 +289,14 @@ def cc_get_losses(ctx, first: int, count: int):
     return out
 
 
+def cc_get_losses_async(ctx, first: int, count: int, out):
+    """Enqueue the copy of log entries into out (device or pinned host, count x 3 float64);
+    read it after the context stream has passed the copy."""
+    _check(_lib().cc_get_losses_async(ctx, int(first), int(count), _ptr(out)),
+           "cc_get_losses_async")
+    return out
+
+
 def cc_iteration(ctx) -> int:
     t = c_int()
     _check(_lib().cc_iteration(ctx, ctypes.byref(t)), "cc_iteration")
@@ -429,7 +438,8 @@ def cc_strerror(code: int) -> str:
 
 EXPORTED = ["cc_param_count", "cc_latent_count", "cc_workspace_size", "cc_init_image",
             "cc_init_image_ws", "cc_set_image", "cc_encode_iters", "cc_rd_cost", "cc_decode",
-            "cc_get_grads", "cc_forward_backward", "cc_get_losses", "cc_iteration", "cc_noise",
+            "cc_get_grads", "cc_forward_backward", "cc_get_losses", "cc_get_losses_async",
+            "cc_iteration", "cc_noise",
             "cc_set_latents", "cc_get_latents", "cc_set_params", "cc_get_params",
             "cc_profile_phases", "cc_graph_kernel_count", "cc_arm_kernel_ms", "cc_rate_bits_noalloc",
             "cc_get_state", "cc_set_state", "cc_write_bitstream", "cc_bitstream_info",

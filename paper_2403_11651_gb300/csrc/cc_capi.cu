@@ -148,6 +148,8 @@ struct cc_ctx {
   cudaStream_t side = nullptr;        // ARM branch of a pass, concurrent with the synthesis
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_arm = nullptr, ev_chain = nullptr;   // ARM done (side) / chain done (main)
+  cudaStream_t up_st = nullptr;                         // image uploads
+  cudaEvent_t ev_planar = nullptr, ev_uploaded = nullptr;
   cudaEvent_t ev_a0 = nullptr, ev_a1 = nullptr;   // timing of the ARM kernel in forked passes
   bool own_mem = false;
   void* mem = nullptr;
@@ -565,10 +567,14 @@ int init_common(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
   if (ce != cudaSuccess) return bail(fail_cuda(ce, "cudaStreamCreate"));
   if ((ce = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(fail_cuda(ce, "cudaStreamCreate"));
+  if ((ce = cudaStreamCreateWithFlags(&c->up_st, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(fail_cuda(ce, "cudaStreamCreate"));
   if ((ce = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
       (ce = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess ||
       (ce = cudaEventCreateWithFlags(&c->ev_arm, cudaEventDisableTiming)) != cudaSuccess ||
       (ce = cudaEventCreateWithFlags(&c->ev_chain, cudaEventDisableTiming)) != cudaSuccess ||
+      (ce = cudaEventCreateWithFlags(&c->ev_planar, cudaEventDisableTiming)) != cudaSuccess ||
+      (ce = cudaEventCreateWithFlags(&c->ev_uploaded, cudaEventDisableTiming)) != cudaSuccess ||
       (ce = cudaEventCreate(&c->ev_a0)) != cudaSuccess ||
       (ce = cudaEventCreate(&c->ev_a1)) != cudaSuccess)
     return bail(fail_cuda(ce, "cudaEventCreate"));
@@ -579,6 +585,7 @@ int init_common(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
   if ((ce = cudaMemcpyAsync(c->img_u8, rgb_hwc, (size_t)3 * c->HW, cudaMemcpyDefault, c->st)))
     return bail(fail_cuda(ce, "image copy"));
   if ((ce = image_to_planar(c->img_u8, c->x, H, W, c->st))) return bail(fail_cuda(ce, "image"));
+  if ((ce = cudaEventRecord(c->ev_planar, c->st))) return bail(fail_cuda(ce, "event"));
   std::vector<float> hp;
   const float* src = init_params;
   if (!src) {
@@ -673,8 +680,14 @@ int cc_init_image_ws(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
 int cc_set_image(cc_ctx* c, const uint8_t* rgb_hwc) {
   if (!c || !rgb_hwc) return CC_EINVAL;
   CK(cudaSetDevice(c->dev));
-  CK(cudaMemcpyAsync(c->img_u8, rgb_hwc, (size_t)3 * c->HW, cudaMemcpyDefault, c->st));
+  // the copy runs on its own stream as soon as the previous image has been converted, so
+  // that it overlaps the iterations still running; only the conversion waits for them
+  CK(cudaStreamWaitEvent(c->up_st, c->ev_planar, 0));
+  CK(cudaMemcpyAsync(c->img_u8, rgb_hwc, (size_t)3 * c->HW, cudaMemcpyDefault, c->up_st));
+  CK(cudaEventRecord(c->ev_uploaded, c->up_st));
+  CK(cudaStreamWaitEvent(c->st, c->ev_uploaded, 0));
   CK(image_to_planar(c->img_u8, c->x, c->geo.H, c->geo.W, c->st));
+  CK(cudaEventRecord(c->ev_planar, c->st));
   return CC_OK;
 }
 
@@ -763,21 +776,49 @@ int cc_get_grads(cc_ctx* c, const float* noise_override, float* grads_out) {
   return cc_forward_backward(c, noise_override, -1, grads_out, nullptr, nullptr);
 }
 
+}  // extern "C"
+
+namespace {
+
+// enqueue copies of log entries first .. first+count-1 (one or two contiguous runs of the
+// ring) to out (3 doubles per entry)
+cudaError_t copy_log(cc_ctx* c, int first, int count, double* out, cudaMemcpyKind kind) {
+  int k = 0;
+  while (k < count) {
+    const int slot = (first + k) % kLogCap;
+    const int run = std::min(count - k, kLogCap - slot);
+    cudaError_t e = cudaMemcpyAsync(out + 3 * (size_t)k, c->log + 3 * (size_t)slot,
+                                    3 * (size_t)run * sizeof(double), kind, c->st);
+    if (e != cudaSuccess) return e;
+    k += run;
+  }
+  return cudaSuccess;
+}
+
+bool log_range_ok(const cc_ctx* c, int first, int count) {
+  return first >= 0 && count >= 0 && first + count <= c->iter && first >= c->iter - kLogCap;
+}
+
+}  // namespace
+
+extern "C" {
+
 int cc_get_losses(cc_ctx* c, int first, int count, double* out) {
-  if (!c || !out || first < 0 || count < 0 || first + count > c->iter ||
-      first < c->iter - kLogCap)
-    return CC_EINVAL;
+  if (!c || !out || !log_range_ok(c, first, count)) return CC_EINVAL;
   CK(cudaSetDevice(c->dev));
-  std::vector<double> all((size_t)kLogCap * 3);
-  CK(cudaMemcpyAsync(all.data(), c->log, all.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                     c->st));
-  CK(cudaStreamSynchronize(c->st));
   std::vector<double> pick((size_t)count * 3);
-  for (int k = 0; k < count; ++k)
-    for (int j = 0; j < 3; ++j) pick[k * 3 + j] = all[((first + k) % kLogCap) * 3 + j];
+  CK(copy_log(c, first, count, pick.data(), cudaMemcpyDeviceToHost));
+  CK(cudaStreamSynchronize(c->st));
   CK(cudaMemcpy(out, pick.data(), pick.size() * sizeof(double), cudaMemcpyDefault));
   for (double v : pick)
     if (!std::isfinite(v)) return CC_ENONFINITE;
+  return CC_OK;
+}
+
+int cc_get_losses_async(cc_ctx* c, int first, int count, double* out) {
+  if (!c || !out || !log_range_ok(c, first, count)) return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  CK(copy_log(c, first, count, out, cudaMemcpyDefault));
   return CC_OK;
 }
 
@@ -1169,6 +1210,12 @@ void cc_free(cc_ctx* c) {
   if (c->side) cudaStreamSynchronize(c->side);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->up_st) {
+    cudaStreamSynchronize(c->up_st);
+    cudaStreamDestroy(c->up_st);
+  }
+  if (c->ev_planar) cudaEventDestroy(c->ev_planar);
+  if (c->ev_uploaded) cudaEventDestroy(c->ev_uploaded);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->ev_arm) cudaEventDestroy(c->ev_arm);

@@ -291,3 +291,56 @@ def test_bad_state_blob_rejected():
     finally:
         p.close()
         q.close()
+
+
+def test_losses_async_matches_sync():
+    """cc_get_losses_async copies the same log entries as cc_get_losses, across the ring's
+    wrap-around, into pinned host or device memory; evicted entries are refused."""
+    d = config_dict("c1", total_iters=5000)
+    H, W = 32, 32
+    cfg = cc.make_config(d, seed=4)
+    rgb = syn.synthetic_image(H, W, 4)
+    ctx = cc.cc_init_image(cfg, rgb, H, W)
+    try:
+        cc.cc_encode_iters(ctx, 4100)
+        ref = cc.cc_get_losses(ctx, 4, 4096)
+        host = torch.zeros((4096, 3), dtype=torch.float64).pin_memory()
+        cc.cc_get_losses_async(ctx, 4, 4096, host)
+        dev = torch.zeros((10, 3), dtype=torch.float64, device="cuda")
+        cc.cc_get_losses_async(ctx, 4090, 10, dev)
+        torch.cuda.synchronize()
+        assert np.array_equal(host.numpy(), ref)
+        assert np.array_equal(dev.cpu().numpy(), ref[-10:])
+        with pytest.raises(cc.CCError):
+            cc.cc_get_losses_async(ctx, 3, 1, host)
+        with pytest.raises(cc.CCError):
+            cc.cc_get_losses_async(ctx, 4099, 2, host)
+    finally:
+        cc.cc_free(ctx)
+
+
+def test_set_image_replaces_the_image():
+    """After cc_set_image (pinned host or device source) a context iterates exactly as a
+    context created with that image."""
+    d = config_dict("c1")
+    H, W = 40, 56
+    cfg = cc.make_config(d, seed=5)
+    img_a, img_b = syn.synthetic_image(H, W, 5), syn.synthetic_image(H, W, 6)
+    init = cc.flatten_params(syn.initial_parameters(syn.ArchSizes.from_config(d), 5), cfg)
+    ca = cc.cc_init_image(cfg, img_a, H, W, init)
+    cb = cc.cc_init_image(cfg, img_b, H, W, init)
+    cc2 = cc.cc_init_image(cfg, img_b, H, W, init)
+    try:
+        cc.cc_set_image(ca, torch.from_numpy(img_b).pin_memory())
+        cc.cc_encode_iters(ca, 5)
+        la = cc.cc_get_losses(ca, 0, 5)
+        cc.cc_encode_iters(cb, 5)
+        lb = cc.cc_get_losses(cb, 0, 5)
+        assert np.array_equal(la, lb)
+        cc.cc_set_image(cc2, torch.from_numpy(img_a).cuda())
+        cc.cc_set_image(cc2, torch.from_numpy(img_b).cuda())
+        cc.cc_encode_iters(cc2, 5)
+        assert np.array_equal(cc.cc_get_losses(cc2, 0, 5), lb)
+    finally:
+        for c in (ca, cb, cc2):
+            cc.cc_free(c)
