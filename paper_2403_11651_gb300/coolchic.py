@@ -395,9 +395,9 @@ def cc_write_bitstream(ctx, cfg: cc_config = None, H: int = 0, W: int = 0) -> by
         cap = n.value
     else:
         cap = bitstream_bound(cfg, H, W)
-    buf = ctypes.create_string_buffer(max(1, cap))
-    _check(_lib().cc_write_bitstream(ctx, buf, cap, ctypes.byref(n)), "cc_write_bitstream")
-    return buf.raw[:n.value]
+    buf = np.empty(max(1, cap), np.uint8)          # not zero-filled
+    _check(_lib().cc_write_bitstream(ctx, _ptr(buf), cap, ctypes.byref(n)), "cc_write_bitstream")
+    return buf[:n.value].tobytes()
 
 
 def cc_bitstream_info(bs: bytes):

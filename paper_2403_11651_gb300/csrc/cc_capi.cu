@@ -1057,7 +1057,7 @@ int cc_write_bitstream(cc_ctx* c, uint8_t* out, size_t capacity, size_t* nbytes)
   std::vector<int32_t> q((size_t)c->lay.n_arm);
   if (!codec_quantize_arm(p.data(), a.N, a.NL, q.data()))
     return set_msg(CC_ENONFINITE, "non-finite ARM parameter");
-  const CodecGeo cg = codec_geo(c->geo);
+  const CodecGeo cg = codec_geo(c->geo, 32);
   const std::vector<uint16_t>& tab = codec_tables();
   DevBuf d_tab, d_sym, d_rows, d_len, d_flag, d_off, d_out;
   CK(d_tab.alloc(codec_table_bytes()));
@@ -1140,7 +1140,7 @@ int cc_decode_bitstream(const uint8_t* bs, size_t nbytes, void* cuda_stream, flo
     }
   }
   const Geo g = geo_of(H, W);
-  const CodecGeo cg = codec_geo(g);
+  const CodecGeo cg = codec_geo(g, 32 / codec_decode_parts(a.N));
   std::vector<long long> row_off((size_t)cg.rows);
   std::vector<int> row_len((size_t)cg.rows);
   long long body = 0;

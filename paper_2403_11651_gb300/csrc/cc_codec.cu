@@ -29,6 +29,7 @@
 //           bytes are dropped (the decoder reads zeros past the end of a substream).
 //   streams: one substream per latent row, so that rows decode as a wavefront.
 #include <climits>
+#include <cstdlib>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -288,23 +289,10 @@ __global__ void __launch_bounds__(256) k_codec_pack(CodecGeo cg, const uint8_t* 
   for (int i = threadIdx.x; i < row_len[row]; i += blockDim.x) dst[i] = src[i];
 }
 
-// ---------------------------------------------------------------------------------------
-// Decoder.  The rows of a level form bands of 32; a warp decodes one band at a time, lane i
-// holding row r0 + i, which decodes position x at the band's local step x + lag i, so
-// that inside the band every causal neighbour was decoded at an earlier step (lag =
-// max over context offsets of ceil((dx + 1) / -dy)).  A band may run local step s once
-// its predecessor band (the 32 rows above) has completed s + 32 lag steps: then every
-// neighbour in those rows is decoded too.  Bands publish their completed step count every
-// 4 steps (release) and wait on their predecessor's (acquire, bounded).  All levels run
-// at once; warps take bands in increasing order, which keeps the waits acyclic, and the
-// cooperative launch keeps every warp resident.
-// ---------------------------------------------------------------------------------------
-
-constexpr int kBandRows = 32;
 constexpr int kDecWarps = 4;                 // warps per block: one per scheduler
 constexpr int kMaxPolls = 1 << 22;           // bounded wait on the predecessor band
 constexpr int kRing = 64;                    // columns of the predecessor rows kept in smem
-constexpr int kFill = 16;                    // steps between ring refills
+constexpr int kFill = 8;                     // steps between ring refills
 
 // The causal offsets (dy, dx) of N = 8, 16, 24 in raster order (the N nearest causal
 // neighbours, ties by smaller |dy| then smaller dx) as compile-time tables: the decoder
@@ -365,18 +353,70 @@ template <int N> __host__ __device__ constexpr int win_of() {
   return m + 1;
 }
 
+// The fixed-point ARM with one row's LinR layers split over its P lanes: lane part p
+// computes outputs [p N / P, (p + 1) N / P) from shared-memory weights (each LinR
+// matrix transposed, as in the constant bank), the ReLU terms are exchanged by shuffles
+// and every lane applies all of them, so that the activations stay replicated; the two
+// outputs are computed whole by every lane.  Integer sums: the same bits as arm_fixed.
+template <int N, int NL, int P>
+__device__ __forceinline__ void arm_fixed_split(const int (&ctx)[N], const int* s_w, int p,
+                                                int lane, int& mu, int& s) {
+  constexpr int OPL = N / P;                 // outputs per lane, loaded as int2 pairs
+  static_assert(N % (2 * P) == 0, "outputs per lane must be even");
+  int a[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) a[j] = min(max(ctx[j], -kCtxLim), kCtxLim) * (1 << kQFrac);
+  const int base = lane & ~(P - 1);
+#pragma unroll
+  for (int i = 0; i < NL; ++i) {
+    const int* Wt = s_w + i * (N * N + N);
+    const int* b = Wt + N * N;
+    int acc[OPL];
+#pragma unroll
+    for (int k = 0; k < OPL; ++k) acc[k] = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const int2* wr = reinterpret_cast<const int2*>(Wt + j * N + p * OPL);
+#pragma unroll
+      for (int k = 0; k < OPL / 2; ++k) {
+        const int2 wv = wr[k];
+        acc[2 * k] += wv.x * a[j];
+        acc[2 * k + 1] += wv.y * a[j];
+      }
+    }
+    int z[OPL];
+#pragma unroll
+    for (int k = 0; k < OPL; ++k) z[k] = max(sat(((acc[k] + 128) >> kQFrac) + b[p * OPL + k]), 0);
+#pragma unroll
+    for (int o = 0; o < N; ++o)
+      a[o] = sat(a[o] + __shfl_sync(0xFFFFFFFFu, z[o % OPL], base | (o / OPL)));
+  }
+  const int* W = s_w + NL * (N * N + N);
+  const int* b = W + 2 * N;
+  int acc0 = 0, acc1 = 0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    acc0 += W[j] * a[j];
+    acc1 += W[N + j] * a[j];
+  }
+  mu = sat(((acc0 + 128) >> kQFrac) + b[0]);
+  s = sat(((acc1 + 128) >> kQFrac) + b[1]);
+}
+
 // ---------------------------------------------------------------------------------------
-// Decoder.  The rows of a level form bands of 32; a warp decodes one band at a time, lane i
-// holding row r0 + i, which decodes position x at the band's local step x + lag i: then
-// every causal neighbour inside the band was decoded at an earlier step.  Each lane keeps
-// its row's last win_of<N>() values in registers (0 before the row starts and after it
-// ends); a neighbour in row r0 + i + dy comes from lane i + dy's registers by a warp
-// shuffle.  Neighbours in the rows above the band come from a shared-memory ring of
-// those rows, refilled every kFill steps (from L2) once the band above has completed
-// enough steps; the band above publishes its completed step count every 4 steps
-// (release) and the refill waits for it (acquire, bounded).  All levels run at once;
-// warps take bands in increasing order, which keeps the waits acyclic, and the
-// cooperative launch keeps every warp resident.
+// Decoder.  The rows of a level form bands of 32 / P rows; a warp decodes one band at a
+// time, the P lanes of row r0 + i together (they split the ARM, see
+// arm_fixed_split, and all run the row's range decoder), row r0 + i decoding position x
+// at the band's local step x + lag i: then every causal neighbour inside the band was
+// decoded at an earlier step.  Each lane keeps its row's last win_of<N>() values in
+// registers (0 before the row starts and after it ends); a neighbour in row
+// r0 + i + dy comes from the registers of the same part of that row by a warp shuffle.
+// Neighbours in the rows above the band come from a shared-memory ring of those rows,
+// refilled every kFill steps (from L2) once the band above has completed enough steps;
+// the band above publishes its completed step count every 4 steps (release) and the
+// refill waits for it (acquire, bounded).  All levels run at once; warps take bands in
+// increasing order, which keeps the waits acyclic, and the cooperative launch keeps every
+// warp resident.
 // ---------------------------------------------------------------------------------------
 
 __device__ __forceinline__ void st_release(int* p, int v) {
@@ -388,19 +428,24 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
-template <int N, int NL>
+template <int N, int NL, int P>
 __global__ void __launch_bounds__(kDecWarps * 32) k_codec_decode(
     CodecGeo cg, const uint16_t* __restrict__ tab, const uint8_t* __restrict__ bytes,
     const long long* __restrict__ row_off, const int* __restrict__ row_len, int* planes,
     int* progress, int* flag) {
   constexpr int LAG = lag_of<N>(), R = reach_of<N>(), WIN = win_of<N>();
+  constexpr int NW = NL * (N * N + N) + 2 * N + 2;
+  constexpr int kBandRows = 32 / P;         // cg.band_rows, set by the host to match
   extern __shared__ __align__(16) uint16_t s_tab[];
   __shared__ int s_ring[kDecWarps][R][kRing];
+  __shared__ __align__(16) int s_w[NW];
   for (int i = threadIdx.x; i < kNtab * kTabStride / 8; i += blockDim.x)
     reinterpret_cast<uint4*>(s_tab)[i] = reinterpret_cast<const uint4*>(tab)[i];
+  for (int i = threadIdx.x; i < NW; i += blockDim.x) s_w[i] = c_qarm[i];
   __syncthreads();
 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int ri = lane / P, part = lane % P;
   int (*ring)[kRing] = s_ring[wid];
   const int tw = gridDim.x * kDecWarps;
   for (int gb = blockIdx.x * kDecWarps + wid; gb < cg.bands; gb += tw) {
@@ -411,7 +456,7 @@ __global__ void __launch_bounds__(kDecWarps * 32) k_codec_decode(
     const int h = cg.h[l], w = cg.w[l];
     const int r0 = kBandRows * b;
     const int nr = min(kBandRows, h - r0);
-    const int r = r0 + lane;
+    const int r = r0 + ri;
     int* plane = planes + cg.off[l];
     const int nsteps = w + LAG * (nr - 1);
     const int pred_steps = w + LAG * (kBandRows - 1);   // a predecessor band is full
@@ -454,7 +499,7 @@ __global__ void __launch_bounds__(kDecWarps * 32) k_codec_decode(
         }
         __syncwarp();
       }
-      const int x = st - LAG * lane;
+      const int x = st - LAG * ri;
       int ctx[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) {
@@ -463,16 +508,17 @@ __global__ void __launch_bounds__(kDecWarps * 32) k_codec_decode(
         if (dy == 0) {
           v = win[-1 - dx];
         } else {
-          v = __shfl_up_sync(0xFFFFFFFFu, win[win_idx<N>(j)], -dy);
-          if (lane + dy < 0) v = ring[-(lane + dy) - 1][(x + dx) & (kRing - 1)];
+          v = __shfl_up_sync(0xFFFFFFFFu, win[win_idx<N>(j)], -dy * P);
+          if (ri + dy < 0) v = ring[-(ri + dy) - 1][(x + dx) & (kRing - 1)];
         }
         ctx[j] = (r + dy >= 0 && x + dx >= 0 && x + dx < w) ? v : 0;
       }
+      int mu, s;
+      arm_fixed_split<N, NL, P>(ctx, s_w, part, lane, mu, s);   // all lanes: shuffles inside
       int val = 0;
-      if (lane < nr && x >= 0 && x < w) {
+      if (ri < nr && x >= 0 && x < w) {
         if (x == 0) dec.init(bytes + row_off[cg.row0[l] + r], row_len[cg.row0[l] + r]);
-        int mu, s, t, m;
-        arm_fixed<N, NL>(ctx, mu, s);
+        int t, m;
         table_of(mu, s, t, m);
         const uint16_t* cr = s_tab + t * kTabStride;
         const uint32_t q = dec.target();
@@ -494,7 +540,7 @@ __global__ void __launch_bounds__(kDecWarps * 32) k_codec_decode(
           k = lo == 0 ? -kA - 1 - (int)e : kA + 1 + (int)e;
         }
         val = m + k;
-        plane[(long long)r * w + x] = val;
+        if (part == 0) plane[(long long)r * w + x] = val;
       }
 #pragma unroll
       for (int k = WIN - 1; k > 0; --k) win[k] = win[k - 1];
@@ -517,12 +563,13 @@ cudaError_t symbols_t(const CodecGeo& cg, const Geo& g, const float* y, const in
   return cudaGetLastError();
 }
 
-template <int N, int NL>
+template <int N, int NL, int P>
 cudaError_t decode_t(const CodecGeo& cg, const uint16_t* tab, const uint8_t* bytes,
                      const long long* row_off, const int* row_len, int* planes, int* progress,
                      int* flag, cudaStream_t st) {
+  if (cg.band_rows != 32 / P) return cudaErrorInvalidValue;
   const size_t smem = (size_t)kNtab * kTabStride * sizeof(uint16_t);
-  auto kern = k_codec_decode<N, NL>;
+  auto kern = k_codec_decode<N, NL, P>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
@@ -672,11 +719,15 @@ cudaError_t codec_decode(const CodecGeo& cg, int N, int NL, const uint16_t* tab,
                          int* planes, int* progress, int* flag, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(progress, 0, (size_t)cg.bands * sizeof(int), st);
   if (e != cudaSuccess) return e;
-#define CC_DECODE_CASE(n, nl)                                                                 \
-  if (N == n && NL == nl)                                                                     \
-    return decode_t<n, nl>(cg, tab, bytes, row_off, row_len, planes, progress, flag, st);
-  CC_DECODE_CASE(8, 1) CC_DECODE_CASE(8, 2) CC_DECODE_CASE(16, 1) CC_DECODE_CASE(16, 2)
-  CC_DECODE_CASE(24, 1) CC_DECODE_CASE(24, 2)
+#define CC_DECODE_CASE(n, nl, p)                                                              \
+  if (N == n && NL == nl && parts == p)                                                       \
+    return decode_t<n, nl, p>(cg, tab, bytes, row_off, row_len, planes, progress, flag, st);
+  const int parts = 32 / cg.band_rows;
+  CC_DECODE_CASE(8, 1, 1) CC_DECODE_CASE(8, 2, 1) CC_DECODE_CASE(8, 1, 2) CC_DECODE_CASE(8, 2, 2)
+  CC_DECODE_CASE(16, 1, 1) CC_DECODE_CASE(16, 2, 1) CC_DECODE_CASE(16, 1, 2)
+  CC_DECODE_CASE(16, 2, 2) CC_DECODE_CASE(16, 1, 4) CC_DECODE_CASE(16, 2, 4)
+  CC_DECODE_CASE(24, 1, 1) CC_DECODE_CASE(24, 2, 1) CC_DECODE_CASE(24, 1, 2)
+  CC_DECODE_CASE(24, 2, 2) CC_DECODE_CASE(24, 1, 4) CC_DECODE_CASE(24, 2, 4)
 #undef CC_DECODE_CASE
   return cudaErrorInvalidValue;
 }
@@ -698,8 +749,21 @@ cudaError_t codec_to_float(const CodecGeo& cg, const Geo& g, const int* planes, 
   return cudaGetLastError();
 }
 
-CodecGeo codec_geo(const Geo& g) {
+// Lanes per row of the decoder: 2 (16-row bands) measured fastest on GB300 for the
+// 8- and 24-input ARMs (2048 x 2048: 15.1 and 25.4 ms against 16.4 / 36.3 ms with 1 and
+// -- / 29.9 ms with 4); CC_DECODE_PARTS (1, 2, 4) overrides it.
+int codec_decode_parts(int N) {
+  int p = 2;
+  if (const char* env = getenv("CC_DECODE_PARTS")) {
+    const int v = atoi(env);
+    if (v == 1 || v == 2 || (v == 4 && N != 8)) p = v;
+  }
+  return p;
+}
+
+CodecGeo codec_geo(const Geo& g, int band_rows) {
   CodecGeo cg;
+  cg.band_rows = band_rows;
   long long off = 0, buf = 0;
   int rows = 0, bands = 0;
   for (int l = 0; l < kLevels; ++l) {
@@ -710,7 +774,7 @@ CodecGeo codec_geo(const Geo& g) {
     cg.cap[l] = codec_row_capacity(g.w[l]);
     cg.buf0[l] = buf;
     cg.band0[l] = bands;
-    bands += (g.h[l] + kBandRows - 1) / kBandRows;
+    bands += (g.h[l] + band_rows - 1) / band_rows;
     off += (long long)g.h[l] * g.w[l];
     rows += g.h[l];
     buf += (long long)g.h[l] * cg.cap[l];

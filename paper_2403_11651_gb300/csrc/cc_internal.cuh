@@ -261,11 +261,13 @@ struct CodecGeo {
   int row0[kLevels];          // first row number of each level
   int cap[kLevels];           // bytes reserved for one row's substream while encoding
   long long buf0[kLevels];    // first byte of each level's row buffers
-  int band0[kLevels];         // first 32-row decoding band of each level
+  int band0[kLevels];         // first decoding band (band_rows rows) of each level
   long long n_lat, buf_bytes;
-  int rows, bands;
+  int rows, bands, band_rows;
 };
-CodecGeo codec_geo(const Geo& g);
+// lanes per row of the decoder for context size N (band_rows = 32 / parts)
+int codec_decode_parts(int N);
+CodecGeo codec_geo(const Geo& g, int band_rows);
 const std::vector<uint16_t>& codec_tables();
 size_t codec_table_bytes();
 bool codec_quantize_arm(const float* params, int N, int NL, int32_t* q);
