@@ -253,9 +253,9 @@ int cc_rate_bits_noalloc(const cc_config* cfg, const float* yhat_flat, int H, in
  * cc_decode_bitstream: decodes a bitstream in host memory on the current device and
  *   the given stream (cudaStream_t or NULL): the latent rows as a wavefront (row r
  *   decodes position x at step x + lag r, lag 3 for N = 8 and 4 for N = 16 or 24), one
- *   warp per band of 32 rows, every band waiting (bounded; CC_ETIMEOUT if it gives up)
- *   on the band above it, all levels at once in one cooperative launch; then the
- *   float32 upsampling and synthesis.  Optional outputs (host or device): rgb_out_hwc (H x W x 3 floats, not
+ *   warp per band of 16 rows (two lanes per row), every band waiting (bounded;
+ *   CC_ETIMEOUT if it gives up) on the band above it, all levels at once in one
+ *   cooperative launch; then the float32 upsampling and synthesis.  Optional outputs (host or device): rgb_out_hwc (H x W x 3 floats, not
  *   clamped, as cc_decode), latents_out (cc_latent_count int32, flat latent order),
  *   latent_ms (device time of the latent decoding).  It holds a temporary context (the
  *   memory of cc_init_image) for the call.  Synchronises. */
