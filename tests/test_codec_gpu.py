@@ -201,3 +201,21 @@ def test_full_size_2048_c2():
     x = syn.synthetic_image(H, W, 3).astype(np.float64) / 255.0
     assert abs(_psnr(rgb, x) - _psnr(ref, x)) < 0.01
     print(f"2048x2048 c2: {len(bs)} bytes, latent decode {ms:.1f} ms")
+
+
+def test_decode_on_a_caller_stream():
+    """cc_decode_bitstream on a caller's stream (and into device buffers) gives the same
+    latents and image as on the default stream."""
+    d = config_dict("t1079")
+    H, W = 40, 72
+    named = _decoder_params(d, 8)
+    y = _latents(H, W, 8, extreme=False)
+    bs = C.write_bitstream(H, W, oracle_arch(d), named, y)
+    rgb0, lat0, _ = cc.cc_decode_bitstream(bs)
+    st = torch.cuda.Stream()
+    rgb1 = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
+    lat1 = torch.empty(lat0.shape, dtype=torch.int32, device="cuda")
+    cc.cc_decode_bitstream(bs, rgb_out=rgb1, latents_out=lat1, stream=st)
+    st.synchronize()
+    np.testing.assert_array_equal(lat1.cpu().numpy(), lat0)
+    np.testing.assert_array_equal(rgb1.cpu().numpy(), rgb0)

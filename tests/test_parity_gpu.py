@@ -344,3 +344,39 @@ def test_set_image_replaces_the_image():
     finally:
         for c in (ca, cb, cc2):
             cc.cc_free(c)
+
+
+def test_autograd_function_matches_oracle():
+    """CoolChicIter: the loss of eq. (1) and, through loss.backward(), the hand-written
+    gradients -- against the FP64 oracle; a few torch.optim.Adam steps through it lower
+    the loss."""
+    from paper_2403_11651_gb300.autograd import coolchic_loss
+    H, W = 40, 56
+    p = Pair(config_dict("c1", lam=1e-2), H, W, seed=3, random_state=True)
+    try:
+        u = syn.uniform_noise(H, W, 5)
+        noise = torch.from_numpy(np.concatenate([a.ravel() for a in u])).cuda()
+        y = torch.from_numpy(cc.cc_get_latents(p.ctx, p.n_lat)).cuda().requires_grad_()
+        prm = torch.from_numpy(cc.cc_get_params(p.ctx, p.n_params)).cuda().requires_grad_()
+        loss = coolchic_loss(p.ctx, p.cfg, y, prm, noise, hard=0)
+        loss.backward()
+        ry, rp, rD, rR = p.oracle_grads(u)
+        assert _rel(float(loss.detach()), rD + 1e-2 * rR) < 1e-5
+        gy = cc.split_latents(y.grad.cpu().numpy(), H, W)
+        for l in range(7):
+            assert_group_close(gy[l], ry[l], 1e-4, f"dL/dy level {l}")
+        gp = cc.unflatten_params(prm.grad.cpu().numpy(), p.cfg)
+        for k in rp:
+            assert_group_close(gp[k], rp[k], 1e-4, k)
+        # optimisation through the Function (PyTorch's Adam)
+        opt = torch.optim.Adam([y, prm], lr=1e-2)
+        first = None
+        for _ in range(30):
+            opt.zero_grad()
+            l = coolchic_loss(p.ctx, p.cfg, y, prm, noise, hard=0)
+            l.backward()
+            opt.step()
+            first = float(l.detach()) if first is None else first
+        assert float(coolchic_loss(p.ctx, p.cfg, y, prm, noise, hard=0).detach()) < 0.9 * first
+    finally:
+        p.close()
