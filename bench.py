@@ -316,14 +316,25 @@ def run_ours(a, cfgd):
     cc.cc_free(ctx2)
     for _ in range(2):
         t0 = time.perf_counter()
-        _, lat, lat_ms = cc.cc_decode_bitstream(bs)
+        x_dec, lat, lat_ms = cc.cc_decode_bitstream(bs)
         dec_ms = 1e3 * (time.perf_counter() - t0)
+    # the bitstream's parts: parameters (and header) against the latent substreams
+    n_params = cc.cc_param_count(cfg)
+    latent_bytes = len(bs) - 20 - 4 * n_params
+    mse = float(np.mean((np.clip(x_dec, 0.0, 1.0).astype(np.float64)
+                         - rgb.astype(np.float64) / 255.0) ** 2))
     codec = {"workload": f"{H}x{W} after the full schedule", "bytes": len(bs),
              "bpp": 8.0 * len(bs) / (H * W), "model_rate_bpp": final[1],
+             "parameter_bytes": 4 * n_params, "latent_bytes": latent_bytes,
+             "latent_bpp": 8.0 * latent_bytes / (H * W),
+             "psnr_db": 10.0 * math.log10(1.0 / mse),
              "encode_ms": enc_ms, "latent_decode_ms": lat_ms,
              "decode_ms": dec_ms, "latents_exact": bool(np.array_equal(lat, y_int)),
              "note": "decode_ms: whole cc_decode_bitstream call (context set-up, upload, "
-                     "wavefront latent decode, upsampling and synthesis, image to host)"}
+                     "wavefront latent decode, upsampling and synthesis, image to host); "
+                     "latent_bytes: row lengths and substreams; parameter_bytes: raw float32 "
+                     "(the 20-byte header aside); psnr_db of the decoded image clamped to "
+                     "[0, 1]"}
 
     pk, src = peaks()
     props = torch.cuda.get_device_properties(dev)
