@@ -28,6 +28,7 @@
 //           of the last interval with the most trailing zero bits, and trailing zero
 //           bytes are dropped (the decoder reads zeros past the end of a substream).
 //   streams: one substream per latent row, so that rows decode as a wavefront.
+#include <algorithm>
 #include <climits>
 #include <cstdlib>
 #include <cmath>
@@ -432,7 +433,7 @@ template <int N, int NL, int P>
 __global__ void __launch_bounds__(kDecWarps * 32) k_codec_decode(
     CodecGeo cg, const uint16_t* __restrict__ tab, const uint8_t* __restrict__ bytes,
     const long long* __restrict__ row_off, const int* __restrict__ row_len, int* planes,
-    int* progress, int* flag) {
+    int* progress, int* flag, int max_polls, int stall_band) {
   constexpr int LAG = lag_of<N>(), R = reach_of<N>(), WIN = win_of<N>();
   constexpr int NW = NL * (N * N + N) + 2 * N + 2;
   constexpr int kBandRows = 32 / P;         // cg.band_rows, set by the host to match
@@ -472,7 +473,7 @@ __global__ void __launch_bounds__(kDecWarps * 32) k_codec_decode(
           const int need = min(st + 2 * kFill + LAG * (kBandRows - 1), pred_steps);
           int v = 0;
           if (lane == 0) {
-            for (int tries = 0; tries < kMaxPolls; ++tries) {
+            for (int tries = 0; tries < max_polls; ++tries) {
               v = ld_acquire(progress + gb - 1);
               if (v >= need) break;
               __nanosleep(64);
@@ -547,7 +548,7 @@ __global__ void __launch_bounds__(kDecWarps * 32) k_codec_decode(
       win[0] = val;
       if ((st & 3) == 3 || st == nsteps - 1) {
         __syncwarp();
-        if (lane == 0) st_release(progress + gb, st + 1);
+        if (lane == 0 && gb != stall_band) st_release(progress + gb, st + 1);
       }
     }
     if (bad) atomicOr(flag, 4);
@@ -580,8 +581,14 @@ cudaError_t decode_t(const CodecGeo& cg, const uint16_t* tab, const uint8_t* byt
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int want = (cg.bands + kDecWarps - 1) / kDecWarps;
   const int grid = want < sms * per_sm ? want : sms * per_sm;
+  // failure injection for the bounded waits (tests): a band that never publishes its
+  // progress, and a shorter wait bound
+  int max_polls = kMaxPolls, stall_band = -1;
+  if (const char* env = getenv("CC_DECODE_MAX_POLLS")) max_polls = std::max(1, atoi(env));
+  if (const char* env = getenv("CC_DECODE_STALL_BAND")) stall_band = atoi(env);
   void* args[] = {(void*)&cg, (void*)&tab, (void*)&bytes, (void*)&row_off, (void*)&row_len,
-                  (void*)&planes, (void*)&progress, (void*)&flag};
+                  (void*)&planes, (void*)&progress, (void*)&flag, (void*)&max_polls,
+                  (void*)&stall_band};
   return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kDecWarps * 32), args,
                                      smem, st);
 }

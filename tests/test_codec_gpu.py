@@ -219,3 +219,23 @@ def test_decode_on_a_caller_stream():
     st.synchronize()
     np.testing.assert_array_equal(lat1.cpu().numpy(), lat0)
     np.testing.assert_array_equal(rgb1.cpu().numpy(), rgb0)
+
+
+def test_decode_band_wait_gives_up(monkeypatch):
+    """Failure detection without a fault: one decoding band never publishes its progress
+    (injected on the host); the bands below it give up after their bounded wait, the call
+    returns CC_ETIMEOUT, and the next decode on the same device succeeds."""
+    d = config_dict("c1")
+    H, W = 80, 64                 # level 0: 5 bands of 16 rows
+    named = _decoder_params(d, 9)
+    y = _latents(H, W, 9, extreme=False)
+    bs = C.write_bitstream(H, W, oracle_arch(d), named, y)
+    monkeypatch.setenv("CC_DECODE_STALL_BAND", "0")
+    monkeypatch.setenv("CC_DECODE_MAX_POLLS", "2000")
+    with pytest.raises(cc.CCError) as e:
+        cc.cc_decode_bitstream(bs)
+    assert e.value.code == cc.CC_ETIMEOUT
+    monkeypatch.delenv("CC_DECODE_STALL_BAND")
+    monkeypatch.delenv("CC_DECODE_MAX_POLLS")
+    _, lat, _ = cc.cc_decode_bitstream(bs, want_rgb=False)
+    np.testing.assert_array_equal(lat.astype(np.int64), np.concatenate([a.ravel() for a in y]))
