@@ -132,3 +132,19 @@ def test_bitstream_header_parsed_on_host(lib, arch, H, W):
     wrong_arch[13] = 7          # N = 7 is not a supported context size
     with pytest.raises(cc.CCError):
         cc.cc_bitstream_info(bytes(wrong_arch))
+
+
+@pytest.mark.parametrize("arch,H,W", [("c1", 1, 1), ("c2", 33, 47), ("t300", 64, 9)])
+def test_bitstream_bound_holds(lib, arch, H, W):
+    """The binding's output-buffer bound covers bitstreams of extreme latents (escapes of
+    2^20 everywhere)."""
+    from oracle import codec as C
+    from .helpers import oracle_arch
+    d = config_dict(arch)
+    a = oracle_arch(d)
+    rng = np.random.default_rng(1)
+    named = {n: rng.normal(0, 0.1, s).astype(np.float32) for n, s in oc.param_shapes(a)}
+    y = [np.where(rng.random(s) < 0.5, C.Y_LIM, -C.Y_LIM).astype(np.int64)
+         for s in oc.level_shapes(H, W)]
+    bs = C.write_bitstream(H, W, a, named, y)
+    assert len(bs) <= cc.bitstream_bound(cc.make_config(d), H, W)
