@@ -293,7 +293,6 @@ __global__ void __launch_bounds__(256) k_codec_pack(CodecGeo cg, const uint8_t* 
 constexpr int kDecWarps = 4;                 // warps per block: one per scheduler
 constexpr int kMaxPolls = 1 << 22;           // bounded wait on the predecessor band
 constexpr int kRing = 64;                    // columns of the predecessor rows kept in smem
-constexpr int kFill = 8;                     // steps between ring refills
 
 // The causal offsets (dy, dx) of N = 8, 16, 24 in raster order (the N nearest causal
 // neighbours, ties by smaller |dy| then smaller dx) as compile-time tables: the decoder
@@ -429,6 +428,8 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
+constexpr int kFill = 8;                     // steps between ring refills (16: slower)
+
 template <int N, int NL, int P>
 __global__ void __launch_bounds__(kDecWarps * 32) k_codec_decode(
     CodecGeo cg, const uint16_t* __restrict__ tab, const uint8_t* __restrict__ bytes,
@@ -515,7 +516,10 @@ __global__ void __launch_bounds__(kDecWarps * 32) k_codec_decode(
         ctx[j] = (r + dy >= 0 && x + dx >= 0 && x + dx < w) ? v : 0;
       }
       int mu, s;
-      arm_fixed_split<N, NL, P>(ctx, s_w, part, lane, mu, s);   // all lanes: shuffles inside
+      if constexpr (P == 1)
+        arm_fixed<N, NL>(ctx, mu, s);                          // weights as bank operands
+      else
+        arm_fixed_split<N, NL, P>(ctx, s_w, part, lane, mu, s);   // shuffles inside
       int val = 0;
       if (ri < nr && x >= 0 && x < w) {
         if (x == 0) dec.init(bytes + row_off[cg.row0[l] + r], row_len[cg.row0[l] + r]);
@@ -731,10 +735,8 @@ cudaError_t codec_decode(const CodecGeo& cg, int N, int NL, const uint16_t* tab,
     return decode_t<n, nl, p>(cg, tab, bytes, row_off, row_len, planes, progress, flag, st);
   const int parts = 32 / cg.band_rows;
   CC_DECODE_CASE(8, 1, 1) CC_DECODE_CASE(8, 2, 1) CC_DECODE_CASE(8, 1, 2) CC_DECODE_CASE(8, 2, 2)
-  CC_DECODE_CASE(16, 1, 1) CC_DECODE_CASE(16, 2, 1) CC_DECODE_CASE(16, 1, 2)
-  CC_DECODE_CASE(16, 2, 2) CC_DECODE_CASE(16, 1, 4) CC_DECODE_CASE(16, 2, 4)
-  CC_DECODE_CASE(24, 1, 1) CC_DECODE_CASE(24, 2, 1) CC_DECODE_CASE(24, 1, 2)
-  CC_DECODE_CASE(24, 2, 2) CC_DECODE_CASE(24, 1, 4) CC_DECODE_CASE(24, 2, 4)
+  CC_DECODE_CASE(16, 1, 2) CC_DECODE_CASE(16, 2, 2)
+  CC_DECODE_CASE(24, 1, 2) CC_DECODE_CASE(24, 2, 2) CC_DECODE_CASE(24, 1, 1) CC_DECODE_CASE(24, 2, 1)
 #undef CC_DECODE_CASE
   return cudaErrorInvalidValue;
 }
@@ -756,14 +758,16 @@ cudaError_t codec_to_float(const CodecGeo& cg, const Geo& g, const int* planes, 
   return cudaGetLastError();
 }
 
-// Lanes per row of the decoder: 2 (16-row bands) measured fastest on GB300 for the
-// 8- and 24-input ARMs (2048 x 2048: 15.1 and 25.4 ms against 16.4 / 36.3 ms with 1 and
-// -- / 29.9 ms with 4); CC_DECODE_PARTS (1, 2, 4) overrides it.
+// Lanes per row of the decoder, measured on GB300 at 2048 x 2048 (latent decode): the
+// 8-input ARM is fastest with one lane per row and its weights as constant-bank operands
+// (13.3 ms; 14.1 with two lanes), the 16- and 24-input ARMs with two lanes (24.9 ms for
+// N = 24; 37.2 with one, 29.9 with four).  CC_DECODE_PARTS (1 or 2; 1 only for N = 8, 24)
+// overrides it.
 int codec_decode_parts(int N) {
-  int p = 2;
+  int p = N == 8 ? 1 : 2;
   if (const char* env = getenv("CC_DECODE_PARTS")) {
     const int v = atoi(env);
-    if (v == 1 || v == 2 || (v == 4 && N != 8)) p = v;
+    if (v == 2 || (v == 1 && N != 16)) p = v;
   }
   return p;
 }
