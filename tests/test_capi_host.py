@@ -148,3 +148,17 @@ def test_bitstream_bound_holds(lib, arch, H, W):
          for s in oc.level_shapes(H, W)]
     bs = C.write_bitstream(H, W, a, named, y)
     assert len(bs) <= cc.bitstream_bound(cc.make_config(d), H, W)
+
+
+def test_library_copies_load_independently(lib):
+    """The batch runner's lanes are separately loaded copies of the library, each its own
+    module (and so its own constant banks); each answers through the C ABI."""
+    import ctypes
+    from paper_2403_11651_gb300.batch import library_instances
+    libs = library_instances(3)
+    assert len({l._handle for l in libs}) == 3
+    cfg = cc.make_config(config_dict("c2"))
+    for l in libs:
+        n = ctypes.c_int()
+        assert l.cc_param_count(ctypes.byref(cfg), ctypes.byref(n)) == 0
+        assert n.value == cc.cc_param_count(cfg)
