@@ -22,7 +22,9 @@
  *   - all GPU work of a context is issued on the stream given to cc_init_image;
  *   - the contexts of one device share its constant-memory weight banks (every pass loads
  *     its own weights first): passes of two contexts must not overlap in time, so issue
- *     them on one stream or synchronise between them;
+ *     them on one stream or synchronise between them.  The banks belong to the loaded
+ *     library: contexts created through separately loaded copies of it have their own
+ *     and may run concurrently;
  *   - the images are 8-bit RGB, row-major, channels last (H x W x 3); the library uses
  *     x = v / 255 in float32.
  *
