@@ -266,6 +266,42 @@ int cc_bitstream_info(const uint8_t* bs, size_t nbytes, cc_config* cfg, int* H, 
 int cc_decode_bitstream(const uint8_t* bs, size_t nbytes, void* cuda_stream,
                         float* rgb_out_hwc, int32_t* latents_out, float* latent_ms);
 
+/* Warm-start predictor.  The paper's encoder starts every image from zero latents; its
+ * Sec. IV-B predicts the latents with an analysis network (the non-overfitted variant)
+ * and Sec. V proposes fine-tuning such a prediction per image.  This small predictor
+ * maps an image to latent levels 0 .. 4: four 3x3 stride-2 convolutions with 32
+ * channels and ReLU (zero padding 1) whose outputs feed 1x1 convolutions giving levels
+ * 1 .. 4, and a 3x3 stride-1 convolution of the image giving level 0; levels 5 and 6 are
+ * 0.  It is trained on latents the encoder reached (loss: the sum over levels 0 .. 4 of
+ * each level's mean squared error), with Adam (beta 0.9 / 0.999, eps 1e-8,
+ * bias-corrected).  FP32.  Every cc_warm_* call runs on the stream given at creation; one
+ * predictor is not used from two threads at once.
+ * Flat parameter order: c1 (W 32 x 3 x 3 x 3, b 32), c2 .. c4 (W 32 x 32 x 3 x 3, b 32),
+ * heads 1 .. 4 (W 32, b 1), head 0 (W 3 x 3 x 3, b 1).
+ * cc_warm_create: predictor for H x W images (H, W >= 16); params (host or device,
+ *   cc_warm_param_count floats) copied in; cuda_stream as cc_init_image.
+ * cc_warm_predict: rgb_hwc (host or device, 8-bit H x W x 3) -> latents_out (host or
+ *   device, cc_latent_count floats in flat latent order).  Synchronises.
+ * cc_warm_loss_grad: loss against target latents (host or device, flat latent order;
+ *   levels 5, 6 ignored) and, if grads_out is not NULL, its gradient (host or device,
+ *   flat parameter order).  Synchronises.
+ * cc_warm_train_step: cc_warm_loss_grad then one Adam step with learning rate lr (queued
+ *   on the stream; the next call, or cc_warm_get_params, sees it).
+ * Errors: CC_EINVAL (NULL pointer, H or W outside 16 .. 16384), CC_ENOMEM, CC_ECUDA,
+ *   CC_ENONFINITE (loss not finite: *loss written, no gradient copied out, no Adam
+ *   step taken). */
+typedef struct cc_warm cc_warm;
+int cc_warm_param_count(int* n_params);
+int cc_warm_create(int H, int W, const float* params, void* cuda_stream, cc_warm** out);
+int cc_warm_predict(cc_warm* w, const uint8_t* rgb_hwc, float* latents_out);
+int cc_warm_loss_grad(cc_warm* w, const uint8_t* rgb_hwc, const float* target_latents,
+                      double* loss, float* grads_out);
+int cc_warm_train_step(cc_warm* w, const uint8_t* rgb_hwc, const float* target_latents,
+                       float lr, double* loss);
+int cc_warm_get_params(cc_warm* w, float* params);
+int cc_warm_set_params(cc_warm* w, const float* params);
+void cc_warm_free(cc_warm* w);
+
 /* Text of the last error seen by the library in this thread ("" if none). */
 const char* cc_last_cuda_error(void);
 

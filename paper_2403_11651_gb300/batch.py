@@ -121,6 +121,21 @@ class BatchOverfitter:
             _check(lib, code, "cc_get_losses")
         return out
 
+    def latents(self, i: int):
+        """Image i's latents (flat latent order, float32)."""
+        lib = self.libs[self.lane_of[i]]
+        H, W = self.shapes[i]
+        out = np.empty(sum(h * w for h, w in cc.level_shapes(H, W)), np.float32)
+        _check(lib, lib.cc_get_latents(self.ctx[i], cc._ptr(out)), "cc_get_latents")
+        return out
+
+    def params(self, i: int, n_params: int):
+        """Image i's decoder parameters (flat parameter order, float32)."""
+        lib = self.libs[self.lane_of[i]]
+        out = np.empty(n_params, np.float32)
+        _check(lib, lib.cc_get_params(self.ctx[i], cc._ptr(out)), "cc_get_params")
+        return out
+
     def close(self):
         for i, h in enumerate(self.ctx):
             if h:

@@ -25,7 +25,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libcoolchic.so")
 TRACE_LIB = os.path.join(BUILD, "libcoolchic_trace.so")
-SOURCES = ["cc_arm.cu", "cc_syn.cu", "cc_iter.cu", "cc_capi.cu", "cc_noalloc.cu", "cc_codec.cu"]
+SOURCES = ["cc_arm.cu", "cc_syn.cu", "cc_iter.cu", "cc_capi.cu", "cc_noalloc.cu", "cc_codec.cu", "cc_warm.cu"]
 HEADERS = [os.path.join(CSRC, "cc_internal.cuh"), os.path.join(CSRC, "cc_laplace.cuh"),
            os.path.join(ROOT, "include", "coolchic.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -77,6 +77,14 @@ def _declare(lib):
         "cc_write_bitstream": (c_int, [P, P, c_size_t, POINTER(c_size_t)]),
         "cc_bitstream_info": (c_int, [P, c_size_t, P, POINTER(c_int), POINTER(c_int)]),
         "cc_decode_bitstream": (c_int, [P, c_size_t, P, P, P, POINTER(ctypes.c_float)]),
+        "cc_warm_param_count": (c_int, [POINTER(c_int)]),
+        "cc_warm_create": (c_int, [c_int, c_int, P, P, POINTER(c_void_p)]),
+        "cc_warm_predict": (c_int, [P, P, P]),
+        "cc_warm_loss_grad": (c_int, [P, P, P, POINTER(c_double), P]),
+        "cc_warm_train_step": (c_int, [P, P, P, ctypes.c_float, POINTER(c_double)]),
+        "cc_warm_get_params": (c_int, [P, P]),
+        "cc_warm_set_params": (c_int, [P, P]),
+        "cc_warm_free": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -427,6 +435,62 @@ def cc_decode_bitstream(bs: bytes, rgb_out=None, latents_out=None, stream=None, 
     return (rgb_out if want_rgb else None), (latents_out if want_latents else None), ms.value
 
 
+WARM_LAYOUT = ([("c1.w", (32, 3, 3, 3)), ("c1.b", (32,))]
+               + [x for i in (2, 3, 4) for x in ((f"c{i}.w", (32, 32, 3, 3)), (f"c{i}.b", (32,)))]
+               + [x for i in (1, 2, 3, 4) for x in ((f"h{i}.w", (1, 32, 1, 1)), (f"h{i}.b", (1,)))]
+               + [("h0.w", (1, 3, 3, 3)), ("h0.b", (1,))])
+
+
+def cc_warm_param_count() -> int:
+    n = c_int()
+    _check(_lib().cc_warm_param_count(ctypes.byref(n)), "cc_warm_param_count")
+    return n.value
+
+
+def cc_warm_create(H: int, W: int, params, stream=None):
+    w = c_void_p()
+    _check(_lib().cc_warm_create(H, W, _ptr(params), _stream_handle(stream), ctypes.byref(w)),
+           "cc_warm_create")
+    return w
+
+
+def cc_warm_predict(w, rgb_hwc, n_latents: int, out=None):
+    if out is None:
+        out = np.empty(n_latents, np.float32)
+    _check(_lib().cc_warm_predict(w, _ptr(rgb_hwc), _ptr(out)), "cc_warm_predict")
+    return out
+
+
+def cc_warm_loss_grad(w, rgb_hwc, target_latents, grads_out=None) -> float:
+    loss = c_double()
+    _check(_lib().cc_warm_loss_grad(w, _ptr(rgb_hwc), _ptr(target_latents), ctypes.byref(loss),
+                                    _ptr(grads_out)), "cc_warm_loss_grad")
+    return loss.value
+
+
+def cc_warm_train_step(w, rgb_hwc, target_latents, lr: float) -> float:
+    loss = c_double()
+    _check(_lib().cc_warm_train_step(w, _ptr(rgb_hwc), _ptr(target_latents), float(lr),
+                                     ctypes.byref(loss)), "cc_warm_train_step")
+    return loss.value
+
+
+def cc_warm_get_params(w, out=None):
+    if out is None:
+        out = np.empty(cc_warm_param_count(), np.float32)
+    _check(_lib().cc_warm_get_params(w, _ptr(out)), "cc_warm_get_params")
+    return out
+
+
+def cc_warm_set_params(w, params):
+    _check(_lib().cc_warm_set_params(w, _ptr(params)), "cc_warm_set_params")
+
+
+def cc_warm_free(w):
+    if w:
+        _lib().cc_warm_free(w)
+
+
 def cc_free(ctx):
     if ctx:
         _lib().cc_free(ctx)
@@ -443,4 +507,7 @@ EXPORTED = ["cc_param_count", "cc_latent_count", "cc_workspace_size", "cc_init_i
             "cc_set_latents", "cc_get_latents", "cc_set_params", "cc_get_params",
             "cc_profile_phases", "cc_graph_kernel_count", "cc_arm_kernel_ms", "cc_rate_bits_noalloc",
             "cc_get_state", "cc_set_state", "cc_write_bitstream", "cc_bitstream_info",
-            "cc_decode_bitstream", "cc_free", "cc_strerror", "cc_last_cuda_error"]
+            "cc_decode_bitstream", "cc_warm_param_count", "cc_warm_create", "cc_warm_predict",
+            "cc_warm_loss_grad", "cc_warm_train_step", "cc_warm_get_params",
+            "cc_warm_set_params", "cc_warm_free", "cc_free", "cc_strerror",
+            "cc_last_cuda_error"]

@@ -32,6 +32,7 @@ __all__ = [
     "initial_parameters",
     "uniform_noise",
     "synthetic_latents",
+    "warm_initial_parameters",
     "keys_cubic",
 ]
 
@@ -182,3 +183,22 @@ def synthetic_latents(H: int, W: int, seed: int, levels: int = 7):
     rng = np.random.Generator(np.random.PCG64(seed ^ 0x5A5A5A))
     return [np.rint(rng.laplace(0.0, 0.4 + 0.6 * l, size=s)).astype(np.int32)
             for l, s in enumerate(level_shapes(H, W, levels))]
+
+
+def warm_initial_parameters(seed: int) -> np.ndarray:
+    """Flat float32 parameters of the warm-start predictor: weights uniform in
+    +-1/sqrt(fan_in), biases 0 (layer order of include/coolchic.h)."""
+    rng = np.random.Generator(np.random.PCG64(seed ^ 0x3C3C3C))
+    shapes = ([((32, 3, 3, 3), 27), ((32,), 0)]
+              + [s for _ in range(3) for s in (((32, 32, 3, 3), 288), ((32,), 0))]
+              + [s for _ in range(4) for s in (((1, 32, 1, 1), 32), ((1,), 0))]
+              + [((1, 3, 3, 3), 27), ((1,), 0)])
+    out = []
+    for shape, fan_in in shapes:
+        n = int(np.prod(shape))
+        if fan_in:
+            b = 1.0 / math.sqrt(fan_in)
+            out.append(rng.uniform(-b, b, n).astype(np.float32))
+        else:
+            out.append(np.zeros(n, np.float32))
+    return np.concatenate(out)

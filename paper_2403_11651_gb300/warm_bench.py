@@ -1,0 +1,192 @@
+"""Learned warm start against plain overfitting, printed as one JSON line.
+
+    python -m paper_2403_11651_gb300.warm_bench [--train 48] [--test 8] [--iters 1000]
+        [--size 256] [--test-size H W] [--ablate K] [--max-data-s S]
+
+1. This project's encoder overfits --train synthetic --size x --size images (2300-MAC
+   decoder, --iters iterations; --chunk at a time through the batch runner, stopping
+   early once --max-data-s seconds have been spent): the pairs (image, latents reached)
+   and the decoders reached.
+2. The warm-start predictor (cc_warm_*) is trained on those pairs (Adam, --epochs).
+3. On --test held-out images of --test-size (default: the training size; a second
+   predictor of that size takes the trained parameters): the plain method (latents 0,
+   the seeded initial decoder) and the warm start (predicted latents, the mean of the
+   trained decoders) run the same schedule (--iters iterations, the last 20 %
+   straight-through); the hard RD cost is read every --every iterations.  Reported: the
+   warm start's iterations and seconds to reach the plain run's final RD cost within 1 %,
+   and both final RD costs; on the first --ablate held-out images also the mean decoder
+   alone and the predicted latents alone.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from .batch import BatchOverfitter   # first: sets the hardware queue count before CUDA starts
+from . import coolchic as cc
+from . import synthetic as syn
+
+
+def config(iters: int):
+    d = dict(cc.load_config("c2"))
+    d["total_iters"] = iters
+    return d
+
+
+def run_schedule(cfg, rgb, init_params, latents, iters, every):
+    """Hard RD cost every `every` iterations (first entry: before any) and seconds."""
+    H, W = rgb.shape[:2]
+    ctx = cc.cc_init_image(cfg, rgb, H, W, init_params)
+    try:
+        if latents is not None:
+            cc.cc_set_latents(ctx, latents)
+        costs = [cc.cc_rd_cost(ctx, True)[2]]
+        spent = 0.0
+        done = 0
+        while done < iters:
+            n = min(every, iters - done)
+            t0 = time.perf_counter()
+            cc.cc_encode_iters(ctx, n)
+            cc.cc_iteration(ctx)
+            c = cc.cc_rd_cost(ctx, True)[2]      # synchronises
+            spent += time.perf_counter() - t0
+            costs.append(c)
+            done += n
+        return np.array(costs), spent
+    finally:
+        cc.cc_free(ctx)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=48)
+    ap.add_argument("--test", type=int, default=8)
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--iters", type=int, default=1000)
+    ap.add_argument("--every", type=int, default=25)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--test-size", type=int, nargs=2, default=None, metavar=("H", "W"))
+    ap.add_argument("--ablate", type=int, default=None)
+    ap.add_argument("--chunk", type=int, default=64)
+    ap.add_argument("--max-data-s", type=float, default=float("inf"))
+    a = ap.parse_args(argv)
+    S = a.size
+    TH, TW = a.test_size if a.test_size else (S, S)
+    n_ablate = a.test if a.ablate is None else min(a.ablate, a.test)
+    d = config(a.iters)
+    n_params = cc.cc_param_count(cc.make_config(d))
+    init = {k: cc.flatten_params(syn.initial_parameters(syn.ArchSizes.from_config(d), k),
+                                 cc.make_config(d))
+            for k in range(a.train + a.test)}
+
+    # 1. training pairs from this project's own encoder
+    t0 = time.perf_counter()
+    images, lat, dec_sum = [], [], np.zeros(n_params, np.float64)
+    for c0 in range(0, a.train, a.chunk):
+        if time.perf_counter() - t0 > a.max_data_s:
+            break
+        items = [(syn.synthetic_image(S, S, 1000 + k), d, init[k], k)
+                 for k in range(c0, min(a.train, c0 + a.chunk))]
+        b = BatchOverfitter(items, lanes=8)
+        try:
+            b.run(a.iters)
+            lat += [b.latents(i) for i in range(len(items))]
+            for i in range(len(items)):
+                dec_sum += b.params(i, n_params)
+        finally:
+            b.close()
+        images += [it[0] for it in items]
+    n_train = len(images)
+    dec = (dec_sum / n_train).astype(np.float32)
+    t_data = time.perf_counter() - t0
+
+    # 2. the predictor
+    w = cc.cc_warm_create(S, S, syn.warm_initial_parameters(0))
+    wt = None
+    try:
+        t0 = time.perf_counter()
+        losses = []
+        order = np.random.default_rng(0)
+        for ep in range(a.epochs):
+            tot = 0.0
+            for i in order.permutation(n_train):
+                tot += cc.cc_warm_train_step(w, images[i], lat[i], a.lr)
+            losses.append(tot / n_train)
+        t_train = time.perf_counter() - t0
+        if (TH, TW) == (S, S):
+            wt = w
+        else:
+            wt = cc.cc_warm_create(TH, TW, cc.cc_warm_get_params(w))
+
+        # 3. held-out images: plain against warm start
+        n_lat = sum(h * w_ for h, w_ in cc.level_shapes(TH, TW))
+        res = []
+        for j, k in enumerate(range(a.train, a.train + a.test)):
+            rgb = syn.synthetic_image(TH, TW, 1000 + k)
+            cfg = cc.make_config(d, seed=k)
+            t0 = time.perf_counter()
+            y0 = cc.cc_warm_predict(wt, rgb, n_lat)
+            t_pred = time.perf_counter() - t0
+            plain, s_plain = run_schedule(cfg, rgb, init[k], None, a.iters, a.every)
+            warm, s_warm = run_schedule(cfg, rgb, dec, y0, a.iters, a.every)
+            # ablations: the mean decoder alone (latents 0), the predicted latents alone
+            if j < n_ablate:
+                dec_only, _ = run_schedule(cfg, rgb, dec, None, a.iters, a.every)
+                lat_only, _ = run_schedule(cfg, rgb, init[k], y0, a.iters, a.every)
+            target = plain[-1] * 1.01
+
+            def first_hit(curve):
+                hit = np.nonzero(curve <= target)[0]
+                return int(hit[0]) * a.every if hit.size else None
+            it_hit = first_hit(warm)
+            res.append({"plain_final": float(plain[-1]), "warm_final": float(warm[-1]),
+                        "plain_start": float(plain[0]), "warm_start": float(warm[0]),
+                        "warm_iters_to_plain_final": it_hit,
+                        "decoder_only_iters_to_plain_final":
+                            first_hit(dec_only) if j < n_ablate else "not run",
+                        "latents_only_iters_to_plain_final":
+                            first_hit(lat_only) if j < n_ablate else "not run",
+                        "warm_s_to_plain_final": (t_pred + s_warm * it_hit / a.iters)
+                        if it_hit is not None else None,
+                        "plain_s": s_plain})
+    finally:
+        if wt is not None and wt is not w:
+            cc.cc_warm_free(wt)
+        cc.cc_warm_free(w)
+    hits = [r["warm_iters_to_plain_final"] for r in res]
+
+    def mean_hits(key):
+        h = [r[key] for r in res if r[key] != "not run"]
+        return (float(np.mean([x if x is not None else a.iters for x in h])),
+                sum(x is not None for x in h))
+    print(json.dumps({
+        "workload": f"{n_train} training synthetic {S}x{S} / {a.test} held-out synthetic "
+                    f"{TH}x{TW} images, 2300-MAC decoder, {a.iters} iterations (last 20 % "
+                    f"straight-through); ablations on {n_ablate} held-out images",
+        "train_requested": a.train, "epochs": a.epochs, "lr": a.lr,
+        "data_s": t_data, "predictor_train_s": t_train,
+        "predictor_loss_first_last_epoch": [losses[0], losses[-1]],
+        "reached": sum(h is not None for h in hits), "of": len(hits),
+        "mean_iters_to_plain_final": float(np.mean([h for h in hits if h is not None]))
+        if any(h is not None for h in hits) else None,
+        "ablation_mean_iters_reached": {
+            "predicted_latents_and_mean_decoder": mean_hits("warm_iters_to_plain_final"),
+            "mean_decoder_only": mean_hits("decoder_only_iters_to_plain_final"),
+            "predicted_latents_only": mean_hits("latents_only_iters_to_plain_final")},
+        "mean_plain_s": float(np.mean([r["plain_s"] for r in res])),
+        "mean_warm_s_to_plain_final_reached": float(np.mean(
+            [r["warm_s_to_plain_final"] for r in res if r["warm_s_to_plain_final"] is not None]))
+        if any(r["warm_s_to_plain_final"] is not None for r in res) else None,
+        "mean_final_cost_ratio_warm_over_plain": float(np.mean(
+            [r["warm_final"] / r["plain_final"] for r in res])),
+        "mean_start_cost_ratio_warm_over_plain": float(np.mean(
+            [r["warm_start"] / r["plain_start"] for r in res])),
+        "per_image": res}))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,83 @@
+"""Warm-start predictor on the GPU against the FP64 oracle (oracle/warm.py): forward,
+loss and every parameter gradient; Adam steps lower the loss."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import warm as ow
+from paper_2403_11651_gb300 import coolchic as cc
+from paper_2403_11651_gb300 import synthetic as syn
+
+from .helpers import assert_group_close
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle(flat):
+    P, k = {}, 0
+    for name, shape in ow.param_shapes():
+        n = int(np.prod(shape))
+        P[name] = torch.tensor(flat[k:k + n].astype(np.float64).reshape(shape),
+                               requires_grad=True)
+        k += n
+    return P
+
+
+@pytest.mark.parametrize("H,W,seed", [(64, 96, 0), (37, 53, 1), (256, 256, 2)])
+def test_forward_loss_gradients(H, W, seed):
+    flat = syn.warm_initial_parameters(seed)
+    rgb = syn.synthetic_image(H, W, seed)
+    shapes = [(-(-H // (1 << l)), -(-W // (1 << l))) for l in range(7)]
+    rng = np.random.default_rng(seed)
+    target = [rng.normal(0, 1.0, s).astype(np.float32) for s in shapes]
+    flat_t = np.concatenate([t.ravel() for t in target])
+    n_lat = flat_t.size
+    w = cc.cc_warm_create(H, W, flat)
+    try:
+        pred = cc.cc_warm_predict(w, rgb, n_lat)
+        g = np.empty(flat.size, np.float32)
+        loss = cc.cc_warm_loss_grad(w, rgb, flat_t, g)
+    finally:
+        cc.cc_warm_free(w)
+    x = torch.tensor(rgb.astype(np.float64) / 255.0).permute(2, 0, 1).contiguous()
+    P = _oracle(flat)
+    ref = ow.forward(x, P)
+    k = 0
+    for l, (h, ww) in enumerate(shapes):
+        got = pred[k:k + h * ww].reshape(h, ww)
+        if l < 5:
+            r = ref[l].detach().numpy()
+            assert np.abs(got - r).max() <= 1e-5 * max(1.0, float(np.abs(r).max()))
+        else:
+            assert not got.any()
+        k += h * ww
+    L = ow.loss(x, P, [torch.tensor(t.astype(np.float64)) for t in target[:5]])
+    L.backward()
+    assert abs(loss - float(L)) <= 1e-5 * float(L)
+    k = 0
+    for name, shape in ow.param_shapes():
+        n = int(np.prod(shape))
+        assert_group_close(g[k:k + n].reshape(shape), P[name].grad.numpy(), 1e-4, name)
+        k += n
+
+
+def test_training_lowers_the_loss():
+    H, W = 64, 64
+    rgb = syn.synthetic_image(H, W, 5)
+    shapes = [(-(-H // (1 << l)), -(-W // (1 << l))) for l in range(7)]
+    x = rgb.astype(np.float32).mean(axis=2) / 255.0
+    # a target the predictor can reach: the image's mean intensity, pooled per level
+    target = []
+    for l, (h, w) in enumerate(shapes):
+        f = 1 << l
+        pad = np.pad(x, ((0, h * f - H), (0, w * f - W)), mode="edge")
+        target.append((pad.reshape(h, f, w, f).mean(axis=(1, 3)) * 4.0 - 2.0).astype(np.float32))
+    flat_t = np.concatenate([t.ravel() for t in target])
+    w = cc.cc_warm_create(H, W, syn.warm_initial_parameters(5))
+    try:
+        first = cc.cc_warm_train_step(w, rgb, flat_t, 1e-3)
+        for _ in range(200):
+            last = cc.cc_warm_train_step(w, rgb, flat_t, 1e-3)
+    finally:
+        cc.cc_warm_free(w)
+    assert last < 0.4 * first, (first, last)

@@ -1,0 +1,94 @@
+"""Pins of the warm-start predictor oracle (oracle/warm.py): the convolution definition
+by explicit loops, output sizes, the constant-output case, gradients by central
+differences; and its parameter order against the binding's."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import warm as ow
+from paper_2403_11651_gb300 import coolchic as cc
+from paper_2403_11651_gb300 import synthetic as syn
+
+
+def _params(seed=0, scale=1.0):
+    flat = syn.warm_initial_parameters(seed).astype(np.float64) * scale
+    P, k = {}, 0
+    for name, shape in ow.param_shapes():
+        n = int(np.prod(shape))
+        P[name] = torch.tensor(flat[k:k + n].reshape(shape), dtype=ow.DT, requires_grad=True)
+        k += n
+    return P
+
+
+def test_parameter_order_matches_binding():
+    assert [(n, tuple(s)) for n, s in ow.param_shapes()] == \
+        [(n, tuple(s)) for n, s in cc.WARM_LAYOUT]
+    assert sum(int(np.prod(s)) for _, s in ow.param_shapes()) == syn.warm_initial_parameters(0).size
+
+
+def test_conv_definition_by_loops():
+    """torch's conv2d (stride 2, zero padding 1) equals the written-out sum."""
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(3, 7, 9))
+    w = rng.normal(size=(4, 3, 3, 3))
+    b = rng.normal(size=4)
+    got = torch.nn.functional.conv2d(torch.tensor(x)[None], torch.tensor(w), torch.tensor(b),
+                                     stride=2, padding=1)[0].numpy()
+    Ho, Wo = 4, 5
+    want = np.zeros((4, Ho, Wo))
+    for co in range(4):
+        for y in range(Ho):
+            for xx in range(Wo):
+                acc = b[co]
+                for ci in range(3):
+                    for ky in range(3):
+                        for kx in range(3):
+                            iy, ix = 2 * y + ky - 1, 2 * xx + kx - 1
+                            if 0 <= iy < 7 and 0 <= ix < 9:
+                                acc += w[co, ci, ky, kx] * x[ci, iy, ix]
+                want[co, y, xx] = acc
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("H,W", [(16, 16), (37, 53), (64, 40)])
+def test_output_sizes_are_the_latent_levels(H, W):
+    lv = ow.forward(torch.zeros(3, H, W, dtype=ow.DT), _params())
+    assert [tuple(t.shape) for t in lv] == \
+        [(-(-H // (1 << l)), -(-W // (1 << l))) for l in range(5)]
+
+
+def test_zero_weights_give_the_biases():
+    P = _params()
+    with torch.no_grad():
+        for n, t in P.items():
+            if n.endswith(".w"):
+                t.zero_()
+            else:
+                t.fill_(0.25)
+    lv = ow.forward(torch.rand(3, 32, 48, dtype=ow.DT), P)
+    assert torch.allclose(lv[0], torch.full_like(lv[0], 0.25))
+    for t in lv[1:]:             # ReLU(0.25) through zero 1x1 weights: the head bias
+        assert torch.allclose(t, torch.full_like(t, 0.25))
+
+
+def test_gradients_central_differences():
+    torch.manual_seed(0)
+    x = torch.rand(3, 24, 32, dtype=ow.DT)
+    P = _params(2)
+    tg = [torch.randn(-(-24 // (1 << l)), -(-32 // (1 << l)), dtype=ow.DT) for l in range(5)]
+    L = ow.loss(x, P, tg)
+    L.backward()
+    rng = np.random.default_rng(3)
+    eps = 1e-6
+    for name in ("c1.w", "c3.w", "c4.b", "h2.w", "h0.w", "h4.b"):
+        t = P[name]
+        for _ in range(3):
+            i = tuple(int(rng.integers(s)) for s in t.shape)
+            with torch.no_grad():
+                t[i] += eps
+                lp = float(ow.loss(x, P, tg))
+                t[i] -= 2 * eps
+                lm = float(ow.loss(x, P, tg))
+                t[i] += eps
+            fd = (lp - lm) / (2 * eps)
+            assert abs(fd - float(t.grad[i])) <= 1e-6 * max(1.0, abs(fd)), (name, i, fd, float(t.grad[i]))
