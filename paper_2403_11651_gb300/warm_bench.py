@@ -21,7 +21,10 @@ from __future__ import annotations
 
 import argparse
 import json
+import multiprocessing as mp
+import os
 import time
+from concurrent.futures import ProcessPoolExecutor
 
 import numpy as np
 
@@ -74,6 +77,17 @@ def main(argv=None):
     ap.add_argument("--chunk", type=int, default=64)
     ap.add_argument("--max-data-s", type=float, default=float("inf"))
     a = ap.parse_args(argv)
+    # the synthetic images are made on the host cores while the GPU overfits (a spawned
+    # pool, started before this process's first CUDA call)
+    pool = ProcessPoolExecutor(max_workers=max(1, min(8, (os.cpu_count() or 2) - 2)),
+                               mp_context=mp.get_context("spawn"))
+    try:
+        return _main(a, pool)
+    finally:
+        pool.shutdown(cancel_futures=True)
+
+
+def _main(a, pool):
     S = a.size
     TH, TW = a.test_size if a.test_size else (S, S)
     n_ablate = a.test if a.ablate is None else min(a.ablate, a.test)
@@ -83,13 +97,17 @@ def main(argv=None):
                                  cc.make_config(d))
             for k in range(a.train + a.test)}
 
+    train_img = [pool.submit(syn.synthetic_image, S, S, 1000 + k) for k in range(a.train)]
+    test_img = [pool.submit(syn.synthetic_image, TH, TW, 1000 + k)
+                for k in range(a.train, a.train + a.test)]
+
     # 1. training pairs from this project's own encoder
     t0 = time.perf_counter()
     images, lat, dec_sum = [], [], np.zeros(n_params, np.float64)
     for c0 in range(0, a.train, a.chunk):
         if time.perf_counter() - t0 > a.max_data_s:
             break
-        items = [(syn.synthetic_image(S, S, 1000 + k), d, init[k], k)
+        items = [(train_img[k].result(), d, init[k], k)
                  for k in range(c0, min(a.train, c0 + a.chunk))]
         b = BatchOverfitter(items, lanes=8)
         try:
@@ -126,7 +144,7 @@ def main(argv=None):
         n_lat = sum(h * w_ for h, w_ in cc.level_shapes(TH, TW))
         res = []
         for j, k in enumerate(range(a.train, a.train + a.test)):
-            rgb = syn.synthetic_image(TH, TW, 1000 + k)
+            rgb = test_img[j].result()
             cfg = cc.make_config(d, seed=k)
             t0 = time.perf_counter()
             y0 = cc.cc_warm_predict(wt, rgb, n_lat)
