@@ -162,3 +162,19 @@ def test_library_copies_load_independently(lib):
         n = ctypes.c_int()
         assert l.cc_param_count(ctypes.byref(cfg), ctypes.byref(n)) == 0
         assert n.value == cc.cc_param_count(cfg)
+
+
+def test_warm_predictor_host_checks(lib):
+    """Parameter count of the warm-start predictor (4 convolutions of 32 channels, 5
+    heads) and its argument checks, all taken before any device work."""
+    ch = 32
+    want = (ch * 3 * 9 + ch) + 3 * (ch * ch * 9 + ch) + 4 * (ch + 1) + (3 * 9 + 1)
+    assert cc.cc_warm_param_count() == want == 28800
+    params = np.zeros(want, np.float32)
+    for H, W in [(15, 64), (64, 15), (16385, 64), (0, 0)]:
+        with pytest.raises(cc.CCError) as e:
+            cc.cc_warm_create(H, W, params)
+        assert e.value.code == cc.CC_EINVAL
+    assert lib.cc_warm_predict(None, None, None) == cc.CC_EINVAL
+    assert lib.cc_warm_set_params(None, None) == cc.CC_EINVAL
+    lib.cc_warm_free(None)
