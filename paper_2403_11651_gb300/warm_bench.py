@@ -63,7 +63,7 @@ def run_schedule(cfg, rgb, init_params, latents, iters, every):
         cc.cc_free(ctx)
 
 
-def main(argv=None):
+def parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=48)
     ap.add_argument("--test", type=int, default=8)
@@ -76,18 +76,24 @@ def main(argv=None):
     ap.add_argument("--ablate", type=int, default=None)
     ap.add_argument("--chunk", type=int, default=64)
     ap.add_argument("--max-data-s", type=float, default=float("inf"))
-    a = ap.parse_args(argv)
+    return ap
+
+
+def main(argv=None):
+    a = parser().parse_args(argv)
     # the synthetic images are made on the host cores while the GPU overfits (a spawned
     # pool, started before this process's first CUDA call)
     pool = ProcessPoolExecutor(max_workers=max(1, min(8, (os.cpu_count() or 2) - 2)),
                                mp_context=mp.get_context("spawn"))
     try:
-        return _main(a, pool)
+        print(json.dumps(experiment(a, pool)))
     finally:
         pool.shutdown(cancel_futures=True)
 
 
-def _main(a, pool):
+def experiment(a, pool):
+    """The whole experiment for the options a (see parser()); pool makes the synthetic
+    images (anything with submit(fn, *args) -> future)."""
     S = a.size
     TH, TW = a.test_size if a.test_size else (S, S)
     n_ablate = a.test if a.ablate is None else min(a.ablate, a.test)
@@ -184,13 +190,15 @@ def _main(a, pool):
 
     def mean_hits(key):
         h = [r[key] for r in res if r[key] != "not run"]
+        if not h:
+            return (None, 0)
         return (float(np.mean([x if x is not None else a.iters for x in h])),
                 sum(x is not None for x in h))
     checkpoints = [min(i * a.every, a.iters) for i in range(len(curves[0][0]))]
     pick = list(range(0, len(checkpoints), 4))
     if pick[-1] != len(checkpoints) - 1:
         pick.append(len(checkpoints) - 1)
-    print(json.dumps({
+    return {
         "workload": f"{n_train} training synthetic {S}x{S} / {a.test} held-out synthetic "
                     f"{TH}x{TW} images, 2300-MAC decoder, {a.iters} iterations (last 20 % "
                     f"straight-through); ablations on {n_ablate} held-out images",
@@ -216,7 +224,7 @@ def _main(a, pool):
             [r["warm_final"] / r["plain_final"] for r in res])),
         "mean_start_cost_ratio_warm_over_plain": float(np.mean(
             [r["warm_start"] / r["plain_start"] for r in res])),
-        "per_image": res}))
+        "per_image": res}
 
 
 if __name__ == "__main__":
