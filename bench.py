@@ -366,13 +366,19 @@ def run_ours(a, cfgd):
     if rank == 0:
         try:
             from paper_2403_11651_gb300 import batch_bench
+            from paper_2403_11651_gb300.batch import autotune
             items = batch_bench.workload(16, 0, 256 * 256)
+            t0 = time.perf_counter()
+            (lanes, chunk), table = autotune(items)
+            t_tune = time.perf_counter() - t0
             t_one, rd_one = batch_bench.timed(items, 1, 500)
-            t_lanes, rd_lanes = batch_bench.timed(items, 8, 500)
+            t_lanes, rd_lanes = batch_bench.timed(items, lanes, 500, chunk)
             px = sum(rgb.shape[0] * rgb.shape[1] for rgb, _, _, _ in items)
             batch = {"workload": "16 synthetic 256x256 images, half with each decoder, "
                                  "lambda log-uniform [1e-4, 1e-2], 500 iterations each",
-                     "one_at_a_time_s": t_one, "batched_s": t_lanes, "lanes": 8,
+                     "one_at_a_time_s": t_one, "batched_s": t_lanes, "lanes": lanes,
+                     "chunk": chunk, "autotune_s": t_tune,
+                     "autotune_probe_s": {f"{k[0]}x{k[1]}": v for k, v in table.items()},
                      "speedup": t_one / t_lanes,
                      "batched_mpx_iter_s": px * 500 / t_lanes / 1e6,
                      "final_rd_identical": rd_one == rd_lanes}

@@ -9,6 +9,8 @@ take turns on the lane's stream (``chunk`` iterations each), and the lanes run
 concurrently -- small, latency-bound images then share the GPU instead of each leaving it
 mostly idle.  Every image runs exactly the iterations it would run alone (same kernels,
 same state, its own weights and schedule), so its results are bit-identical.
+``autotune`` picks the lane count and chunk length for a batch by timing each candidate
+on throwaway contexts of the same images.
 """
 from __future__ import annotations
 
@@ -141,3 +143,33 @@ class BatchOverfitter:
             if h:
                 self.libs[self.lane_of[i]].cc_free(h)
         self.ctx = []
+
+
+def autotune(items, lanes_options=(1, 2, 4, 8, 16), chunk_options=(16, 32, 64),
+             probe_iters: int = 64, timer=None):
+    """Choose (lanes, chunk) for a batch by measurement.
+
+    Each candidate runs the same images on throwaway contexts: one chunk of warm-up (CUDA
+    graph capture), then probe_iters timed iterations; the images of the real run are not
+    touched.  Lane counts above the number of images are clamped and repeated candidates
+    skipped.  Any choice gives bit-identical results, so only the time is compared.
+    Returns ((lanes, chunk), {(lanes, chunk): seconds})."""
+    import time
+    timer = timer or time.perf_counter
+    seen, table = set(), {}
+    for lanes in lanes_options:
+        lanes = max(1, min(lanes, len(items)))
+        for chunk in chunk_options:
+            if (lanes, chunk) in seen:
+                continue
+            seen.add((lanes, chunk))
+            b = BatchOverfitter(items, lanes=lanes, chunk=chunk)
+            try:
+                b.run(chunk)
+                t0 = timer()
+                b.run(probe_iters)
+                table[(lanes, chunk)] = timer() - t0
+            finally:
+                b.close()
+    best = min(table, key=lambda k: (table[k], k))
+    return best, table

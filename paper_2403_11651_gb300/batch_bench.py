@@ -39,8 +39,8 @@ def workload(n: int, seed: int, max_pixels: int = 0):
     return items
 
 
-def timed(items, lanes, iters):
-    b = BatchOverfitter(items, lanes=lanes)
+def timed(items, lanes, iters, chunk=16):
+    b = BatchOverfitter(items, lanes=lanes, chunk=chunk)
     try:
         b.run(3)                              # graph capture and warm-up
         t0 = time.perf_counter()

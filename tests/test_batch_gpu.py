@@ -5,6 +5,7 @@ import pytest
 
 from paper_2403_11651_gb300 import coolchic as cc
 from paper_2403_11651_gb300 import synthetic as syn
+from paper_2403_11651_gb300 import batch as batch_mod
 from paper_2403_11651_gb300.batch import BatchOverfitter
 
 from .helpers import config_dict
@@ -44,3 +45,24 @@ def test_batch_matches_single_runs():
             assert cc.cc_rd_cost(ctx, True) == got_rd[i], i
         finally:
             cc.cc_free(ctx)
+
+
+def test_autotuned_batch_matches_one_lane():
+    """The autotuner measures every candidate on throwaway contexts; the configuration it
+    picks gives the same results as one lane."""
+    items = _items()
+    best, table = batch_mod.autotune(items, lanes_options=(1, 2, 5), chunk_options=(16, 32),
+                                     probe_iters=32)
+    assert set(table) == {(1, 16), (1, 32), (2, 16), (2, 32), (5, 16), (5, 32)}
+    assert best in table and all(t > 0 for t in table.values())
+    out = []
+    for lanes, chunk in ((1, 16), best):
+        b = BatchOverfitter(items, lanes=lanes, chunk=chunk)
+        try:
+            b.run(24)
+            out.append(([b.losses(i, 0, 24) for i in range(len(items))], b.rd_costs()))
+        finally:
+            b.close()
+    assert out[0][1] == out[1][1]
+    for a, c in zip(out[0][0], out[1][0]):
+        assert np.array_equal(a, c)
