@@ -231,7 +231,7 @@ struct cc_warm {
   int h[5], w[5];          // activation sizes: level l = conv l output (l = 1 .. 4), 0 = image
   void* mem = nullptr;
   float *params, *grads, *m, *v;
-  float *x, *act[5], *dact[5], *pred, *dpred;
+  float *x, *act[5], *dact[5], *pred, *dpred, *target;
   uint8_t* img;
   double* part;
   int n_part = 0;
@@ -379,6 +379,7 @@ int cc_warm_create(int H, int W, const float* params, void* stream, cc_warm** ou
   }
   const size_t o_pred = take((size_t)c->geo.n_lat * sizeof(float));
   const size_t o_dpred = take((size_t)c->geo.n_lat * sizeof(float));
+  const size_t o_tgt = take((size_t)c->geo.n_lat * sizeof(float));
   const size_t o_img = take((size_t)3 * H * W);
   const size_t o_part = take((size_t)c->n_part * sizeof(double));
   cudaError_t e = cudaMalloc(&c->mem, off);
@@ -390,6 +391,7 @@ int cc_warm_create(int H, int W, const float* params, void* stream, cc_warm** ou
   c->act[0] = c->dact[0] = nullptr;
   for (int i = 1; i <= 4; ++i) { c->act[i] = (float*)(b + o_a[i]); c->dact[i] = (float*)(b + o_d[i]); }
   c->pred = (float*)(b + o_pred); c->dpred = (float*)(b + o_dpred);
+  c->target = (float*)(b + o_tgt);
   c->img = (uint8_t*)(b + o_img); c->part = (double*)(b + o_part);
   if ((e = cudaMemsetAsync(c->mem, 0, off, c->st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(c->params, params, NP, cudaMemcpyDefault, c->st)) != cudaSuccess ||
@@ -418,9 +420,12 @@ int cc_warm_loss_grad(cc_warm* c, const uint8_t* rgb_hwc, const float* target, d
                       float* grads_out) {
   if (!c || !rgb_hwc || !target) return CC_EINVAL;
   WCK(cudaSetDevice(c->dev));
+  // the target may be host memory: staged on the device before the loss kernels read it
+  WCK(cudaMemcpyAsync(c->target, target, (size_t)c->geo.n_lat * sizeof(float),
+                      cudaMemcpyDefault, c->st));
   int e = warm_image(c, rgb_hwc);
   if (!e) e = warm_forward(c);
-  if (!e) e = warm_backward(c, target, loss);
+  if (!e) e = warm_backward(c, c->target, loss);
   if (e) return e;
   if (grads_out) {
     WCK(cudaMemcpyAsync(grads_out, c->grads, (size_t)c->L.total * sizeof(float),

@@ -81,3 +81,28 @@ def test_training_lowers_the_loss():
     finally:
         cc.cc_warm_free(w)
     assert last < 0.4 * first, (first, last)
+
+
+def test_host_and_device_buffers_agree():
+    """Image, target and outputs may each be host or device memory: same results."""
+    H, W = 48, 80
+    flat = syn.warm_initial_parameters(3)
+    rgb = syn.synthetic_image(H, W, 3)
+    n_lat = sum(-(-H // (1 << l)) * -(-W // (1 << l)) for l in range(7))
+    tgt = np.random.default_rng(3).normal(0, 1.0, n_lat).astype(np.float32)
+    d_flat, d_rgb, d_tgt = (torch.from_numpy(a).cuda() for a in (flat, rgb, tgt))
+    g_dev = torch.empty(flat.size, dtype=torch.float32, device="cuda")
+    p_dev = torch.empty(n_lat, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    w = cc.cc_warm_create(H, W, d_flat)
+    try:
+        g_host = np.empty(flat.size, np.float32)
+        l_host = cc.cc_warm_loss_grad(w, rgb, tgt, g_host)
+        l_dev = cc.cc_warm_loss_grad(w, d_rgb, d_tgt, g_dev)
+        p_host = cc.cc_warm_predict(w, rgb, n_lat)
+        cc.cc_warm_predict(w, d_rgb, n_lat, p_dev)
+    finally:
+        cc.cc_warm_free(w)
+    assert l_host == l_dev
+    assert np.array_equal(g_host, g_dev.cpu().numpy())
+    assert np.array_equal(p_host, p_dev.cpu().numpy())
