@@ -39,8 +39,21 @@ def config(iters: int):
     return d
 
 
+def checkpoints(iters: int, every: int):
+    """Iteration counts at which run_schedule reads the cost: 0, every, 2 every, ..., iters."""
+    out = list(range(0, iters, every)) + [iters]
+    return out if iters > 0 else [0]
+
+
+def first_at_or_below(curve, target):
+    """Index of the first entry of curve at or below target, or None."""
+    hit = np.nonzero(np.asarray(curve) <= target)[0]
+    return int(hit[0]) if hit.size else None
+
+
 def run_schedule(cfg, rgb, init_params, latents, iters, every):
-    """Hard RD cost every `every` iterations (first entry: before any) and seconds."""
+    """Hard RD cost at each of checkpoints(iters, every), and the seconds spent up to each
+    (host clock around the iterations and the synchronising cost reads; 0 at the start)."""
     H, W = rgb.shape[:2]
     ctx = cc.cc_init_image(cfg, rgb, H, W, init_params)
     try:
@@ -48,6 +61,7 @@ def run_schedule(cfg, rgb, init_params, latents, iters, every):
             cc.cc_set_latents(ctx, latents)
         costs = [cc.cc_rd_cost(ctx, True)[2]]
         spent = 0.0
+        secs = [0.0]
         done = 0
         while done < iters:
             n = min(every, iters - done)
@@ -57,8 +71,9 @@ def run_schedule(cfg, rgb, init_params, latents, iters, every):
             c = cc.cc_rd_cost(ctx, True)[2]      # synchronises
             spent += time.perf_counter() - t0
             costs.append(c)
+            secs.append(spent)
             done += n
-        return np.array(costs), spent
+        return np.array(costs), np.array(secs)
     finally:
         cc.cc_free(ctx)
 
@@ -159,18 +174,20 @@ def experiment(a, pool):
             t0 = time.perf_counter()
             y0 = cc.cc_warm_predict(wt, rgb, n_lat)
             t_pred = time.perf_counter() - t0
-            plain, s_plain = run_schedule(cfg, rgb, init, None, a.iters, a.every)
-            warm, s_warm = run_schedule(cfg, rgb, dec, y0, a.iters, a.every)
+            plain, plain_s = run_schedule(cfg, rgb, init, None, a.iters, a.every)
+            warm, warm_s = run_schedule(cfg, rgb, dec, y0, a.iters, a.every)
             # ablations: the mean decoder alone (latents 0), the predicted latents alone
             if j < n_ablate:
                 dec_only, _ = run_schedule(cfg, rgb, dec, None, a.iters, a.every)
                 lat_only, _ = run_schedule(cfg, rgb, init, y0, a.iters, a.every)
             target = plain[-1] * 1.01
+            cps = checkpoints(a.iters, a.every)
 
             def first_hit(curve):
-                hit = np.nonzero(curve <= target)[0]
-                return int(hit[0]) * a.every if hit.size else None
-            it_hit = first_hit(warm)
+                i = first_at_or_below(curve, target)
+                return cps[i] if i is not None else None
+            i_hit = first_at_or_below(warm, target)
+            it_hit = cps[i_hit] if i_hit is not None else None
             curves.append((plain / plain[-1], warm / plain[-1]))
             res.append({"plain_final": float(plain[-1]), "warm_final": float(warm[-1]),
                         "plain_start": float(plain[0]), "warm_start": float(warm[0]),
@@ -179,9 +196,9 @@ def experiment(a, pool):
                             first_hit(dec_only) if j < n_ablate else "not run",
                         "latents_only_iters_to_plain_final":
                             first_hit(lat_only) if j < n_ablate else "not run",
-                        "warm_s_to_plain_final": (t_pred + s_warm * it_hit / a.iters)
-                        if it_hit is not None else None,
-                        "plain_s": s_plain})
+                        "warm_s_to_plain_final": (t_pred + float(warm_s[i_hit]))
+                        if i_hit is not None else None,
+                        "plain_s": float(plain_s[-1])})
     finally:
         if wt is not None and wt is not w:
             cc.cc_warm_free(wt)
@@ -194,10 +211,10 @@ def experiment(a, pool):
             return (None, 0)
         return (float(np.mean([x if x is not None else a.iters for x in h])),
                 sum(x is not None for x in h))
-    checkpoints = [min(i * a.every, a.iters) for i in range(len(curves[0][0]))]
-    pick = list(range(0, len(checkpoints), 4))
-    if pick[-1] != len(checkpoints) - 1:
-        pick.append(len(checkpoints) - 1)
+    cps = checkpoints(a.iters, a.every)
+    pick = list(range(0, len(cps), 4))
+    if pick[-1] != len(cps) - 1:
+        pick.append(len(cps) - 1)
     return {
         "workload": f"{n_train} training synthetic {S}x{S} / {a.test} held-out synthetic "
                     f"{TH}x{TW} images, 2300-MAC decoder, {a.iters} iterations (last 20 % "
@@ -216,7 +233,7 @@ def experiment(a, pool):
         "mean_warm_s_to_plain_final_reached": float(np.mean(
             [r["warm_s_to_plain_final"] for r in res if r["warm_s_to_plain_final"] is not None]))
         if any(r["warm_s_to_plain_final"] is not None for r in res) else None,
-        "curve_iters": [checkpoints[i] for i in pick],
+        "curve_iters": [cps[i] for i in pick],
         "mean_cost_over_plain_final": {
             "plain": [float(v) for v in np.mean([c[0] for c in curves], axis=0)[pick]],
             "warm": [float(v) for v in np.mean([c[1] for c in curves], axis=0)[pick]]},
