@@ -123,6 +123,12 @@ class BatchOverfitter:
             _check(lib, code, "cc_get_losses")
         return out
 
+    def set_latents(self, i: int, y_flat):
+        """Replace image i's latents (flat latent order, float32, host or device)."""
+        lib = self.libs[self.lane_of[i]]
+        y = np.ascontiguousarray(y_flat, np.float32) if isinstance(y_flat, np.ndarray) else y_flat
+        _check(lib, lib.cc_set_latents(self.ctx[i], cc._ptr(y)), "cc_set_latents")
+
     def latents(self, i: int):
         """Image i's latents (flat latent order, float32)."""
         lib = self.libs[self.lane_of[i]]

@@ -78,6 +78,55 @@ def run_schedule(cfg, rgb, init_params, latents, iters, every):
         cc.cc_free(ctx)
 
 
+def batched_eval(a, d, init, dec, starts, plain_finals):
+    """The held-out images as one batch on a.lanes concurrent lanes (every image's
+    iterations bit-identical to its own run).  Plain: zero latents and the seeded decoder
+    for the whole schedule.  Warm: the predicted latents and the mean trained decoder until
+    every image's hard RD cost is within 1 % of its plain run's final cost, read every
+    a.every iterations.  Plain runs the whole schedule (the runner synchronises every
+    a.every iterations) and reads the costs once at the end.  Seconds on the host clock
+    from the first iteration; the warm start's include the predictor's inference of every
+    image."""
+    cps = checkpoints(a.iters, a.every)
+
+    def run(init_params, latents, targets):
+        items = [(rgb, d, init_params, a.train + j) for j, (rgb, _, _, _) in enumerate(starts)]
+        b = BatchOverfitter(items, lanes=a.lanes, chunk=16)
+        try:
+            if latents is not None:
+                for i, y in enumerate(latents):
+                    b.set_latents(i, y)
+            reached = [None] * len(items)
+            done = 0
+            t0 = time.perf_counter()
+            for it in cps[1:]:
+                b.run(it - done)
+                done = it
+                if targets is None:
+                    continue
+                for i, (_, _, cost) in enumerate(b.rd_costs()):
+                    if reached[i] is None and cost <= targets[i]:
+                        reached[i] = it
+                if all(r is not None for r in reached):
+                    break
+            if targets is None:
+                b.rd_costs()
+            return time.perf_counter() - t0, reached, done
+        finally:
+            b.close()
+
+    t_plain, _, _ = run(init, None, None)
+    targets = [p * 1.01 for p in plain_finals]
+    t_warm, reached, stopped = run(dec, [y for _, _, y, _ in starts], targets)
+    t_pred = sum(t for _, _, _, t in starts)
+    return {"images": len(starts), "lanes": a.lanes,
+            "plain_batched_s": t_plain,
+            "warm_batched_s_to_all_reached": t_warm + t_pred,
+            "warm_stopped_at_iter": stopped,
+            "warm_reached_iters": reached,
+            "all_reached": all(r is not None for r in reached)}
+
+
 def parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=48)
@@ -91,6 +140,11 @@ def parser():
     ap.add_argument("--ablate", type=int, default=None)
     ap.add_argument("--chunk", type=int, default=64)
     ap.add_argument("--max-data-s", type=float, default=float("inf"))
+    ap.add_argument("--batched-eval", action="store_true",
+                    help="also run the held-out images as one batch (concurrent lanes): "
+                         "plain for the whole schedule, and warm-started until every image "
+                         "reaches its plain run's final cost")
+    ap.add_argument("--lanes", type=int, default=8)
     return ap
 
 
@@ -167,13 +221,14 @@ def experiment(a, pool):
 
         # 3. held-out images: plain against warm start
         n_lat = sum(h * w_ for h, w_ in cc.level_shapes(TH, TW))
-        res, curves = [], []
+        res, curves, starts = [], [], []
         for j, k in enumerate(range(a.train, a.train + a.test)):
             rgb = test_img[j].result()
             cfg = cc.make_config(d, seed=k)
             t0 = time.perf_counter()
             y0 = cc.cc_warm_predict(wt, rgb, n_lat)
             t_pred = time.perf_counter() - t0
+            starts.append((rgb, cfg, y0, t_pred))
             plain, plain_s = run_schedule(cfg, rgb, init, None, a.iters, a.every)
             warm, warm_s = run_schedule(cfg, rgb, dec, y0, a.iters, a.every)
             # ablations: the mean decoder alone (latents 0), the predicted latents alone
@@ -203,6 +258,8 @@ def experiment(a, pool):
         if wt is not None and wt is not w:
             cc.cc_warm_free(wt)
         cc.cc_warm_free(w)
+    batched = batched_eval(a, d, init, dec, starts, [r["plain_final"] for r in res]) \
+        if a.batched_eval else None
     hits = [r["warm_iters_to_plain_final"] for r in res]
 
     def mean_hits(key):
@@ -241,6 +298,7 @@ def experiment(a, pool):
             [r["warm_final"] / r["plain_final"] for r in res])),
         "mean_start_cost_ratio_warm_over_plain": float(np.mean(
             [r["warm_start"] / r["plain_start"] for r in res])),
+        "batched_eval": batched,
         "per_image": res}
 
 
