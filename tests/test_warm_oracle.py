@@ -1,6 +1,7 @@
 """Pins of the warm-start predictor oracle (oracle/warm.py): the convolution definition
-by explicit loops, output sizes, the constant-output case, gradients by central
-differences; and its parameter order against the binding's."""
+by explicit loops, the whole forward wiring restated with tap loops, output sizes, the
+constant-output case, gradients by central differences; and its parameter order against
+the binding's."""
 import numpy as np
 import pytest
 import torch
@@ -92,3 +93,37 @@ def test_gradients_central_differences():
                 t[i] += eps
             fd = (lp - lm) / (2 * eps)
             assert abs(fd - float(t.grad[i])) <= 1e-6 * max(1.0, abs(fd)), (name, i, fd, float(t.grad[i]))
+
+
+def _conv_loops(x, w, b, s):
+    """out[co, y, x] = b[co] + sum w[co, ci, ky, kx] in[ci, s y + ky - 1, s x + kx - 1]
+    (0 outside), written out over the taps; x [Ci, H, W], w [Co, Ci, 3, 3]."""
+    Ci, H, W = x.shape
+    Ho, Wo = -(-H // s), -(-W // s)
+    pad = np.zeros((Ci, H + 2 + s, W + 2 + s))
+    pad[:, 1:H + 1, 1:W + 1] = x
+    out = np.zeros((w.shape[0], Ho, Wo)) + b[:, None, None]
+    for ky in range(3):
+        for kx in range(3):
+            win = pad[:, ky:ky + s * Ho:s, kx:kx + s * Wo:s]        # in[ci, s y + ky - 1, ...]
+            out += np.einsum("oc,chw->ohw", w[:, :, ky, kx], win)
+    return out
+
+
+@pytest.mark.parametrize("H,W", [(16, 16), (21, 35)])
+def test_forward_wiring_by_loops(H, W):
+    """The architecture as written: level 0 = 3x3 stride-1 convolution of the image;
+    a_1 .. a_4 = ReLU(3x3 stride-2 convolution of the previous stage, the image first);
+    level l = 1x1 head of a_l.  Restated with explicit tap loops, not torch's conv2d."""
+    rng = np.random.default_rng(H * W)
+    x = rng.uniform(0, 1, (3, H, W))
+    P = _params(5)
+    Pn = {k: v.detach().numpy() for k, v in P.items()}
+    want = [_conv_loops(x, Pn["h0.w"], Pn["h0.b"], 1)[0]]
+    a = x
+    for i in (1, 2, 3, 4):
+        a = np.maximum(_conv_loops(a, Pn[f"c{i}.w"], Pn[f"c{i}.b"], 2), 0.0)
+        want.append(np.einsum("c,chw->hw", Pn[f"h{i}.w"][0, :, 0, 0], a) + Pn[f"h{i}.b"][0])
+    got = ow.forward(torch.tensor(x, dtype=ow.DT), P)
+    for l in range(5):
+        np.testing.assert_allclose(got[l].detach().numpy(), want[l], rtol=1e-12, atol=1e-12)
