@@ -422,6 +422,35 @@ def run_ours(a, cfgd):
         except Exception as e:   # reported, never fatal to the main measurement
             warm = {"error": f"{type(e).__name__}: {e}"}
 
+    # the same iteration written with plain PyTorch eager operations (autograd backward,
+    # torch.optim.Adam) on the same GPU and image: what the hand-written kernels gain
+    eager = None
+    if rank == 0:
+        try:
+            from paper_2403_11651_gb300.eager_baseline import EagerIteration
+            it = EagerIteration(rgb, cfgd, syn.initial_parameters(
+                syn.ArchSizes.from_config(cfgd), rank), dev)
+            for _ in range(3):
+                it.step()
+            n_eager = 10
+            s_eager = torch.cuda.current_stream(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(s_eager)
+            for _ in range(n_eager):
+                it.step()
+            e1.record(s_eager)
+            torch.cuda.synchronize(dev)
+            eager_ms = e0.elapsed_time(e1) / n_eager
+            eager = {"workload": f"{H}x{W}, the same configuration and image",
+                     "ms_per_iter": eager_ms, "value": H * W / (eager_ms * 1e3), "unit": UNIT,
+                     "library_speedup": eager_ms / (total_ms / a.steps),
+                     "note": f"{n_eager} iterations after 3 warm-up ones, CUDA events on the "
+                             f"current stream, L2 not flushed; float32; noise from torch.rand"}
+            del it
+        except Exception as e:   # reported, never fatal to the main measurement
+            eager = {"error": f"{type(e).__name__}: {e}"}
+
     pk, src = peaks()
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
@@ -462,6 +491,7 @@ def run_ours(a, cfgd):
         "first_configuration": c1,
         "batch": batch,
         "warm_start": warm,
+        "pytorch_eager": eager,
     }
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         v, n, dt, cores = oracle_rate(cfgd, 15.0, H, W)
