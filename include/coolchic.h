@@ -234,8 +234,9 @@ int cc_rate_bits_noalloc(const cc_config* cfg, const float* yhat_flat, int H, in
  * conditioned on its already-decoded causal neighbours, then upsamples and synthesises.
  * The decoder re-evaluates the ARM, so both sides run it in integer arithmetic:
  *   - ARM weights and biases rounded (half to even) to multiples of 2^-8 (Q8; weights
- *     clamped to +-2^20, biases to +-2^28 in Q8 units); inputs = integer latents x 256; a
- *     layer z = ((sum W a) + 128) >> 8 + b in 64-bit integers, saturated to +-2^28; LinR
+ *     clamped to +-2^11 in Q8 units, i.e. |w| <= 8, biases to +-2^15); inputs = integer
+ *     latents clamped to [-128, 128], times 256; a layer z = ((sum W a) + 128) >> 8 + b
+ *     (round half up), every sum exact in 32-bit integers, saturated to +-2^15; LinR
  *     output a + max(z, 0), saturated; the output layer gives (mu, log-scale) in Q8;
  *   - probabilities from 744 Laplace frequency tables (93 log-scale bins of width 1/8 from
  *     ln 0.01, 8 bins of mu's fraction; symbols y - floor(mu) in [-64, 64] plus one escape
@@ -255,7 +256,8 @@ int cc_rate_bits_noalloc(const cc_config* cfg, const float* yhat_flat, int H, in
  * cc_decode_bitstream: decodes a bitstream in host memory on the current device and
  *   the given stream (cudaStream_t or NULL): the latent rows as a wavefront (row r
  *   decodes position x at step x + lag r, lag 3 for N = 8 and 4 for N = 16 or 24), one
- *   warp per band of 16 rows (two lanes per row), every band waiting (bounded;
+ *   warp per band of rows (32 rows of one lane each for N = 8, 16 rows of two lanes each
+ *   for N = 16 or 24), every band waiting (bounded;
  *   CC_ETIMEOUT if it gives up) on the band above it, all levels at once in one
  *   cooperative launch; then the float32 upsampling and synthesis.  Optional outputs (host or device): rgb_out_hwc (H x W x 3 floats, not
  *   clamped, as cc_decode), latents_out (cc_latent_count int32, flat latent order),
