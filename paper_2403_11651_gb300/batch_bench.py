@@ -2,12 +2,13 @@
 other, printed as one JSON line.
 
     python -m paper_2403_11651_gb300.batch_bench [--images 32] [--iters 300] [--lanes 8]
-                                                 [--max-pixels N]
+                                                 [--max-pixels N] [--autotune]
 
 Workload: images of sizes drawn uniformly from 256x256, 512x768, 768x512, 1024x1024 and
 1920x1080 (seeded synthetic images), half with the first configuration's decoder and half
 with the 2300-MAC one, lambda log-uniform in [1e-4, 1e-2].  Both runs start from the
-same state and run the same iterations: the final RD costs must agree exactly.
+same state and run the same iterations: the final RD costs must agree exactly.  With
+--autotune the lane count and chunk length come from batch.autotune instead of --lanes.
 """
 from __future__ import annotations
 
@@ -18,7 +19,7 @@ import time
 
 import numpy as np
 
-from .batch import BatchOverfitter   # first: sets the hardware queue count before CUDA starts
+from .batch import BatchOverfitter, autotune   # first: sets the hardware queue count
 from . import coolchic as cc
 from . import synthetic as syn
 
@@ -59,18 +60,26 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--max-pixels", type=int, default=0,
                     help="only the sizes with at most this many pixels (0: all)")
+    ap.add_argument("--autotune", action="store_true")
     a = ap.parse_args(argv)
     items = workload(a.images, a.seed, a.max_pixels)
     sizes = [s for s in SIZES if not a.max_pixels or s[0] * s[1] <= a.max_pixels]
     px = sum(rgb.shape[0] * rgb.shape[1] for rgb, _, _, _ in items)
+    lanes, chunk, tune = a.lanes, 16, None
+    if a.autotune:
+        t0 = time.perf_counter()
+        (lanes, chunk), table = autotune(items)
+        tune = {"seconds": time.perf_counter() - t0,
+                "probe_s": {f"{k[0]}x{k[1]}": v for k, v in table.items()}}
     t_plain, rd_plain = timed(items, 1, a.iters)
-    t_batch, rd_batch = timed(items, a.lanes, a.iters)
+    t_batch, rd_batch = timed(items, lanes, a.iters, chunk)
     small = [i for i, (rgb, _, _, _) in enumerate(items) if rgb.shape[0] * rgb.shape[1] <= 512 * 768]
     print(json.dumps({
         "workload": f"{a.images} images ({px / 1e6:.1f} Mpixel), sizes in {sizes}, "
                     f"half first configuration / half 2300-MAC, lambda log-uniform "
                     f"[1e-4, 1e-2], {a.iters} iterations each",
-        "plain_s": t_plain, "batched_s": t_batch, "lanes": a.lanes,
+        "plain_s": t_plain, "batched_s": t_batch, "lanes": lanes, "chunk": chunk,
+        "autotune": tune,
         "speedup": t_plain / t_batch,
         "plain_mpx_iter_s": px * a.iters / t_plain / 1e6,
         "batched_mpx_iter_s": px * a.iters / t_batch / 1e6,
