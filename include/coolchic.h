@@ -119,13 +119,39 @@ int cc_set_image(cc_ctx* ctx, const uint8_t* rgb_hwc);
 /* Run n_iters overfitting iterations (forward, backward, Adam), asynchronously on the
  * context stream, replaying a CUDA graph of one iteration.  Iteration t (counted from 0
  * since cc_init_image) uses noise quantisation while t < round(total_iters (1 -
- * ste_frac)) and rint + straight-through after.  Per-iteration D, R and loss are logged
+ * ste_frac)) (half-way cases to even) and rint + straight-through after.  Per-iteration D, R and loss are logged
  * on the device (see cc_get_losses). */
 int cc_encode_iters(cc_ctx* ctx, int n_iters);
 
+/* cc_encode_iters with a non-finite check and rollback (failure detection; the paper has
+ * no counterpart).  Runs up to n_iters iterations in chunks of check_every (1 .. 4096):
+ * before each chunk the optimisation state (latents, parameters, Adam moments, iteration
+ * scalars) is copied on the device; after it the chunk's logged D, R and loss are read.
+ * If any of them is NaN or infinite, or a pass of the chunk read a non-finite latent or
+ * produced a non-finite latent or parameter, or an ARM tensor-core wait gave up, the
+ * state is restored to the copy taken before the chunk, the iteration counter steps back,
+ * and the call returns CC_ENONFINITE (or CC_ETIMEOUT); *iters_done (host) receives the
+ * number of iterations kept.  (The kernels' ReLUs and clamps map a NaN input to a finite
+ * value, so a NaN in the state need not show in the loss; every pass therefore also
+ * checks the latents it reads and the values its updates write.)  Synchronises once per
+ * chunk.  CC_OK: all n_iters ran. */
+int cc_encode_iters_checked(cc_ctx* ctx, int n_iters, int check_every, int* iters_done);
+
+/* Host-side fault injection for tests of the failure paths (no GPU fault is involved).
+ *   CC_FAULT_NAN_GRAD (ctx given): the latent update of iteration at_iteration (>= the
+ *     current iteration) replaces the gradient of latent 0 by NaN, once; a rollback of
+ *     cc_encode_iters_checked clears it.
+ *   CC_FAULT_ALLOC (ctx NULL, at_iteration ignored): the next cc_init_image of this
+ *     process that would call cudaMalloc returns CC_ENOMEM instead, once.
+ * CC_EINVAL for any other combination. */
+#define CC_FAULT_NAN_GRAD 1
+#define CC_FAULT_ALLOC 2
+int cc_debug_inject(cc_ctx* ctx, int fault, int at_iteration);
+
 /* Rate-distortion cost of the current state, eq. (1): D = mean squared error over the
  * 3HW values, R_bpp = bits / (H W), cost = D + lambda R.  hard_round = 1: rint latents
- * (the decoded image); 0: the current iteration's noisy latents.  Synchronises. */
+ * (the decoded image); 0: the current iteration's noisy latents.  CC_ENONFINITE if the
+ * cost is not finite or a latent is (values still written).  Synchronises. */
 int cc_rd_cost(cc_ctx* ctx, int hard_round, double* D, double* R_bpp, double* cost);
 
 /* Decoded image x_hat = f_theta(f_upsilon(rint(y))) as H x W x 3 float32 (host or
@@ -141,9 +167,10 @@ int cc_get_grads(cc_ctx* ctx, const float* noise_override, float* grads_out);
 
 /* cc_get_grads with the loss terms of that pass and an explicit mode:
  * hard = 1 forces rint latents (noise_override ignored), 0 forces noise, -1 follows the
- * schedule.  D, R_bpp may be NULL. */
+ * schedule.  D, R_bpp and loss = D + lambda R_bpp (eq. (1)) are host doubles; each may be
+ * NULL. */
 int cc_forward_backward(cc_ctx* ctx, const float* noise_override, int hard,
-                        float* grads_out, double* D, double* R_bpp);
+                        float* grads_out, double* D, double* R_bpp, double* loss);
 
 /* D, R_bpp and loss of iterations first .. first+count-1 (3 doubles each, host or
  * device).  Only the last 4096 iterations are kept.  Synchronises. */
@@ -217,12 +244,18 @@ const char* cc_strerror(int code);
  *   bits_out:  host or device, one double;  cuda_stream: cudaStream_t or NULL.
  * Allocates nothing: its scratch -- one float per tile of 128 latents plus the double
  * total -- is a fixed file-scope __device__ array held by every device that loads the
- * library until the process exits.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  All calls share the array, so calls whose GPU work overlaps race:
- * issue them on one stream or synchronise between them.  Every call rewrites all the
- * scratch it reads.  Pyramids needing more than CC_NOALLOC_MAX_TILES tiles (about 8.4
- * million latents, e.g. 2048 x 3072 pixels) are rejected with CC_EINVAL and a message in
+ * library until the process exits.  The first call on a device (per loaded copy of the
+ * library) is a warm-up: it looks up that array's device address (cudaGetSymbolAddress)
+ * and caches it, and with CUDA's lazy module loading it is also the call that loads the
+ * library's kernels onto the device, which may itself reserve device memory.  Make that
+ * first call before the caller's no-allocation phase begins, and before any stream
+ * capture; later calls allocate nothing.  cuda_stream must belong to the device that is
+ * current when the call is made.  All calls share the scratch array and two
+ * __constant__ banks holding the ARM weights and context offsets, which every call
+ * overwrites before its kernels run: calls whose GPU work overlaps race on both, so issue
+ * them on one stream or synchronise between them.  Every call rewrites all the scratch it
+ * reads.  Pyramids needing more than CC_NOALLOC_MAX_TILES tiles (about 8.4 million
+ * latents, e.g. 2048 x 3072 pixels) are rejected with CC_EINVAL and a message in
  * cc_last_cuda_error().  Synchronises before returning. */
 #define CC_NOALLOC_MAX_TILES 65536
 int cc_rate_bits_noalloc(const cc_config* cfg, const float* yhat_flat, int H, int W,

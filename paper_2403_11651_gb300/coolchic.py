@@ -56,7 +56,8 @@ def _declare(lib):
         "cc_rd_cost": (c_int, [P, c_int, POINTER(c_double), POINTER(c_double), POINTER(c_double)]),
         "cc_decode": (c_int, [P, P]),
         "cc_get_grads": (c_int, [P, P, P]),
-        "cc_forward_backward": (c_int, [P, P, c_int, P, POINTER(c_double), POINTER(c_double)]),
+        "cc_forward_backward": (c_int, [P, P, c_int, P, POINTER(c_double), POINTER(c_double),
+                                        POINTER(c_double)]),
         "cc_get_losses": (c_int, [P, c_int, c_int, P]),
         "cc_get_losses_async": (c_int, [P, c_int, c_int, P]),
         "cc_iteration": (c_int, [P, POINTER(c_int)]),
@@ -69,7 +70,9 @@ def _declare(lib):
         "cc_graph_kernel_count": (c_int, [P, POINTER(c_int)]),
         "cc_get_state": (c_int, [P, P, POINTER(c_size_t)]),
         "cc_set_state": (c_int, [P, P, c_size_t]),
-        "cc_rate_bits_noalloc": (c_int, [P, P, c_int, c_int, P, P, POINTER(c_double)]),
+        "cc_rate_bits_noalloc": (c_int, [P, P, c_int, c_int, P, P, P]),
+        "cc_encode_iters_checked": (c_int, [P, c_int, c_int, POINTER(c_int)]),
+        "cc_debug_inject": (c_int, [P, c_int, c_int]),
         "cc_free": (None, [P]),
         "cc_strerror": (ctypes.c_char_p, [c_int]),
         "cc_last_cuda_error": (ctypes.c_char_p, []),
@@ -271,15 +274,34 @@ def cc_decode(ctx, H: int, W: int, out=None):
     return out
 
 
-def cc_forward_backward(ctx, n_total: int, noise=None, hard: int = -1, out=None):
+def cc_forward_backward(ctx, n_total: int, noise=None, hard: int = -1, out=None,
+                        with_loss: bool = False):
+    """(grads, D, R_bpp), or (grads, D, R_bpp, loss) with with_loss."""
     if out is None:
         out = np.empty(n_total, np.float32)
-    D, R = c_double(), c_double()
+    D, R, L = c_double(), c_double(), c_double()
     code = _lib().cc_forward_backward(ctx, _ptr(noise), int(hard), _ptr(out), ctypes.byref(D),
-                                      ctypes.byref(R))
+                                      ctypes.byref(R), ctypes.byref(L))
     if code not in (CC_OK, CC_ENONFINITE):
         _check(code, "cc_forward_backward")
-    return out, D.value, R.value
+    return (out, D.value, R.value, L.value) if with_loss else (out, D.value, R.value)
+
+
+def cc_encode_iters_checked(ctx, n_iters: int, check_every: int):
+    """(code, iterations kept): CC_OK, or CC_ENONFINITE / CC_ETIMEOUT after a rollback to
+    the state before the chunk that went wrong."""
+    done = c_int()
+    code = _lib().cc_encode_iters_checked(ctx, int(n_iters), int(check_every), ctypes.byref(done))
+    if code not in (CC_OK, CC_ENONFINITE, CC_ETIMEOUT):
+        _check(code, "cc_encode_iters_checked")
+    return code, done.value
+
+
+CC_FAULT_NAN_GRAD, CC_FAULT_ALLOC = 1, 2
+
+
+def cc_debug_inject(ctx, fault: int, at_iteration: int = 0):
+    _check(_lib().cc_debug_inject(ctx, int(fault), int(at_iteration)), "cc_debug_inject")
 
 
 def cc_get_grads(ctx, n_total: int, noise=None, out=None):
@@ -376,13 +398,24 @@ def cc_set_state(ctx, blob: bytes):
     _check(_lib().cc_set_state(ctx, buf, len(blob)), "cc_set_state")
 
 
-def cc_rate_bits_noalloc(cfg: cc_config, yhat_flat, H: int, W: int, params, stream=None) -> float:
-    """Total rate (bits) of a quantised pyramid, computed without allocating device memory."""
-    out = c_double()
+def cc_rate_bits_noalloc(cfg: cc_config, yhat_flat, H: int, W: int, params, stream=None,
+                         out=None):
+    """Total rate (bits) of a quantised pyramid, computed without allocating device memory.
+    With out (a one-element float64 tensor, host or device) the total is written there and
+    out is returned; otherwise it is returned as a float."""
+    if out is None:
+        v = c_double()
+        _check(_lib().cc_rate_bits_noalloc(ctypes.byref(cfg), _ptr(yhat_flat), H, W,
+                                           _ptr(params), _stream_handle(stream),
+                                           ctypes.byref(v)), "cc_rate_bits_noalloc")
+        return v.value
+    n_out = out.size if isinstance(out, np.ndarray) else out.numel()
+    if str(out.dtype) not in ("torch.float64", "float64") or n_out < 1:
+        raise ValueError("cc_rate_bits_noalloc: out must hold one float64")
     _check(_lib().cc_rate_bits_noalloc(ctypes.byref(cfg), _ptr(yhat_flat), H, W, _ptr(params),
-                                       _stream_handle(stream), ctypes.byref(out)),
+                                       _stream_handle(stream), _ptr(out)),
            "cc_rate_bits_noalloc")
-    return out.value
+    return out
 
 
 def bitstream_bound(cfg: cc_config, H: int, W: int) -> int:
@@ -510,4 +543,4 @@ EXPORTED = ["cc_param_count", "cc_latent_count", "cc_workspace_size", "cc_init_i
             "cc_decode_bitstream", "cc_warm_param_count", "cc_warm_create", "cc_warm_predict",
             "cc_warm_loss_grad", "cc_warm_train_step", "cc_warm_get_params",
             "cc_warm_set_params", "cc_warm_free", "cc_free", "cc_strerror",
-            "cc_last_cuda_error"]
+            "cc_last_cuda_error", "cc_encode_iters_checked", "cc_debug_inject"]

@@ -15,6 +15,7 @@ using namespace cc;
 namespace {
 
 thread_local char g_err[512] = "";
+bool g_fail_next_alloc = false;   // cc_debug_inject(NULL, CC_FAULT_ALLOC, 0)
 
 int fail_cuda(cudaError_t e, const char* what) {
   snprintf(g_err, sizeof(g_err), "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
@@ -174,6 +175,9 @@ struct cc_ctx {
   cudaGraphExec_t g1 = nullptr, g16 = nullptr;
   int iter = 0;
   int kernels_per_iter = 0;
+  // device copy of the state taken before each chunk of cc_encode_iters_checked
+  float *snap_y, *snap_my, *snap_vy, *snap_p, *snap_mp, *snap_vp;
+  IterScalars* snap_sc;
 };
 
 namespace {
@@ -224,6 +228,13 @@ size_t plan(cc_ctx* c, char* base) {
   c->syn_image = take(syn_image_bytes());
   c->sc = (IterScalars*)take(sizeof(IterScalars));
   c->log = (double*)take((size_t)kLogCap * 3 * sizeof(double));
+  c->snap_y = (float*)take(L);
+  c->snap_my = (float*)take(L);
+  c->snap_vy = (float*)take(L);
+  c->snap_p = (float*)take((size_t)c->lay.total * sizeof(float));
+  c->snap_mp = (float*)take((size_t)c->lay.total * sizeof(float));
+  c->snap_vp = (float*)take((size_t)c->lay.total * sizeof(float));
+  c->snap_sc = (IterScalars*)take(sizeof(IterScalars));
   for (int l = 1; l < kLevels; ++l)
     for (int j = 0; j < l; ++j) {
       const size_t n = (size_t)align32((long long)g.h[j] * g.w[j]) * sizeof(float);
@@ -242,7 +253,8 @@ int setup(cc_ctx* c, const cc_config* cfg, int H, int W) {
   c->lay = layout_of(c->arch);
   c->geo = geo_of(H, W);
   c->HW = H * W;
-  c->ste_start = (int)std::llround((double)cfg->total_iters * (1.0 - (double)cfg->ste_frac));
+  // round half to even (the default rounding mode), the rule of rint for the latents too
+  c->ste_start = (int)std::nearbyint((double)cfg->total_iters * (1.0 - (double)cfg->ste_frac));
   c->h_tiles.clear();
   // ARM tiles: blocks of kArmTileY x kArmTileX latents of one level, (level, y0 << 16 | x0)
   for (int l = 0; l < kLevels; ++l)
@@ -551,6 +563,12 @@ int init_common(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
     c->mem = ws;
     c->own_mem = false;
   } else {
+    if (g_fail_next_alloc) {   // host-side fault injection (cc_debug_inject)
+      g_fail_next_alloc = false;
+      delete c;
+      set_error_text("cc_init_image: injected allocation failure");
+      return CC_ENOMEM;
+    }
     cudaError_t ce = cudaMalloc(&c->mem, need);
     if (ce != cudaSuccess) { delete c; fail_cuda(ce, "cudaMalloc"); return CC_ENOMEM; }
     c->own_mem = true;
@@ -635,6 +653,30 @@ int copy_latents(cc_ctx* c, float* dev, float* flat, bool to_flat) {
   return CC_OK;
 }
 
+cudaError_t copy_log(cc_ctx* c, int first, int count, double* out, cudaMemcpyKind kind);
+
+// The host is writing new state: forget that an earlier pass saw non-finite values.
+cudaError_t clear_nonfinite(cc_ctx* c) {
+  static const int zero = 0;
+  return cudaMemcpyAsync(&c->sc->nonfinite, &zero, sizeof(int), cudaMemcpyHostToDevice, c->st);
+}
+
+// Device-to-device copies of the optimisation state (latents, parameters, Adam moments,
+// iteration scalars) into (save) or out of (restore) the snapshot buffers.
+cudaError_t snapshot_copy(cc_ctx* c, bool save) {
+  const size_t L = (size_t)c->geo.n_pad * sizeof(float);
+  const size_t P = (size_t)c->lay.total * sizeof(float);
+  struct { float* live; float* snap; size_t n; } b[6] = {
+      {c->y, c->snap_y, L}, {c->my, c->snap_my, L}, {c->vy, c->snap_vy, L},
+      {c->params, c->snap_p, P}, {c->mp, c->snap_mp, P}, {c->vp, c->snap_vp, P}};
+  for (auto& x : b)
+    CKE(cudaMemcpyAsync(save ? x.snap : x.live, save ? x.live : x.snap, x.n,
+                        cudaMemcpyDeviceToDevice, c->st));
+  return cudaMemcpyAsync(save ? (void*)c->snap_sc : (void*)c->sc,
+                         save ? (void*)c->sc : (void*)c->snap_sc, sizeof(IterScalars),
+                         cudaMemcpyDeviceToDevice, c->st);
+}
+
 }  // namespace
 
 extern "C" {
@@ -715,6 +757,53 @@ int cc_encode_iters(cc_ctx* c, int n_iters) {
   return CC_OK;
 }
 
+int cc_encode_iters_checked(cc_ctx* c, int n_iters, int check_every, int* iters_done) {
+  if (!c || !iters_done || n_iters < 0 || check_every < 1 || check_every > kLogCap)
+    return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  *iters_done = 0;
+  std::vector<double> h;
+  while (*iters_done < n_iters) {
+    const int k = std::min(check_every, n_iters - *iters_done);
+    CK(snapshot_copy(c, true));
+    int e = cc_encode_iters(c, k);
+    if (e) return e;
+    h.resize(3 * (size_t)k);
+    CK(copy_log(c, c->iter - k, k, h.data(), cudaMemcpyDeviceToHost));
+    IterScalars sc;
+    e = sync_copy_scalars(c, &sc);   // waits for the chunk; CC_ETIMEOUT on an ARM wait fault
+    bool bad = e != CC_OK || sc.nonfinite;
+    for (double v : h) bad = bad || !std::isfinite(v);
+    if (bad) {
+      // back to the state before the chunk; a one-shot injected fault does not return
+      CK(snapshot_copy(c, false));
+      const int never = -1, zero = 0;
+      CK(cudaMemcpyAsync(&c->sc->nan_at, &never, sizeof(int), cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemcpyAsync(&c->sc->fault, &zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
+      CK(clear_nonfinite(c));
+      CK(rebuild_images(c, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      c->iter -= k;
+      return e != CC_OK ? e : CC_ENONFINITE;
+    }
+    *iters_done += k;
+  }
+  return CC_OK;
+}
+
+int cc_debug_inject(cc_ctx* c, int fault, int at_iteration) {
+  if (fault == CC_FAULT_ALLOC) {
+    if (c) return CC_EINVAL;
+    g_fail_next_alloc = true;
+    return CC_OK;
+  }
+  if (fault != CC_FAULT_NAN_GRAD || !c || at_iteration < c->iter) return CC_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  CK(cudaMemcpyAsync(&c->sc->nan_at, &at_iteration, sizeof(int), cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return CC_OK;
+}
+
 int cc_rd_cost(cc_ctx* c, int hard_round, double* D, double* R_bpp, double* cost) {
   if (!c) return CC_EINVAL;
   CK(cudaSetDevice(c->dev));
@@ -725,7 +814,7 @@ int cc_rd_cost(cc_ctx* c, int hard_round, double* D, double* R_bpp, double* cost
   if (D) *D = h.D;
   if (R_bpp) *R_bpp = h.R;
   if (cost) *cost = h.loss;
-  return std::isfinite(h.loss) ? CC_OK : CC_ENONFINITE;
+  return std::isfinite(h.loss) && !h.nonfinite ? CC_OK : CC_ENONFINITE;
 }
 
 int cc_decode(cc_ctx* c, float* rgb_out_hwc) {
@@ -746,7 +835,7 @@ int cc_decode(cc_ctx* c, float* rgb_out_hwc) {
 }
 
 int cc_forward_backward(cc_ctx* c, const float* noise_override, int hard, float* grads_out,
-                        double* D, double* R_bpp) {
+                        double* D, double* R_bpp, double* loss) {
   if (!c || hard < -1 || hard > 1) return CC_EINVAL;
   CK(cudaSetDevice(c->dev));
   int qmode = 0;
@@ -769,11 +858,12 @@ int cc_forward_backward(cc_ctx* c, const float* noise_override, int hard, float*
   if (e) return e;
   if (D) *D = h.D;
   if (R_bpp) *R_bpp = h.R;
-  return std::isfinite(h.loss) ? CC_OK : CC_ENONFINITE;
+  if (loss) *loss = h.loss;
+  return std::isfinite(h.loss) && !h.nonfinite ? CC_OK : CC_ENONFINITE;
 }
 
 int cc_get_grads(cc_ctx* c, const float* noise_override, float* grads_out) {
-  return cc_forward_backward(c, noise_override, -1, grads_out, nullptr, nullptr);
+  return cc_forward_backward(c, noise_override, -1, grads_out, nullptr, nullptr, nullptr);
 }
 
 }  // extern "C"
@@ -825,6 +915,7 @@ int cc_get_losses_async(cc_ctx* c, int first, int count, double* out) {
 int cc_set_latents(cc_ctx* c, const float* y_flat) {
   if (!c || !y_flat) return CC_EINVAL;
   CK(cudaSetDevice(c->dev));
+  CK(clear_nonfinite(c));
   return copy_latents(c, c->y, const_cast<float*>(y_flat), false);
 }
 
@@ -840,6 +931,7 @@ int cc_get_latents(cc_ctx* c, float* y_flat) {
 int cc_set_params(cc_ctx* c, const float* params) {
   if (!c || !params) return CC_EINVAL;
   CK(cudaSetDevice(c->dev));
+  CK(clear_nonfinite(c));
   CK(cudaMemcpyAsync(c->params, params, (size_t)c->lay.total * sizeof(float), cudaMemcpyDefault,
                      c->st));
   CK(rebuild_images(c, c->st));

@@ -132,7 +132,11 @@ struct IterScalars {
   double D, R, loss;
   double b1t, b2t;    // beta1^t, beta2^t, carried by repeated multiplication
   unsigned ticket;    // blocks of the latent update done (reset by the last one)
-  int pad2;
+  int nan_at;         // fault injection: the latent update of this iteration makes the
+                      // gradient of latent 0 NaN (-1: never; cc_debug_inject)
+  int nonfinite;      // set when a pass read a non-finite latent or an update produced a
+                      // non-finite latent or parameter; cleared when the host writes state
+  int pad3;
 };
 // IterScalars of iteration t, computed on the host (context set-up, state restore).
 IterScalars iter_scalars_at(int t);

@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(256) k_quantize(Geo g, const float* __restrict
     const int i = i0 + e;
     if (i >= n) break;
     const float yv = y[base + i];
+    if (!isfinite(yv)) const_cast<IterScalars*>(sc)->nonfinite = 1;
     float out;
     if (m == 1) {
       out = rintf(yv);
@@ -266,6 +267,7 @@ __device__ __forceinline__ void param_update_one(const VirtualMap& vm, const flo
   if (apply) {
     float p = params[j];
     adam_apply(p, m[j], v[j], g, st);
+    if (!isfinite(p) || !isfinite(v[j])) const_cast<IterScalars*>(sc)->nonfinite = 1;
     params[j] = p;
     const int4 d = slots.map[j];
     if (d.x >= 0) slots.arm_image[d.x] = p;
@@ -347,6 +349,7 @@ __global__ void __launch_bounds__(256) k_latent_update(Geo g, const float* __res
   const long long i = q - g.off[l];
   if (q < g.n_pad && i < (long long)g.h[l] * g.w[l]) {
     float gt = __ldg(gsyn + q) + rate_scale * __ldg(grate + q);   // dL / d y_hat
+    if (q == 0 && sc->t == sc->nan_at) gt = __int_as_float(0x7fc00000);   // injected fault
     // soft-rounding pass: dL/dy = dL/dy_hat * dy_hat/dy (1: always, 2: noise phase only)
     if (soft == 1 || (soft == 2 && sc->t < ste_start)) gt *= __ldg(dq + q);
     if (grad_out) {
@@ -361,6 +364,7 @@ __global__ void __launch_bounds__(256) k_latent_update(Geo g, const float* __res
       st.inv_sqrt_bc2 = sc->inv_sqrt_bc2;
       float yv = y[q], mv = m[q], vv = v[q];
       adam_apply(yv, mv, vv, gt, st);
+      if (!isfinite(yv) || !isfinite(vv)) sc->nonfinite = 1;
       y[q] = yv; m[q] = mv; v[q] = vv;
     }
   }
@@ -436,6 +440,7 @@ cudaError_t ctx_gather(const Geo& g, const int2* d_offsets, int N, float* gself,
 IterScalars iter_scalars_at(int t) {
   IterScalars s{};
   s.t = t;
+  s.nan_at = -1;
   s.b1t = pow(0.9, (double)t);
   s.b2t = pow(0.999, (double)t);
   s.inv_bc1 = (float)(1.0 / (1.0 - s.b1t * 0.9));

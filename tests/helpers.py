@@ -140,3 +140,45 @@ def assert_latents_close_with_ties(got, ref, level, arm_margin, syn_margin, offs
             ok = True
         assert ok, (f"level {level} ({r},{c}): {got[r, c]:.6e} vs {ref[r, c]:.6e} "
                     f"(scale {scale:.3e}) with no near-tie decision nearby")
+
+
+STATE_MAGIC, STATE_VERSION = 0x31534343, 1   # "CCS1", the header of cc_get_state
+
+
+def state_blob(d: dict, H: int, W: int, seed: int, iteration: int, y_flat, p_flat,
+               my, vy, mp, vp) -> bytes:
+    """A cc_set_state blob (include/coolchic.h) from float32 arrays in flat orders: the
+    header (magic, version, H, W, latent and parameter counts, iteration, seed, the
+    architecture fields), then y, parameters, latent m, latent v, parameter m, parameter v."""
+    import struct
+    arrays = [np.asarray(a, np.float32).ravel() for a in (y_flat, p_flat, my, vy, mp, vp)]
+    arch = [d["arm_ctx"], d["arm_layers"], d["up_kernel"], int(d["up_per_level"]),
+            d["syn_hidden"], d["syn_res3x3"], 7, 0]
+    hdr = struct.pack("<IIiiiiiiQ8i", STATE_MAGIC, STATE_VERSION, H, W, arrays[0].size,
+                      arrays[1].size, iteration, 0, seed & 0xFFFFFFFFFFFFFFFF, *arch)
+    return hdr + b"".join(a.tobytes() for a in arrays)
+
+
+def share_oracle_state(pair: Pair):
+    """Round the oracle's whole state (latents, parameters, Adam moments) to float32, put
+    the rounded values back into the oracle and load them into the CUDA context, so that
+    both continue from one identical state at the oracle's iteration."""
+    enc = pair.oracle
+    nl = len(enc.y)
+
+    def flat(ts):
+        return np.concatenate([np.asarray(t.detach().numpy(), np.float32).ravel() for t in ts])
+
+    parts = [flat(enc.tensors[:nl]), flat(enc.tensors[nl:]), flat(enc.m[:nl]), flat(enc.v[:nl]),
+             flat(enc.m[nl:]), flat(enc.v[nl:])]
+    with torch.no_grad():
+        for group, src in ((enc.tensors, parts[0:2]), (enc.m, parts[2:3] + parts[4:5]),
+                           (enc.v, parts[3:4] + parts[5:6])):
+            vals = np.concatenate(src)
+            k = 0
+            for t in group:
+                n = t.numel()
+                t.copy_(torch.from_numpy(vals[k:k + n].astype(np.float64)).reshape(t.shape))
+                k += n
+    blob = state_blob(pair.d, pair.H, pair.W, pair.seed, enc.t, *parts)
+    cc.cc_set_state(pair.ctx, blob)
