@@ -143,9 +143,15 @@ int cc_encode_iters_checked(cc_ctx* ctx, int n_iters, int check_every, int* iter
  *     cc_encode_iters_checked clears it.
  *   CC_FAULT_ALLOC (ctx NULL, at_iteration ignored): the next cc_init_image of this
  *     process that would call cudaMalloc returns CC_ENOMEM instead, once.
+ *   CC_FAULT_ARM_STALL (ctx given, at_iteration ignored): from the next pass on, every CTA
+ *     of the ARM kernel leaves out its first context load and waits for it with a budget
+ *     of about half a millisecond; the wait runs out, the kernel records the fault, waits
+ *     for its loads in flight and returns, and the call that synchronises reports
+ *     CC_ETIMEOUT.  A rollback of cc_encode_iters_checked clears it.
  * CC_EINVAL for any other combination. */
 #define CC_FAULT_NAN_GRAD 1
 #define CC_FAULT_ALLOC 2
+#define CC_FAULT_ARM_STALL 3
 int cc_debug_inject(cc_ctx* ctx, int fault, int at_iteration);
 
 /* Rate-distortion cost of the current state, eq. (1): D = mean squared error over the

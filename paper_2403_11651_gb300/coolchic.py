@@ -297,7 +297,7 @@ def cc_encode_iters_checked(ctx, n_iters: int, check_every: int):
     return code, done.value
 
 
-CC_FAULT_NAN_GRAD, CC_FAULT_ALLOC = 1, 2
+CC_FAULT_NAN_GRAD, CC_FAULT_ALLOC, CC_FAULT_ARM_STALL = 1, 2, 3
 
 
 def cc_debug_inject(ctx, fault: int, at_iteration: int = 0):

@@ -8,24 +8,25 @@
 // One thread owns one latent; a tile is 128 latents of one level (kArmTile).  The weights
 // live in a __constant__ bank refreshed before every pass.
 //
-// Forward and backward (the encoder iteration), k_arm_tc: the N x N layers of the forward
-// pass (z = W h + b) and of the input gradient (dh += W^T dz) run on the tensor cores
-// (tcgen05.mma kind::tf32 with operands split into TF32 high and low parts, FP32
-// accumulation in tensor memory, cc_tc.cuh): M = the 128 latents of the tile, N = the
-// layer width padded to a multiple of 16, K = N.  Each thread writes its latent's row of
-// the A operand to shared memory and reads its row of the result back from its lane of
-// the tensor memory.  The output layer (N -> 2), the Laplace rate and the weight gradients
-// (sums over latents of dz (x) input: RB x RB register blocks of packed FP32 pairs over
-// fp32 rows in shared memory, kept in registers over the CTA's tiles) run on the CUDA
-// cores.  Every sum has a fixed order, so results are bit-reproducible on a given device.
+// Forward and backward (the encoder iteration), k_arm_fb: one persistent loop over tiles of
+// 4 x 32 latents, three CTAs of 128 threads per SM.  A tile's causal context (8 x 40
+// floats of the zero-bordered y_hat plane) arrives by TMA, issued one tile ahead into a
+// double buffer.  The N x N layers of the forward pass and of the input gradient run as
+// packed FP32 pairs whose weight pairs come from the constant bank; the output layer, the
+// Laplace rate, then the weight gradients (sums over latents of dz (x) input: RB x RB
+// register blocks of packed pairs over the tile's rows staged in shared memory, kept in
+// registers over the CTA's tiles).  Every sum has a fixed order, so results are
+// bit-reproducible on a given device.
 //
-// Forward only (rate of a pass without gradients), k_arm_fwd: every layer on the CUDA
-// cores, weights as constant-bank operands in packed FP32 pairs.
+// Forward only (rate of a pass without gradients), k_arm_fwd: the same layers without the
+// backward half.
 #include "cc_internal.cuh"
 #include "cc_laplace.cuh"
 #include "cc_tc.cuh"
 
 #include <cudaTypedefs.h>
+
+#include <cstdlib>
 
 namespace cc {
 
@@ -54,7 +55,8 @@ struct ArmArgs {
   float* part_bits;  // [gridDim.x]
   const int2* tiles; // (level, first latent of the tile within the level)
   int n_tiles;
-  int* fault;        // set when a tensor-core wait gives up
+  int* fault;        // set when a context-load wait gives up
+  const int* stall;  // > 0: skip the first context load and wait this many cycles for it
   Geo g;
 };
 
@@ -177,140 +179,64 @@ __global__ void __launch_bounds__(kArmTile) k_arm_fwd(ArmArgs a) {
   }
 }
 
-// ------------------------------------------------------------ forward + backward (tensor cores)
-
-template <int N, int NL>
-struct ArmTcShape {
-  static constexpr int T = kArmTile;            // latents per tile = threads per CTA
-  static constexpr int NP = (N + 15) / 16 * 16; // MMA N: the layer width padded
-  static constexpr int KS = N / 8;              // K steps of 8
-  static constexpr int LW = N * N + N;          // floats per LinR layer (W then b)
-  static constexpr int OW = NL * LW;            // W_out
-  static constexpr int OB = OW + 2 * N;         // b_out
-  static constexpr int NP_ARM = OB + 2;         // ARM parameters
-  static constexpr int S = N;                   // fp32 row stride of the weight-gradient rows
-  static constexpr int LS = T * S + 8;          // per-layer arrays (8-float bank skew)
-  // bytes: A operand (hi, lo), then per layer W (hi, lo) and W^T (hi, lo), NP rows each
-  static constexpr int A_BYTES = T * N * 4;
-  static constexpr int W_BYTES = NP * N * 4;
-  static constexpr int TC_BYTES = 2 * A_BYTES + NL * 4 * W_BYTES;
-  // floats after the operands: s_in [NL][LS], s_dz [NL][LS], s_ho [T][S], s_do [T][2]
-  static constexpr int F_FLOATS = 2 * NL * LS + T * S + 2 * T;
-  static constexpr int NBLK = NL * ArmBlocking<N>::NB * ArmBlocking<N>::NB;
-  static constexpr int G = T / NBLK;            // interleaved latent groups
-  static constexpr int NCH_B = NL * N / 4;      // bias chunks of 4
-  static constexpr int NCH = NCH_B + N / 4;     // + W_out column chunks (b_out rides on #0)
-  static constexpr int XPER = (NCH + NBLK - 1) / NBLK;
-  static constexpr int RED_FLOATS = G * NP_ARM;
-  static constexpr int BYTES_MAIN = TC_BYTES + F_FLOATS * 4;
-  static constexpr int BYTES = (BYTES_MAIN > RED_FLOATS * 4 ? BYTES_MAIN : RED_FLOATS * 4) + 16;
-  static constexpr uint32_t TMEM_COLS = 32;
-  static_assert(T % NBLK == 0 && G >= 1, "threads must split evenly into weight blocks");
-  static_assert(N % 8 == 0 && NP <= 32, "tensor-core ARM widths: 8, 16, 24");
-};
-
-// wait budget of a tensor-core phase (SM clocks, about half a second)
+// wait budget of a context load (SM clocks, about half a second)
 constexpr long long kTcWaitCycles = 1ll << 30;
 
+// ------------------------------------------------------------ forward + backward (CUDA cores)
+//
+// Measured alone on all SMs at 512 x 768 with the 24-input ARM (GB300): 104 us.  Three
+// alternatives were slower: the N x N layers on tcgen05 tensor cores (TF32 x 3, a chain of
+// four MMA round trips per tile, two CTAs per SM): 121 us; scalar FMAs with constant-bank
+// operands: 120 us (weights beyond what the immediate-constant cache holds are fetched
+// one by one) and 146 us rolled over the inputs.
+
 template <int N, int NL>
-__global__ void __launch_bounds__(kArmTile, 2) k_arm_tc(ArmArgs a, const __grid_constant__ ArmMaps maps) {
+struct ArmFbShape {
+  static constexpr int T = kArmTile;
+  static constexpr int LW = N * N + N, OW = NL * LW, OB = OW + 2 * N, NP_ARM = OB + 2;
+  static constexpr int S = N;                     // row stride of the staged rows
+  static constexpr int LS = T * S + 8;            // per-layer arrays (8-float bank skew)
+  static constexpr int F_FLOATS = 2 * NL * LS + T * S + 2 * T;
+  static constexpr int NBLK = NL * ArmBlocking<N>::NB * ArmBlocking<N>::NB;
+  static constexpr int G = T / NBLK;
+  static constexpr int NCH_B = NL * N / 4;
+  static constexpr int NCH = NCH_B + N / 4;
+  static constexpr int XPER = (NCH + NBLK - 1) / NBLK;
+  static constexpr int RED_FLOATS = G * NP_ARM;
+  static constexpr int BYTES = (F_FLOATS > RED_FLOATS ? F_FLOATS : RED_FLOATS) * 4;
+  static_assert(T % NBLK == 0 && G >= 1, "threads must split evenly into weight blocks");
+};
+constexpr int kArmFbBlocksPerSm = 3;
+
+template <int N, int NL>
+__global__ void __launch_bounds__(kArmTile, kArmFbBlocksPerSm)
+k_arm_fb(ArmArgs a, const __grid_constant__ ArmMaps maps) {
   pdl_wait();
   pdl_trigger();
-  using Sh = ArmTcShape<N, NL>;
-  constexpr int T = Sh::T, NP = Sh::NP, KS = Sh::KS, LW = Sh::LW, OW = Sh::OW, OB = Sh::OB;
-  constexpr int S = Sh::S, LS = Sh::LS, NPA = Sh::NP_ARM;
+  using Sh = ArmFbShape<N, NL>;
+  constexpr int T = Sh::T, LW = Sh::LW, OW = Sh::OW, OB = Sh::OB, NPA = Sh::NP_ARM;
+  constexpr int S = Sh::S, LS = Sh::LS;
   constexpr int RB = ArmBlocking<N>::RB, NB = ArmBlocking<N>::NB;
   constexpr int NBLK = Sh::NBLK, G = Sh::G, NCH_B = Sh::NCH_B, NCH = Sh::NCH, XPER = Sh::XPER;
-  constexpr uint32_t SBO_A = (N / 4) * 128;
-  constexpr uint32_t IDESC = tc_idesc_tf32(T, NP);
 
-  extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* sA_hi = smem;
-  unsigned char* sA_lo = sA_hi + Sh::A_BYTES;
-  unsigned char* sW = sA_lo + Sh::A_BYTES;   // [L][W hi, W lo, W^T hi, W^T lo]
-  float* sf = reinterpret_cast<float*>(smem + Sh::TC_BYTES);
+  extern __shared__ __align__(16) float sf[];
   float* s_in = sf;                  // [NL][T][S] input of LinR layer L (layer stride LS)
   float* s_dz = s_in + NL * LS;      // [NL][T][S] dz of LinR layer L
   float* s_ho = s_dz + NL * LS;      // [T][S]     input of the output layer
   float* s_do = s_ho + T * S;        // [T][2]     (d bits/d mu, d bits/d s)
-  __shared__ __align__(8) uint64_t s_mbar;
-  __shared__ uint32_t s_tmem;
-  // causal context of a tile, loaded by TMA (double-buffered): rows y0 - kCtxPad .. y0 + 3,
-  // columns x0 - kCtxPad .. x0 + 35 of the level (zeros outside it)
   constexpr int HR = kArmTileY + kCtxPad, HC = kArmTileX + 2 * kCtxPad;
   constexpr uint32_t HALO_BYTES = HR * HC * 4;
   __shared__ __align__(128) float s_halo[2][HR * HC];
   __shared__ __align__(8) uint64_t s_tbar[2];
 
   const int tid = threadIdx.x;
-  const int warp = tid >> 5;
-  // weights as B operands: W (K = input, rows = outputs) and W^T, split into TF32 parts;
-  // rows N .. NP-1 are zero
-  for (int i = tid; i < NL * NP * N; i += T) {
-    const int L = i / (NP * N), rk = i - L * NP * N, row = rk / N, k = rk - row * N;
-    const float wf = row < N ? c_armb[L * LW + row * N + k] : 0.f;   // W[row][k]
-    const float wt = row < N ? c_armb[L * LW + k * N + row] : 0.f;   // W^T[row][k] = W[k][row]
-    const float fh = tf32_hi(wf), th = tf32_hi(wt);
-    unsigned char* base = sW + L * 4 * Sh::W_BYTES;
-    const int off = tc_off(row, k, N);
-    *reinterpret_cast<float*>(base + off) = fh;
-    *reinterpret_cast<float*>(base + Sh::W_BYTES + off) = wf - fh;
-    *reinterpret_cast<float*>(base + 2 * Sh::W_BYTES + off) = th;
-    *reinterpret_cast<float*>(base + 3 * Sh::W_BYTES + off) = wt - th;
-  }
   if (tid == 0) {
-    mbar_init(smem_u32(&s_mbar), 1);
     mbar_init(smem_u32(&s_tbar[0]), 1);
     mbar_init(smem_u32(&s_tbar[1]), 1);
   }
-  if (warp == 0) tc_alloc(smem_u32(&s_tmem), Sh::TMEM_COLS);
-  fence_async_smem();
-  tc_fence_before();
   __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = s_tmem;
-  const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's lanes
-  const uint32_t mbar = smem_u32(&s_mbar);
-  uint32_t phase = 0;
 
-  // Stage the A operand (this thread's row, split), run D = A B^T for B = layer L's W
-  // (transpose = false) or W^T (true), and return this thread's row of D.  False when a
-  // wait gave up (the CTA then stops).
-  auto layer_mma = [&](const float (&x)[N], int L, bool transpose, float (&d)[NP]) -> bool {
-#pragma unroll
-    for (int k = 0; k < N; k += 4) {
-      const float4 hi = make_float4(tf32_hi(x[k]), tf32_hi(x[k + 1]), tf32_hi(x[k + 2]),
-                                    tf32_hi(x[k + 3]));
-      const float4 lo = make_float4(x[k] - hi.x, x[k + 1] - hi.y, x[k + 2] - hi.z, x[k + 3] - hi.w);
-      *reinterpret_cast<float4*>(sA_hi + tc_off(tid, k, N)) = hi;
-      *reinterpret_cast<float4*>(sA_lo + tc_off(tid, k, N)) = lo;
-    }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t ah = smem_u32(sA_hi), al = smem_u32(sA_lo);
-      const uint32_t wb = smem_u32(sW + L * 4 * Sh::W_BYTES + (transpose ? 2 : 0) * Sh::W_BYTES);
-      const uint32_t bh = wb, bl = wb + Sh::W_BYTES;
-#pragma unroll
-      for (int s = 0; s < KS; ++s) {
-        const uint32_t ko = (uint32_t)s * 256u;
-        tc_mma_tf32(tmem, tc_desc(ah + ko, SBO_A), tc_desc(bh + ko, SBO_A), IDESC, s > 0 ? 1u : 0u);
-        tc_mma_tf32(tmem, tc_desc(ah + ko, SBO_A), tc_desc(bl + ko, SBO_A), IDESC, 1u);
-        tc_mma_tf32(tmem, tc_desc(al + ko, SBO_A), tc_desc(bh + ko, SBO_A), IDESC, 1u);
-      }
-      tc_commit(mbar);
-    }
-    const bool ok = mbar_wait(mbar, phase, kTcWaitCycles);
-    phase ^= 1u;
-    if (__syncthreads_or(ok ? 0 : 1)) return false;   // every thread takes the same branch
-    tc_fence_after();
-    tc_ld_row<NP>(t_row, d);
-    return true;
-  };
-
-  float2 acc[RB][RB / 2];   // weight-gradient block as packed pairs along its columns
+  float2 acc[RB][RB / 2];
   float xacc[XPER][10];
 #pragma unroll
   for (int r = 0; r < RB; ++r)
@@ -325,8 +251,6 @@ __global__ void __launch_bounds__(kArmTile, 2) k_arm_tc(ArmArgs a, const __grid_
   float bits_acc = 0.f;
   bool ok = true;
 
-  // TMA of a tile's context into halo buffer `buf` (thread 0): the buffer's earlier
-  // readers are ordered before the asynchronous write by a barrier and this fence
   auto issue = [&](int t, int buf) {
     const int2 tq = a.tiles[t];
     fence_async_smem();
@@ -334,17 +258,25 @@ __global__ void __launch_bounds__(kArmTile, 2) k_arm_tc(ArmArgs a, const __grid_
     mbar_expect_tx(bar, HALO_BYTES);
     tma_load_2d(smem_u32(&s_halo[buf][0]), &maps.m[tq.x], tq.y & 0xFFFF, tq.y >> 16, bar);
   };
-  if (tid == 0 && (int)blockIdx.x < a.n_tiles) issue(blockIdx.x, 0);
+  // fault injection (host-requested): the first load is not issued, so its wait runs out
+  const int stall = *a.stall;
+  const long long budget = stall > 0 ? (long long)stall : kTcWaitCycles;
+  // bit b: a load issued into buffer b and not yet waited for
+  unsigned inflight = 0u;
+  if ((int)blockIdx.x < a.n_tiles && stall <= 0) {
+    if (tid == 0) issue(blockIdx.x, 0);
+    inflight |= 1u;
+  }
   int it = 0;
-  bool pending = (int)blockIdx.x < a.n_tiles;   // a load in flight into buffer it & 1
-  for (int tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x, ++it) {
+  for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
     const int buf = it & 1;
-    // the next tile's context goes to the other buffer, read during the previous tile
-    const bool more = tile + (int)gridDim.x < a.n_tiles;
-    if (tid == 0 && more) issue(tile + gridDim.x, buf ^ 1);
-    const bool hok = mbar_wait(smem_u32(&s_tbar[buf]), (uint32_t)(it >> 1) & 1u, kTcWaitCycles);
+    if (tile + (int)gridDim.x < a.n_tiles) {
+      if (tid == 0) issue(tile + gridDim.x, buf ^ 1);
+      inflight |= 1u << (buf ^ 1);
+    }
+    const bool hok = mbar_wait(smem_u32(&s_tbar[buf]), (uint32_t)(it >> 1) & 1u, budget);
     if (__syncthreads_or(hok ? 0 : 1)) { ok = false; break; }
-    pending = more;
+    inflight &= ~(1u << buf);
     const int2 td = a.tiles[tile];
     int ly, lx;
     tile_latent(td, tid, ly, lx);
@@ -358,47 +290,76 @@ __global__ void __launch_bounds__(kArmTile, 2) k_arm_tc(ArmArgs a, const __grid_
     }
     const float yq = valid ? hb[0] : 0.f;
 
-    // forward: h <- h + relu(W h + b), NL times
+    // forward: h <- h + relu(W h + b), NL times; every weight is the constant-bank operand
+    // of a scalar FMA (packed pairs with a constant-bank pair operand measured 3x slower)
     uint32_t mask[NL];
 #pragma unroll
     for (int L = 0; L < NL; ++L) {
       store_row<N>(s_in + L * LS + tid * S, h);
-      float z[NP];
-      if (!layer_mma(h, L, false, z)) { ok = false; break; }
+      // packed FP32 pairs over adjacent outputs, the weight pair (W[2m][k], W[2m+1][k])
+      // read from the forward copy of the bank
+      float z[N];
+      {
+        const float2* wp = reinterpret_cast<const float2*>(c_arm + L * LW);
+        float2 zp[N / 2];
+#pragma unroll
+        for (int m = 0; m < N / 2; ++m) zp[m] = wp[N * N / 2 + m];   // bias pair
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          const float2 hk = make_float2(h[k], h[k]);
+#pragma unroll
+          for (int m = 0; m < N / 2; ++m) zp[m] = __ffma2_rn(wp[m * N + k], hk, zp[m]);
+        }
+#pragma unroll
+        for (int m = 0; m < N / 2; ++m) { z[2 * m] = zp[m].x; z[2 * m + 1] = zp[m].y; }
+      }
       uint32_t mk = 0;
 #pragma unroll
       for (int o = 0; o < N; ++o) {
-        const float zo = z[o] + c_armb[L * LW + N * N + o];
-        mk |= (zo > 0.f ? 1u : 0u) << o;
-        h[o] += fmaxf(zo, 0.f);
+        mk |= (z[o] > 0.f ? 1u : 0u) << o;
+        h[o] += fmaxf(z[o], 0.f);
       }
       mask[L] = mk;
     }
-    if (!ok) break;
     store_row<N>(s_ho + tid * S, h);
-    const float2 ms = output_layer<N, NL>(h);
-    LapOut lo = laplace_bits(yq, ms.x, ms.y);
+    // the forward reads the bank copy `w`, the backward the row-major copy `wb`: a weight
+    // read by both from one copy is kept in a register between its two uses, and with
+    // 1250 weights that pushes the rest out to separate loads
+    float mu = c_arm[OB], sl = c_arm[OB + 1];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      mu = fmaf(c_arm[OW + 2 * k], h[k], mu);
+      sl = fmaf(c_arm[OW + 2 * k + 1], h[k], sl);
+    }
+    LapOut lo = laplace_bits(yq, mu, sl);
     if (!valid) lo.bits = lo.g_y = lo.g_mu = lo.g_s = 0.f;
     bits_acc += lo.bits;
 
-    // backward: dh = W_out^T (d mu, d s), then dh += W_L^T (mask_L * dh) for L = NL-1 .. 0
+    // backward: dh = W_out^T (d mu, d s), then dh += W_L^T (mask_L * dh), L = NL-1 .. 0
     reinterpret_cast<float2*>(s_do)[tid] = make_float2(lo.g_mu, lo.g_s);
     float dh[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k)
-      dh[k] = fmaf(c_armb[OW + k], lo.g_mu, c_armb[OW + N + k] * lo.g_s);
+    for (int k = 0; k < N; ++k) dh[k] = fmaf(c_armb[OW + k], lo.g_mu, c_armb[OW + N + k] * lo.g_s);
 #pragma unroll
     for (int L = NL - 1; L >= 0; --L) {
       float dz[N];
 #pragma unroll
       for (int o = 0; o < N; ++o) dz[o] = ((mask[L] >> o) & 1u) ? dh[o] : 0.f;
       store_row<N>(s_dz + L * LS + tid * S, dz);
-      float t[NP];
-      if (!layer_mma(dz, L, true, t)) { ok = false; break; }
+      // packed pairs over adjacent inputs, (W[o][2j], W[o][2j+1]) from the row-major copy
+      const float2* wr = reinterpret_cast<const float2*>(c_armb + L * LW);
+      float2 dhp[N / 2];
 #pragma unroll
-      for (int k = 0; k < N; ++k) dh[k] += t[k];
+      for (int j = 0; j < N / 2; ++j) dhp[j] = make_float2(dh[2 * j], dh[2 * j + 1]);
+#pragma unroll
+      for (int o = 0; o < N; ++o) {
+        const float2 d2 = make_float2(dz[o], dz[o]);
+#pragma unroll
+        for (int j = 0; j < N / 2; ++j) dhp[j] = __ffma2_rn(wr[o * (N / 2) + j], d2, dhp[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < N / 2; ++j) { dh[2 * j] = dhp[j].x; dh[2 * j + 1] = dhp[j].y; }
     }
-    if (!ok) break;
     if (valid) {
       const long long qq = a.g.off[td.x] + (long long)ly * a.g.w[td.x] + lx;
 #pragma unroll
@@ -453,20 +414,18 @@ __global__ void __launch_bounds__(kArmTile, 2) k_arm_tc(ArmArgs a, const __grid_
   }
 
   if (!ok) {
-    // a tensor-core wait gave up: report, give the MMAs in flight another bounded wait,
-    // free the tensor memory and stop
+    // a context wait gave up at iteration it: report, give every load still in flight
+    // another bounded wait (nothing may land in shared memory after the CTA has left) and
+    // stop.  Buffer it & 1 has completed it >> 1 phases, the other (it + 1) >> 1.
     if (tid == 0) atomicExch(a.fault, 1);
-    mbar_wait(mbar, phase ^ 1u, kTcWaitCycles);
-    if (pending)   // the context load still in flight
-      mbar_wait(smem_u32(&s_tbar[(it + 1) & 1]), (uint32_t)((it + 1) >> 1) & 1u, kTcWaitCycles);
-    tc_fence_before();
+    const int b = it & 1;
+    if (inflight & (1u << b))
+      mbar_wait(smem_u32(&s_tbar[b]), (uint32_t)(it >> 1) & 1u, kTcWaitCycles);
+    if (inflight & (1u << (b ^ 1)))
+      mbar_wait(smem_u32(&s_tbar[b ^ 1]), (uint32_t)((it + 1) >> 1) & 1u, kTcWaitCycles);
     __syncthreads();
-    if (warp == 0) tc_dealloc(tmem, Sh::TMEM_COLS);
     return;
   }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) tc_dealloc(tmem, Sh::TMEM_COLS);
 
   // rate partial of this CTA
   {
@@ -474,7 +433,7 @@ __global__ void __launch_bounds__(kArmTile, 2) k_arm_tc(ArmArgs a, const __grid_
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     __shared__ float s_bits[T / 32];
-    if ((tid & 31) == 0) s_bits[warp] = v;
+    if ((tid & 31) == 0) s_bits[tid >> 5] = v;
     __syncthreads();
     if (tid == 0) {
       float t = 0.f;
@@ -484,7 +443,7 @@ __global__ void __launch_bounds__(kArmTile, 2) k_arm_tc(ArmArgs a, const __grid_
     }
   }
   // every (group, parameter) slot is written exactly once, then summed over groups
-  float* red = reinterpret_cast<float*>(smem);
+  float* red = sf;
   float* mine = red + grp * NPA;
 #pragma unroll
   for (int rr = 0; rr < RB; ++rr)
@@ -522,7 +481,7 @@ template <int N, int NL>
 static cudaError_t launch_t(bool bwd, const ArmArgs& a, const ArmMaps& maps, int grid,
                             cudaStream_t st) {
   if (bwd) {
-    k_arm_tc<N, NL><<<grid, kArmTile, ArmTcShape<N, NL>::BYTES, st>>>(a, maps);
+    k_arm_fb<N, NL><<<grid, kArmTile, ArmFbShape<N, NL>::BYTES, st>>>(a, maps);
   } else {
     k_arm_fwd<N, NL><<<grid, kArmTile, 0, st>>>(a);
   }
@@ -531,13 +490,13 @@ static cudaError_t launch_t(bool bwd, const ArmArgs& a, const ArmMaps& maps, int
 
 template <int N, int NL>
 static cudaError_t prepare_t() {
-  return cudaFuncSetAttribute(k_arm_tc<N, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              ArmTcShape<N, NL>::BYTES);
+  return cudaFuncSetAttribute(k_arm_fb<N, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              ArmFbShape<N, NL>::BYTES);
 }
 
 template <int N, int NL>
 static size_t smem_t(bool bwd) {
-  return bwd ? (size_t)ArmTcShape<N, NL>::BYTES : 0;
+  return bwd ? (size_t)ArmFbShape<N, NL>::BYTES : 0;
 }
 
 #define CC_ARM_DISPATCH(FN, ...)                                              \
@@ -554,10 +513,11 @@ static size_t smem_t(bool bwd) {
 cudaError_t arm_launch(const Arch& a, bool backward, const float* yhat, const Geo& g,
                        const ArmMaps& maps, const int2* tiles, int n_tiles, int grid,
                        float* dctx, float* gself, float* part_grad, float* part_bits,
-                       int* fault, cudaStream_t st) {
+                       int* fault, const int* stall, cudaStream_t st) {
   ArmArgs k;
   k.yhat = yhat; k.dctx = dctx; k.gself = gself; k.part_grad = part_grad;
-  k.part_bits = part_bits; k.tiles = tiles; k.n_tiles = n_tiles; k.fault = fault; k.g = g;
+  k.part_bits = part_bits; k.tiles = tiles; k.n_tiles = n_tiles; k.fault = fault;
+  k.stall = stall; k.g = g;
   CC_ARM_DISPATCH(launch_t, backward, k, maps, grid, st);
   return cudaErrorInvalidValue;
 }
@@ -598,12 +558,12 @@ size_t arm_smem_bytes(const Arch& a, bool backward) {
   return 0;
 }
 
-// two CTAs of the tensor-core kernel fit an SM (shared memory); the forward-only kernel
-// runs on the same grid
+// CTAs per SM of the backward kernel (its shared memory and registers allow three); the
+// forward-only kernel runs on the same grid
 int arm_blocks_per_sm(const Arch& a, bool backward) {
   (void)a;
   (void)backward;
-  return 2;
+  return kArmFbBlocksPerSm;
 }
 
 __global__ void k_arm_image(const float* __restrict__ params, int n_arm,

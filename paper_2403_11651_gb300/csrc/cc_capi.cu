@@ -406,7 +406,8 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
   };
   if (fork) CKE(record_on_side(c->ev_a0));
   CKE(arm_launch(a, backward, c->yhat_bord, c->geo, c->maps, c->tiles, c->n_tiles, c->grid_arm,
-                 c->dctx, c->gself, c->part_arm, c->part_bits, &c->sc->fault, sa));
+                 c->dctx, c->gself, c->part_arm, c->part_bits, &c->sc->fault,
+                 &c->sc->arm_stall, sa));
   if (fork) CKE(record_on_side(c->ev_a1));
   if (fork) CKE(cudaEventRecord(c->ev_arm, sa));
   // the context gather follows the ARM on its stream; timed per phase it runs after the
@@ -633,7 +634,7 @@ int sync_copy_scalars(cc_ctx* c, IterScalars* h) {
   CK(cudaMemcpyAsync(h, c->sc, sizeof(IterScalars), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   if (h->fault) {
-    set_error_text("a tensor-core wait of the ARM kernel gave up; results are invalid");
+    set_error_text("a context-load wait of the ARM kernel gave up; results are invalid");
     return CC_ETIMEOUT;
   }
   return CC_OK;
@@ -780,6 +781,7 @@ int cc_encode_iters_checked(cc_ctx* c, int n_iters, int check_every, int* iters_
       const int never = -1, zero = 0;
       CK(cudaMemcpyAsync(&c->sc->nan_at, &never, sizeof(int), cudaMemcpyHostToDevice, c->st));
       CK(cudaMemcpyAsync(&c->sc->fault, &zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemcpyAsync(&c->sc->arm_stall, &zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
       CK(clear_nonfinite(c));
       CK(rebuild_images(c, c->st));
       CK(cudaStreamSynchronize(c->st));
@@ -795,6 +797,14 @@ int cc_debug_inject(cc_ctx* c, int fault, int at_iteration) {
   if (fault == CC_FAULT_ALLOC) {
     if (c) return CC_EINVAL;
     g_fail_next_alloc = true;
+    return CC_OK;
+  }
+  if (fault == CC_FAULT_ARM_STALL) {
+    if (!c) return CC_EINVAL;
+    CK(cudaSetDevice(c->dev));
+    const int cycles = 1 << 20;   // about half a millisecond
+    CK(cudaMemcpyAsync(&c->sc->arm_stall, &cycles, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
     return CC_OK;
   }
   if (fault != CC_FAULT_NAN_GRAD || !c || at_iteration < c->iter) return CC_EINVAL;

@@ -128,7 +128,7 @@ struct IterScalars {
   int t;              // index of the current iteration (0-based)
   float inv_bc1;      // Adam 1 / (1 - beta1^(t+1)) of the current update
   float inv_sqrt_bc2; // Adam 1 / sqrt(1 - beta2^(t+1))
-  int fault;          // set when a bounded tensor-core wait of the ARM kernel gave up
+  int fault;          // set when a bounded context-load wait of the ARM kernel gave up
   double D, R, loss;
   double b1t, b2t;    // beta1^t, beta2^t, carried by repeated multiplication
   unsigned ticket;    // blocks of the latent update done (reset by the last one)
@@ -136,7 +136,8 @@ struct IterScalars {
                       // gradient of latent 0 NaN (-1: never; cc_debug_inject)
   int nonfinite;      // set when a pass read a non-finite latent or an update produced a
                       // non-finite latent or parameter; cleared when the host writes state
-  int pad3;
+  int arm_stall;      // fault injection: > 0 makes the ARM kernel skip its first context
+                      // load and wait that many cycles for it (cc_debug_inject)
 };
 // IterScalars of iteration t, computed on the host (context set-up, state restore).
 IterScalars iter_scalars_at(int t);
@@ -168,7 +169,7 @@ cudaError_t arm_make_maps(const Geo& g, const float* yhat_bord, ArmMaps* out);
 cudaError_t arm_launch(const Arch& a, bool backward, const float* yhat, const Geo& g,
                        const ArmMaps& maps, const int2* tiles, int n_tiles, int grid,
                        float* dctx, float* gself, float* part_grad, float* part_bits,
-                       int* fault, cudaStream_t st);
+                       int* fault, const int* stall, cudaStream_t st);
 int arm_blocks_per_sm(const Arch& a, bool backward);
 cudaError_t arm_prepare(const Arch& a);   // kernel attributes; call once before capture
 size_t arm_smem_bytes(const Arch& a, bool backward);
