@@ -33,9 +33,9 @@ UNIT = "Mpixel-iter/s"
 PAPER_DERIVED_MPXIT = 22.5   # 512x768, 2300-MAC, 102 950 iterations in ~30 min (Sec. V, Fig. 5)
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one launch of the ARM kernel on this workload, from the ncu
-# capture summarised in profiles/k_arm_tc_512x768.md; None when the kernel has changed
-# since the counters were taken
-ARM_DRAM_BYTES_PER_LAUNCH = 2242048 + 579840
+# capture summarised in profiles/k_arm_fb_512x768.md (the kernel as built from the source
+# of that capture); None when the kernel has changed since the counters were taken
+ARM_DRAM_BYTES_PER_LAUNCH = None
 
 
 def dist_env():
@@ -465,9 +465,10 @@ def run_ours(a, cfgd):
         "warmup": a.warmup, "ms_per_step": it_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": value / PAPER_DERIVED_MPXIT / world if world else None,
         "dtype": "f32", "data": "synthetic", "config": workload(cfgd),
-        "roofline": {"bound": "alu", "kernel": "k_arm_tc<24,2> (ARM + rate, fwd+bwd)",
+        "roofline": {"bound": "alu", "kernel": "k_arm_fb<24,2> (ARM + rate, fwd+bwd)",
                      "achieved": arm_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": arm_tflops / peak_tflops, "traffic": ARM_DRAM_BYTES_PER_LAUNCH,
+                     "whole_iteration_frac": 6 * kappa * H * W / (it_ms / 1e3) / 1e12 / peak_tflops,
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {clk_max:.0f} MHz "
                                    f"(sm_max_mhz, {src}); the kernel's CTAs share the SMs "
                                    f"with the synthesis chain",
