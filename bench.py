@@ -35,7 +35,7 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one launch of the ARM kernel on this workload, from the ncu
 # capture summarised in profiles/k_arm_fb_512x768.md (the kernel as built from the source
 # of that capture); None when the kernel has changed since the counters were taken
-ARM_DRAM_BYTES_PER_LAUNCH = None
+ARM_DRAM_BYTES_PER_LAUNCH = 2257664 + 932096
 
 
 def dist_env():

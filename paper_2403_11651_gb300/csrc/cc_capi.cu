@@ -169,7 +169,7 @@ struct cc_ctx {
   double* log;
   UpPlan up;
   std::vector<int2> h_tiles, h_offs;
-  int n_tiles = 0, grid_arm = 0, grid_syn = 0, grid_tiles = 0, slices = 16, n_virtual = 0;
+  int n_tiles = 0, grid_arm = 0, grid_syn = 0, grid_tiles = 0, slices = kSlices, n_virtual = 0;
   SectionTable tab;
   ArmMaps maps;   // tensor maps of the zero-bordered y_hat planes (ARM context tiles)
   cudaGraphExec_t g1 = nullptr, g16 = nullptr;

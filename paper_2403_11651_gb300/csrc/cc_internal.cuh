@@ -15,6 +15,7 @@ constexpr int kArmTile = 128;     // latents per ARM tile (= threads per ARM blo
 constexpr int kArmTileY = 4, kArmTileX = 32;   // an ARM tile: 4 rows x 32 latents of a level
 constexpr int kPixTile = 256;     // pixels per synthesis block
 constexpr int kLogCap = 4096;     // per-iteration loss log entries kept on the device
+constexpr int kSlices = 16;       // slices of the first stage of the parameter-gradient sums
 
 // Latent pyramid geometry.  Every latent-shaped buffer holds the L planes back to back,
 // each plane row-major with row stride w_l, starting at a 32-float aligned offset.

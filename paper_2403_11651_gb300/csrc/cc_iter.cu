@@ -106,20 +106,38 @@ cudaError_t quantize_launch(const Geo& g, const float* y, float* yhat, float* yh
 }
 
 // part2[slice][col0 + j] = scale * sum over the slice's rows of part[row][j], rows summed
-// in a fixed tree (8 interleaved sequential sums, then those 8 in order).
+// in a fixed tree (8 interleaved sequential sums, then those 8 in order).  blockIdx.x runs
+// over the (section, chunk of 32 columns) pairs of the table only; each thread issues all
+// loads of its rows before adding them.
 __global__ void __launch_bounds__(256) k_reduce_sections(SectionTable tab, float* part2,
                                                          int n_virtual) {
   pdl_wait();
   pdl_trigger();
-  const Section s = tab.s[blockIdx.z];
-  const int j = blockIdx.x * 32 + threadIdx.x;
+  int sec = 0, chunk = blockIdx.x;
+  while (sec + 1 < tab.n && chunk >= (tab.s[sec].cols + 31) / 32) {
+    chunk -= (tab.s[sec].cols + 31) / 32;
+    ++sec;
+  }
+  const Section s = tab.s[sec];
+  const int j = chunk * 32 + threadIdx.x;
   const int slices = gridDim.y, slice = blockIdx.y;
   const int rps = (s.rows + slices - 1) / slices;
   const int r0 = slice * rps;
   const int r1 = min(s.rows, r0 + rps);
   float acc = 0.f;
-  if (j < s.cols)
-    for (int r = r0 + (int)threadIdx.y; r < r1; r += 8) acc += s.part[(long long)r * s.stride + j];
+  if (j < s.cols) {
+    constexpr int B = 8;   // rows in flight per thread
+    for (int rb = r0 + (int)threadIdx.y; rb < r1; rb += 8 * B) {
+      float v[B];
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        const int r = rb + 8 * q;
+        v[q] = r < r1 ? s.part[(long long)r * s.stride + j] : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < B; ++q) acc += v[q];
+    }
+  }
   __shared__ float sm[8][33];
   sm[threadIdx.y][threadIdx.x] = acc;
   __syncthreads();
@@ -133,9 +151,9 @@ __global__ void __launch_bounds__(256) k_reduce_sections(SectionTable tab, float
 
 cudaError_t reduce_sections(const SectionTable& tab, float* part2, int n_virtual, int slices,
                             cudaStream_t st) {
-  int maxc = 0;
-  for (int i = 0; i < tab.n; ++i) maxc = tab.s[i].cols > maxc ? tab.s[i].cols : maxc;
-  dim3 grid((maxc + 31) / 32, slices, tab.n);
+  int chunks = 0;
+  for (int i = 0; i < tab.n; ++i) chunks += (tab.s[i].cols + 31) / 32;
+  dim3 grid(chunks, slices);
   k_reduce_sections<<<grid, dim3(32, 8), 0, st>>>(tab, part2, n_virtual);
   return cudaGetLastError();
 }
@@ -259,8 +277,14 @@ __device__ __forceinline__ void param_update_one(const VirtualMap& vm, const flo
   }
   float g = 0.f;
   for (int k = 0; k < nv; ++k) {
+    // the slices' loads issued together, then summed in slice order
+    float v[kSlices];
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s)
+      v[s] = s < slices ? part2[(long long)s * vm.n_virtual + vs[k]] : 0.f;
     float t = 0.f;
-    for (int s = 0; s < slices; ++s) t += part2[(long long)s * vm.n_virtual + vs[k]];
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) t += v[s];
     g += t;
   }
   if (grad_out) grad_out[j] = g;
@@ -409,31 +433,45 @@ cudaError_t image_to_planar(const uint8_t* rgb_hwc, float* x, int H, int W, cuda
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256) k_ctx_gather(Geo g, const int2* __restrict__ offs, int N,
+// One thread per latent of the whole pyramid (the latent-shaped buffer's padding skipped),
+// so the grid holds only the blocks that have latents.
+template <int N>
+__global__ void __launch_bounds__(256) k_ctx_gather(Geo g, const int2* __restrict__ offs,
                                                     float* gself, const float* __restrict__ dctx) {
   pdl_wait();
   pdl_trigger();
-  const int l = blockIdx.y;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int l = 0;
+#pragma unroll
+  for (int k = 1; k < kLevels; ++k) l = q >= g.off[k] ? k : l;
   const int w = g.w[l], h = g.h[l];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= h * w) return;
-  const int r = i / w, c = i - r * w;
-  const long long q = g.off[l] + i;
-  float gr = gself[q];
+  const long long i = q - g.off[l];
+  if (q >= g.n_pad || i >= (long long)h * w) return;
+  const int r = (int)(i / w), c = (int)(i - (long long)r * w);
+  // the N context gradients are loaded together, then added in slot order
+  float v[N];
+#pragma unroll
   for (int k = 0; k < N; ++k) {
     const int2 o = __ldg(offs + k);
     const int pr = r - o.x, pc = c - o.y;
-    if (pr < h && pc >= 0 && pc < w)
-      gr += __ldg(dctx + (long long)k * g.n_pad + g.off[l] + pr * w + pc);
+    v[k] = (pr < h && pc >= 0 && pc < w) ? __ldg(dctx + (long long)k * g.n_pad + g.off[l] + pr * w + pc)
+                                        : 0.f;
   }
+  float gr = gself[q];
+#pragma unroll
+  for (int k = 0; k < N; ++k) gr += v[k];
   gself[q] = gr;
 }
 
 cudaError_t ctx_gather(const Geo& g, const int2* d_offsets, int N, float* gself,
                        const float* dctx, cudaStream_t st) {
-  int maxn = 0;
-  for (int l = 0; l < kLevels; ++l) maxn = g.h[l] * g.w[l] > maxn ? g.h[l] * g.w[l] : maxn;
-  k_ctx_gather<<<dim3((maxn + 255) / 256, kLevels), 256, 0, st>>>(g, d_offsets, N, gself, dctx);
+  const dim3 grid((unsigned)((g.n_pad + 255) / 256));
+  switch (N) {
+    case 8: k_ctx_gather<8><<<grid, 256, 0, st>>>(g, d_offsets, gself, dctx); break;
+    case 16: k_ctx_gather<16><<<grid, 256, 0, st>>>(g, d_offsets, gself, dctx); break;
+    case 24: k_ctx_gather<24><<<grid, 256, 0, st>>>(g, d_offsets, gself, dctx); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -185,17 +185,39 @@ __global__ void __launch_bounds__(256, 2) k_up_bwd(UpBwdArgs a) {
   for (int tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) {
     const int y0 = (tile / a.tiles_x) * kUpTY, x0 = (tile % a.tiles_x) * kUpTX;
     const int rb = 2 * (y0 - R) - c, cb = 2 * (x0 - R) - c;
-    for (int i = tid; i < S::DR * 2 * S::DW; i += 256) {
-      const int r = i / (2 * S::DW), cc2 = i - r * (2 * S::DW);
-      const int oy = rb + r, ox = cb + cc2;
-      float v = 0.f;
-      if (oy >= 0 && oy < a.dh && ox >= 0 && ox < a.dw) v = __ldg(dout + (size_t)oy * a.dw + ox);
-      s_d[cc2 & 1][r][cc2 >> 1] = v;
-    }
-    for (int i = tid; i < S::AR * S::AW; i += 256) {
-      const int r = i / S::AW, m = i - r * S::AW;
-      const int vy = clampi(y0 - R + r, 0, a.sh - 1), vx = clampi(x0 - R + m, 0, a.sw - 1);
-      s_a[r][m] = __ldg(in + (size_t)vy * a.sw + vx);
+    // every load of a thread is issued before the first is used (fixed trip counts,
+    // unrolled): on the small grids of the coarse steps this latency is the kernel's time
+    {
+      constexpr int ND = S::DR * 2 * S::DW, KD = (ND + 255) / 256;
+      constexpr int NA = S::AR * S::AW, KA = (NA + 255) / 256;
+      float vd[KD], va[KA];
+#pragma unroll
+      for (int k = 0; k < KD; ++k) {
+        const int i = tid + 256 * k;
+        const int r = i / (2 * S::DW), cc2 = i - r * (2 * S::DW);
+        const int oy = rb + r, ox = cb + cc2;
+        vd[k] = (i < ND && oy >= 0 && oy < a.dh && ox >= 0 && ox < a.dw)
+                    ? __ldg(dout + (size_t)oy * a.dw + ox) : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < KA; ++k) {
+        const int i = tid + 256 * k;
+        const int r = i / S::AW, m = i - r * S::AW;
+        const int vy = clampi(y0 - R + r, 0, a.sh - 1), vx = clampi(x0 - R + m, 0, a.sw - 1);
+        va[k] = i < NA ? __ldg(in + (size_t)vy * a.sw + vx) : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < KD; ++k) {
+        const int i = tid + 256 * k;
+        const int r = i / (2 * S::DW), cc2 = i - r * (2 * S::DW);
+        if (i < ND) s_d[cc2 & 1][r][cc2 >> 1] = vd[k];
+      }
+#pragma unroll
+      for (int k = 0; k < KA; ++k) {
+        const int i = tid + 256 * k;
+        const int r = i / S::AW, m = i - r * S::AW;
+        if (i < NA) s_a[r][m] = va[k];
+      }
     }
     __syncthreads();
     // ---- input gradient at (iy, ix) and (iy + 1, ix)
