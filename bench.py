@@ -14,6 +14,7 @@ back.  `--impl reference` times the FP64 CPU oracle on a bounded sample of the w
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -32,10 +33,26 @@ METRIC = "encode Mpixel-iter/s (fwd+bwd+Adam) vs plain; s to RD-cost within 1% o
 UNIT = "Mpixel-iter/s"
 PAPER_DERIVED_MPXIT = 22.5   # 512x768, 2300-MAC, 102 950 iterations in ~30 min (Sec. V, Fig. 5)
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) of one launch of the ARM kernel on this workload, from the ncu
-# capture summarised in profiles/k_arm_fb_512x768.md (the kernel as built from the source
-# of that capture); None when the kernel has changed since the counters were taken
-ARM_DRAM_BYTES_PER_LAUNCH = 2257664 + 932096
+# DRAM bytes (read + write) of one launch of the ARM kernel on this workload: the mean over
+# six launches of the ncu capture summarised in profiles/k_arm_fb_512x768.md.  They hold
+# for the kernel built from the sources whose SHA-256 is recorded beside them; bench.py
+# reports traffic null when those sources have changed since.
+ARM_DRAM_BYTES_PER_LAUNCH = 2257621 + 980395
+ARM_COUNTER_SOURCES = ("cc_arm.cu", "cc_laplace.cuh", "cc_tc.cuh")
+ARM_COUNTER_SOURCES_SHA256 = "548df8a913694ef31925807f11f9d2e29815145a034984acf60fc8d9ac7391f7"
+
+
+def arm_sources_sha256():
+    h = hashlib.sha256()
+    for name in ARM_COUNTER_SOURCES:
+        with open(os.path.join(ROOT, "paper_2403_11651_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def arm_traffic():
+    """ARM DRAM bytes per launch, or None if the kernel's sources differ from the profiled ones."""
+    return ARM_DRAM_BYTES_PER_LAUNCH if arm_sources_sha256() == ARM_COUNTER_SOURCES_SHA256 else None
 
 
 def dist_env():
@@ -467,7 +484,7 @@ def run_ours(a, cfgd):
         "dtype": "f32", "data": "synthetic", "config": workload(cfgd),
         "roofline": {"bound": "alu", "kernel": "k_arm_fb<24,2> (ARM + rate, fwd+bwd)",
                      "achieved": arm_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": arm_tflops / peak_tflops, "traffic": ARM_DRAM_BYTES_PER_LAUNCH,
+                     "frac": arm_tflops / peak_tflops, "traffic": arm_traffic(),
                      "whole_iteration_frac": 6 * kappa * H * W / (it_ms / 1e3) / 1e12 / peak_tflops,
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {clk_max:.0f} MHz "
                                    f"(sm_max_mhz, {src}); the kernel's CTAs share the SMs "

@@ -148,7 +148,9 @@ struct cc_ctx {
   cudaStream_t cap = nullptr;
   cudaStream_t side = nullptr;        // ARM branch of a pass, concurrent with the synthesis
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  cudaEvent_t ev_arm = nullptr, ev_chain = nullptr;   // ARM done (side) / chain done (main)
+  cudaEvent_t ev_chain = nullptr;   // upsampling adjoint done (main)
+  cudaEvent_t ev_syn = nullptr;     // synthesis adjoint done (main)
+  cudaEvent_t ev_red = nullptr;     // ARM, synthesis and 3x3 partials reduced (side)
   cudaStream_t up_st = nullptr;                         // image uploads
   cudaEvent_t ev_planar = nullptr, ev_uploaded = nullptr;
   cudaEvent_t ev_a0 = nullptr, ev_a1 = nullptr;   // timing of the ARM kernel in forked passes
@@ -170,7 +172,8 @@ struct cc_ctx {
   UpPlan up;
   std::vector<int2> h_tiles, h_offs;
   int n_tiles = 0, grid_arm = 0, grid_syn = 0, grid_tiles = 0, slices = kSlices, n_virtual = 0;
-  SectionTable tab;
+  SectionTable tab;                   // every section of the parameter gradient
+  SectionTable tab_early, tab_late;   // the same split: ARM / 1x1 / 3x3, then upsampling
   ArmMaps maps;   // tensor maps of the zero-bordered y_hat planes (ARM context tiles)
   cudaGraphExec_t g1 = nullptr, g16 = nullptr;
   int iter = 0;
@@ -303,6 +306,11 @@ void build_sections(cc_ctx* c) {
     t.s[n++] = {c->part_up + (size_t)l * K2, l * c->grid_syn, K2, kLevels * K2,
                 vup + (l - 1) * K2, 1.f};
   t.n = n;
+  const int n_early = 2 + a.NR;
+  c->tab_early.n = n_early;
+  for (int i = 0; i < n_early; ++i) c->tab_early.s[i] = t.s[i];
+  c->tab_late.n = n - n_early;
+  for (int i = n_early; i < n; ++i) c->tab_late.s[i - n_early] = t.s[i];
 }
 
 // Whether a pass quantising with mode qmode used the soft-rounding proxy: 0 never (no
@@ -409,27 +417,41 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
                  c->dctx, c->gself, c->part_arm, c->part_bits, &c->sc->fault,
                  &c->sc->arm_stall, sa));
   if (fork) CKE(record_on_side(c->ev_a1));
-  if (fork) CKE(cudaEventRecord(c->ev_arm, sa));
-  // the context gather follows the ARM on its stream; timed per phase it runs after the
-  // upsampling adjoint instead, so that the phase events stay in stream order
-  if (backward && fork) CKE(ctx_gather(c->geo, c->offs, a.N, c->gself, c->dctx, sa));
+  // with gradients, the side stream continues once the synthesis adjoint is enqueued (below)
   if (fork && !backward) CKE(cudaEventRecord(c->ev_join, sa));
   CKE(mark(2));
   CKE(up_forward(a, c->geo, c->yhat, c->up, c->grid_syn, s));
   CKE(mark(3));
+  // with gradients and two 3x3 layers, one kernel runs the 3x3 layers' forward and backward
+  const bool pair = backward && a.NR == 2;
   CKE(syn_forward(a, c->geo, c->yhat, c->up, c->x, c->hbuf, c->dhbuf + (size_t)a.NR * 3 * HW,
-                  c->part_d, c->part_conv, c->grid_tiles, s));
+                  c->part_d, c->part_conv, c->grid_tiles, s,
+                  pair ? c->dhbuf + (size_t)3 * HW : nullptr, pair ? c->dz : nullptr));
   CKE(mark(4));
   if (backward) {
-    CKE(syn_backward(a, c->geo, c->yhat, c->up, c->hbuf, c->dhbuf, c->dz, c->gsyn, c->part_conv,
-                     c->part_syn, c->grid_tiles, s));
-    CKE(mark(5));
-    CKE(up_backward(a, c->geo, c->yhat, c->up, c->gsyn, c->part_up, c->grid_syn, s));
-    CKE(mark(6));
     PassFinish pf;
     pf.part_d = c->part_d; pf.nd = c->grid_tiles; pf.part_bits = c->part_bits;
     pf.nb = c->grid_arm; pf.d_scale = 1.0 / (3.0 * (double)HW); pf.r_scale = 1.0 / (double)HW;
     pf.lam = (double)c->cfg.lam; pf.log = c->log;
+    CKE(syn_backward(a, c->geo, c->yhat, c->up, c->hbuf, c->dhbuf, c->dz, c->gsyn, c->part_conv,
+                     c->part_syn, c->grid_tiles, s, pair));
+    if (fork) {
+      // after the ARM kernel and the synthesis adjoint, the side stream reduces the ARM,
+      // 1x1 and 3x3 partials and those of D and R, then gathers the context gradients, while
+      // the upsampling adjoint runs; only the upsampling partials are reduced at the end.
+      // (Timed per phase, the gather runs after the upsampling adjoint instead, so that the
+      // phase events stay in stream order.)  Measured against the gather first, or the
+      // reductions on a third stream: 1-4 us shorter per iteration.
+      CKE(cudaEventRecord(c->ev_syn, s));
+      CKE(cudaStreamWaitEvent(sa, c->ev_syn, 0));
+      CKE(reduce_sections(c->tab_early, c->part2, c->n_virtual, c->slices, sa));
+      CKE(pass_loss(pf, c->sc, sa));
+      CKE(cudaEventRecord(c->ev_red, sa));
+      CKE(ctx_gather(c->geo, c->offs, a.N, c->gself, c->dctx, sa));
+    }
+    CKE(mark(5));
+    CKE(up_backward(a, c->geo, c->yhat, c->up, c->gsyn, c->part_up, c->grid_syn, s));
+    CKE(mark(6));
     // the parameter update (after the reduction of the partial sums) and the latent update
     // are independent; forked, they run at once and the last block of either finishes
     // the pass
@@ -444,11 +466,13 @@ cudaError_t enqueue_pass(cc_ctx* c, cudaStream_t s, int qmode, bool backward, bo
       CKE(cudaEventRecord(c->ev_chain, s));
       CKE(cudaStreamWaitEvent(sa, c->ev_chain, 0));
       CKE(latents(sa));
-      CKE(cudaStreamWaitEvent(s, c->ev_arm, 0));
+      CKE(cudaStreamWaitEvent(s, c->ev_red, 0));
+      CKE(reduce_sections(c->tab_late, c->part2, c->n_virtual, c->slices, s));
     } else {
       CKE(ctx_gather(c->geo, c->offs, a.N, c->gself, c->dctx, s));
+      CKE(reduce_sections(c->tab, c->part2, c->n_virtual, c->slices, s));
+      CKE(pass_loss(pf, c->sc, s));
     }
-    CKE(reduce_sections(c->tab, c->part2, c->n_virtual, c->slices, s));
     CKE(param_update(c->lay, a, c->part2, c->slices, c->params, c->mp, c->vp,
                      grad_out ? grad_out + c->geo.n_lat : nullptr, apply, c->cfg.lr, c->sc,
                      image_slots(c), &pf, tickets, advance, s));
@@ -590,8 +614,9 @@ int init_common(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
     return bail(fail_cuda(ce, "cudaStreamCreate"));
   if ((ce = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
       (ce = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess ||
-      (ce = cudaEventCreateWithFlags(&c->ev_arm, cudaEventDisableTiming)) != cudaSuccess ||
       (ce = cudaEventCreateWithFlags(&c->ev_chain, cudaEventDisableTiming)) != cudaSuccess ||
+      (ce = cudaEventCreateWithFlags(&c->ev_syn, cudaEventDisableTiming)) != cudaSuccess ||
+      (ce = cudaEventCreateWithFlags(&c->ev_red, cudaEventDisableTiming)) != cudaSuccess ||
       (ce = cudaEventCreateWithFlags(&c->ev_planar, cudaEventDisableTiming)) != cudaSuccess ||
       (ce = cudaEventCreateWithFlags(&c->ev_uploaded, cudaEventDisableTiming)) != cudaSuccess ||
       (ce = cudaEventCreate(&c->ev_a0)) != cudaSuccess ||
@@ -617,6 +642,7 @@ int init_common(const cc_config* cfg, const uint8_t* rgb_hwc, int H, int W,
   const IterScalars sc0 = iter_scalars_at(0);
   if ((ce = cudaMemcpyAsync(c->sc, &sc0, sizeof(sc0), cudaMemcpyHostToDevice, c->st)))
     return bail(fail_cuda(ce, "scalars copy"));
+  if ((ce = adam_bc_upload(c->st))) return bail(fail_cuda(ce, "Adam bias-correction table"));
   if ((ce = cudaMemcpyAsync(c->tiles, c->h_tiles.data(), c->h_tiles.size() * sizeof(int2),
                             cudaMemcpyHostToDevice, c->st)))
     return bail(fail_cuda(ce, "tiles copy"));
@@ -1320,8 +1346,9 @@ void cc_free(cc_ctx* c) {
   if (c->ev_uploaded) cudaEventDestroy(c->ev_uploaded);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
-  if (c->ev_arm) cudaEventDestroy(c->ev_arm);
   if (c->ev_chain) cudaEventDestroy(c->ev_chain);
+  if (c->ev_syn) cudaEventDestroy(c->ev_syn);
+  if (c->ev_red) cudaEventDestroy(c->ev_red);
   if (c->ev_a0) cudaEventDestroy(c->ev_a0);
   if (c->ev_a1) cudaEventDestroy(c->ev_a1);
   if (c->own_mem && c->mem) cudaFree(c->mem);

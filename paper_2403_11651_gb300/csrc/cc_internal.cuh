@@ -42,6 +42,7 @@ constexpr int kCtxPad = 4;        // reach of the largest causal context (N = 24
 // holds blocks that wait.  CC_PDL=0 in the environment turns the attribute off.
 #ifndef CC_TRACE
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void trace_point(const char*) {}
 #else
 // Traced build (all sources in one translation unit): block (0, 0, 0) of every kernel
 // records, once its wait returns, the global timer, an FNV-1a hash of the kernel's name
@@ -71,6 +72,20 @@ __device__ __forceinline__ void pdl_wait_traced(const char* name) {
   }
 }
 #define pdl_wait() pdl_wait_traced(__func__)
+// A point inside a kernel, recorded by the calling thread: the global timer, the tag's hash,
+// the block index (gx) and gy = -1.
+__device__ __forceinline__ void trace_point(const char* tag) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  unsigned h = 2166136261u;
+  for (int i = 0; tag[i] && i < 64; ++i) h = (h ^ (unsigned char)tag[i]) * 16777619u;
+  const unsigned k = atomicAdd(&g_trace_n, 1u) % kTraceCap;
+  g_trace[k].t = t;
+  g_trace[k].hash = h;
+  g_trace[k].gx = blockIdx.x;
+  g_trace[k].gy = -1;
+  g_trace[k].bx = 0;
+}
 #endif
 __device__ __forceinline__ void pdl_trigger() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -131,7 +146,6 @@ struct IterScalars {
   float inv_sqrt_bc2; // Adam 1 / sqrt(1 - beta2^(t+1))
   int fault;          // set when a bounded context-load wait of the ARM kernel gave up
   double D, R, loss;
-  double b1t, b2t;    // beta1^t, beta2^t, carried by repeated multiplication
   unsigned ticket;    // blocks of the latent update done (reset by the last one)
   int nan_at;         // fault injection: the latent update of this iteration makes the
                       // gradient of latent 0 NaN (-1: never; cc_debug_inject)
@@ -142,6 +156,8 @@ struct IterScalars {
 };
 // IterScalars of iteration t, computed on the host (context set-up, state restore).
 IterScalars iter_scalars_at(int t);
+// Fill the device's table of Adam bias corrections (before the first pass on a device).
+cudaError_t adam_bc_upload(cudaStream_t st);
 
 // ---- launchers (each returns the cudaError_t of its launch) ----
 // ARM (cc_arm.cu)
@@ -192,12 +208,17 @@ cudaError_t up_backward(const Arch& a, const Geo& g, const float* yhat, const Up
 // Synthesis kernels run on 8 x 32 pixel tiles; `grid` CTAs loop over syn_tile_count(g)
 // tiles and write `grid` rows of partial sums (distortion; 84 per 3x3 layer; 11C + 3).
 int syn_tile_count(const Geo& g);
+// With dh and dz (two 3-layer with gradients), the forward's 3x3 kernel also computes the
+// 3x3 part of the backward (layer 1's input gradient into dh, layer 0's pre-activation
+// gradient into dz, both weight gradients); syn_backward is then called with convs_done.
 cudaError_t syn_forward(const Arch& a, const Geo& g, const float* yhat, const UpPlan& up,
                         const float* x, float* hbuf, float* dxhat, float* part_d,
-                        float* part_conv, int grid, cudaStream_t st);
+                        float* part_conv, int grid, cudaStream_t st, float* dh = nullptr,
+                        float* dz = nullptr);
 cudaError_t syn_backward(const Arch& a, const Geo& g, const float* yhat, const UpPlan& up,
                          float* hbuf, float* dhbuf, float* dz, float* gsyn,
-                         float* part_conv, float* part_syn, int grid, cudaStream_t st);
+                         float* part_conv, float* part_syn, int grid, cudaStream_t st,
+                         bool convs_done = false);
 cudaError_t syn_decode(const Arch& a, const Geo& g, const float* hbuf_last, float* out_hwc,
                        cudaStream_t st);
 int syn1x1_partial_cols(const Arch& a);
@@ -232,9 +253,9 @@ struct PassFinish {
   double d_scale, r_scale, lam;
   double* log;
 };
-// The pass is finished by the last block to end among the latent update's blocks and, if
-// it takes part (pf != nullptr), the parameter update's: tickets = the sum of their block
-// counts (latent_update_blocks, param_update_blocks).
+// The step to the next iteration is taken by the last block to end among the latent
+// update's blocks and, if it takes part (pf != nullptr), the parameter update's: tickets =
+// the sum of their block counts (latent_update_blocks, param_update_blocks).
 unsigned param_update_blocks(const Layout& lay);
 unsigned latent_update_blocks(const Geo& g);
 cudaError_t param_update(const Layout& lay, const Arch& a, const float* part2, int slices,
@@ -247,6 +268,9 @@ cudaError_t latent_update(const Geo& g, const float* gsyn, const float* grate, f
                           float* y, float* m, float* v, float* grad_out, bool apply, float lr,
                           IterScalars* sc, const PassFinish& pf, unsigned tickets, bool advance,
                           const float* dq, int soft, int ste_start, cudaStream_t st);
+// D, R, the loss and the loss log entry of a pass with gradients (one block; the step to
+// the next iteration is taken by the last update block).
+cudaError_t pass_loss(const PassFinish& pf, IterScalars* sc, cudaStream_t st);
 cudaError_t finish_iteration(const float* part_d, int nd, const float* part_bits, int nb,
                              double d_scale, double r_scale, double lam, IterScalars* sc,
                              double* log, bool advance, cudaStream_t st,

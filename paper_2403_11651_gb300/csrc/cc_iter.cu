@@ -2,6 +2,8 @@
 // as used in Sec. IV-B), plus the deterministic reductions of the per-CTA partial sums.
 #include "cc_internal.cuh"
 
+#include <vector>
+
 #include <cmath>
 #include <cstdlib>
 
@@ -169,62 +171,108 @@ __device__ __forceinline__ void adam_apply(float& p, float& m, float& v, float g
   p -= a.lr * (m * a.inv_bc1) / (sqrtf(v) * a.inv_sqrt_bc2 + 1e-8f);
 }
 
-// D, R and the loss of the pass from the per-CTA partial sums (FP64, fixed order), the
-// loss log entry, and with `advance` the step to the next iteration (t and the Adam powers
-// and bias corrections of its update).  Run by one block of any power-of-two size up to
-// 256: the sums run over 256 virtual lanes in a fixed order, so the result does not
-// depend on which kernel's block finishes the pass.
-__device__ __forceinline__ void finish_block(const float* part_d, int nd, const float* part_bits,
-                                             int nb, double d_scale, double r_scale, double lam,
-                                             IterScalars* sc, double* log, int advance) {
-  __shared__ double sd[256], sb[256];
+// Adam bias corrections of step s >= 1, (1 / (1 - beta1^s), 1 / sqrt(1 - beta2^s)), computed
+// in FP64 on the host and rounded to float; from step kAdamBcSteps on both round to 1.0f
+// (beta2^s < 2^-47).  The passes look them up instead of evaluating FP64 powers, divisions
+// and square roots, which are slow on this GPU's FP64 units.
+constexpr int kAdamBcSteps = 32768;
+__device__ float2 g_adam_bc[kAdamBcSteps];
+
+__device__ __forceinline__ float2 adam_bc(int s) {
+  return s < kAdamBcSteps ? g_adam_bc[s] : make_float2(1.f, 1.f);
+}
+
+static float2 adam_bc_host(int s) {
+  return make_float2((float)(1.0 / (1.0 - pow(0.9, (double)s))),
+                     (float)(1.0 / sqrt(1.0 - pow(0.999, (double)s))));
+}
+
+cudaError_t adam_bc_upload(cudaStream_t st) {
+  static const std::vector<float2> tab = [] {
+    std::vector<float2> v(kAdamBcSteps, make_float2(1.f, 1.f));
+    for (int s = 1; s < kAdamBcSteps; ++s) v[s] = adam_bc_host(s);
+    return v;
+  }();
+  return cudaMemcpyToSymbolAsync(g_adam_bc, tab.data(), sizeof(float2) * kAdamBcSteps, 0,
+                                 cudaMemcpyHostToDevice, st);
+}
+
+// a + b as the unevaluated pair (s, e) with s + e = a + b exactly (Knuth's TwoSum)
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = a + b, v = s - a;
+  return make_float2(s, (a - (s - v)) + (b - v));
+}
+
+// (a.x + a.y) + (b.x + b.y) in float-float arithmetic (Dekker): the exact sum of the high
+// parts plus the low parts, renormalised.  For the non-negative partial sums added here
+// the relative error is a few units of 2^-44.
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float2 s = two_sum(a.x, b.x);
+  const float e = s.y + (a.y + b.y);
+  const float h = s.x + e;
+  return make_float2(h, e - (h - s.x));
+}
+
+// D, R and the loss of the pass from the per-CTA partial sums, and the loss log entry of
+// iteration t.  The partials are summed in float-float arithmetic over 256 virtual lanes
+// (all loads of a lane issued together) and a tree, in a fixed order; run by one block of
+// any power-of-two size up to 256.
+constexpr int kLossLoads = 8;   // partials per virtual lane loaded at once
+__device__ __forceinline__ float2 lane_sum(const float* part, int n, int v) {
+  float2 a = make_float2(0.f, 0.f);
+  for (int k0 = v; k0 < n; k0 += 256 * kLossLoads) {
+    float x[kLossLoads];
+#pragma unroll
+    for (int j = 0; j < kLossLoads; ++j) x[j] = k0 + 256 * j < n ? part[k0 + 256 * j] : 0.f;
+#pragma unroll
+    for (int j = 0; j < kLossLoads; ++j) a = ff_add(a, make_float2(x[j], 0.f));
+  }
+  return a;
+}
+
+__device__ __forceinline__ void loss_block(const float* part_d, int nd, const float* part_bits,
+                                           int nb, double d_scale, double r_scale, double lam,
+                                           IterScalars* sc, double* log) {
+  __shared__ float2 sd[256], sb[256];
   for (int v = threadIdx.x; v < 256; v += blockDim.x) {
-    double a = 0.0, b = 0.0;
-    for (int k = v; k < nd; k += 256) a += (double)part_d[k];
-    for (int k = v; k < nb; k += 256) b += (double)part_bits[k];
-    sd[v] = a;
-    sb[v] = b;
+    sd[v] = lane_sum(part_d, nd, v);
+    sb[v] = lane_sum(part_bits, nb, v);
   }
   __syncthreads();
   for (int s = 128; s > 0; s >>= 1) {
     for (int v = threadIdx.x; v < s; v += blockDim.x) {
-      sd[v] += sd[v + s];
-      sb[v] += sb[v + s];
+      sd[v] = ff_add(sd[v], sd[v + s]);
+      sb[v] = ff_add(sb[v], sb[v + s]);
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const double D = sd[0] * d_scale, R = sb[0] * r_scale;
+    const double D = ((double)sd[0].x + (double)sd[0].y) * d_scale;
+    const double R = ((double)sb[0].x + (double)sb[0].y) * r_scale;
     sc->D = D;
     sc->R = R;
     sc->loss = D + lam * R;
-    const int t = sc->t;
-    double* e = log + 3 * (long long)(t % kLogCap);
+    double* e = log + 3 * (long long)(sc->t % kLogCap);
     e[0] = D;
     e[1] = R;
     e[2] = D + lam * R;
-    if (advance) {
-      const double b1 = sc->b1t * 0.9, b2 = sc->b2t * 0.999;   // beta^(t+1)
-      sc->t = t + 1;
-      sc->b1t = b1;
-      sc->b2t = b2;
-      sc->inv_bc1 = (float)(1.0 / (1.0 - b1 * 0.9));             // step t + 2
-      sc->inv_sqrt_bc2 = (float)(1.0 / sqrt(1.0 - b2 * 0.999));
-    }
   }
+}
+
+// The step to the next iteration: t and the Adam bias corrections of its update (one thread).
+__device__ __forceinline__ void advance_step(IterScalars* sc) {
+  const int t = sc->t;
+  sc->t = t + 1;
+  const float2 bc = adam_bc(t + 2);   // the update of iteration t + 1 is Adam step t + 2
+  sc->inv_bc1 = bc.x;
+  sc->inv_sqrt_bc2 = bc.y;
 }
 
 // The pass ends with the latent update and the parameter update, which may run on two
 // streams at once; the last of their blocks to end (a ticket in IterScalars counting the
-// blocks of both) finishes the pass (finish_block), after every block has read the
-// iteration's scalars.
+// blocks of both) takes the step to the next iteration, after every block has read the
+// iteration's scalars.  The loss of the pass is computed beforehand (pass_loss).
 struct FinishArgs {
-  const float* part_d;
-  int nd;
-  const float* part_bits;
-  int nb;
-  double d_scale, r_scale, lam;
-  double* log;
   int advance;
   unsigned tickets;   // blocks that take a ticket: the latent update's, plus the parameter
                       // update's when it shares the finish
@@ -232,15 +280,27 @@ struct FinishArgs {
 
 __device__ __forceinline__ void finish_if_last(IterScalars* sc, const FinishArgs& fa) {
   __shared__ bool s_last;
+  // t and the next bias corrections are read before the ticket (no block changes them
+  // before the last ticket), so that the last block only stores
+  int t = 0;
+  float2 bc = make_float2(1.f, 1.f);
+  if (threadIdx.x == 0 && fa.advance) {
+    t = sc->t;
+    bc = adam_bc(t + 2);   // the update of iteration t + 1 is Adam step t + 2
+  }
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) s_last = atomicAdd(&sc->ticket, 1u) == fa.tickets - 1;
   __syncthreads();
-  if (s_last) {
-    __threadfence();
-    finish_block(fa.part_d, fa.nd, fa.part_bits, fa.nb, fa.d_scale, fa.r_scale, fa.lam, sc,
-                 fa.log, fa.advance);
-    if (threadIdx.x == 0) sc->ticket = 0u;
+  if (s_last && threadIdx.x == 0) {
+    trace_point("finish_begin");
+    if (fa.advance) {
+      sc->t = t + 1;
+      sc->inv_bc1 = bc.x;
+      sc->inv_sqrt_bc2 = bc.y;
+    }
+    sc->ticket = 0u;
+    trace_point("finish_end");
   }
 }
 
@@ -312,13 +372,12 @@ __global__ void __launch_bounds__(128) k_param_update(VirtualMap vm, const float
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < total) param_update_one(vm, part2, slices, params, m, v, grad_out, apply, lr, sc, j,
                                   slots);
+  if (threadIdx.x == 0) trace_point("param_block_done");
   if (fa.tickets) finish_if_last(sc, fa);
 }
 
-FinishArgs finish_args(const PassFinish& pf, bool advance, unsigned tickets) {
+FinishArgs finish_args(bool advance, unsigned tickets) {
   FinishArgs fa;
-  fa.part_d = pf.part_d; fa.nd = pf.nd; fa.part_bits = pf.part_bits; fa.nb = pf.nb;
-  fa.d_scale = pf.d_scale; fa.r_scale = pf.r_scale; fa.lam = pf.lam; fa.log = pf.log;
   fa.advance = advance ? 1 : 0;
   fa.tickets = tickets;
   return fa;
@@ -338,7 +397,7 @@ cudaError_t param_update(const Layout& lay, const Arch& a, const float* part2, i
   vm.per_level = a.per_level;
   vm.vsyn = lay.n_arm; vm.vconv = vm.vsyn + vm.n1x1; vm.vup = vm.vconv + vm.nconv;
   vm.n_virtual = vm.vup + (kLevels - 1) * vm.K2;
-  const FinishArgs fa = pf ? finish_args(*pf, advance, tickets) : FinishArgs{};
+  const FinishArgs fa = pf ? finish_args(advance, tickets) : FinishArgs{};
   return launch_k(k_param_update, dim3(param_update_blocks(lay)), dim3(128), 0, st, vm, part2,
                   slices, params, m, v, grad_out, apply ? 1 : 0, lr,
                   const_cast<IterScalars*>(sc), lay.total, slots, fa);
@@ -350,7 +409,14 @@ __global__ void __launch_bounds__(256) k_finish(const float* part_d, int nd,
                                                 double* log, int advance) {
   pdl_wait();
   pdl_trigger();
-  finish_block(part_d, nd, part_bits, nb, d_scale, r_scale, lam, sc, log, advance);
+  loss_block(part_d, nd, part_bits, nb, d_scale, r_scale, lam, sc, log);
+  if (advance && threadIdx.x == 0) advance_step(sc);
+}
+
+cudaError_t pass_loss(const PassFinish& pf, IterScalars* sc, cudaStream_t st) {
+  k_finish<<<1, 256, 0, st>>>(pf.part_d, pf.nd, pf.part_bits, pf.nb, pf.d_scale, pf.r_scale,
+                              pf.lam, sc, pf.log, 0);
+  return cudaGetLastError();
 }
 
 // Gradient of a latent: the synthesis path, plus lambda/(HW) times the rate terms in
@@ -399,7 +465,7 @@ cudaError_t latent_update(const Geo& g, const float* gsyn, const float* grate, f
                           float* y, float* m, float* v, float* grad_out, bool apply, float lr,
                           IterScalars* sc, const PassFinish& pf, unsigned tickets, bool advance,
                           const float* dq, int soft, int ste_start, cudaStream_t st) {
-  const FinishArgs fa = finish_args(pf, advance, tickets);
+  const FinishArgs fa = finish_args(advance, tickets);
   return launch_k(k_latent_update, dim3(latent_update_blocks(g)), dim3(256), 0, st, g, gsyn,
                   grate, rate_scale, y, m, v, grad_out, apply ? 1 : 0, lr, sc, fa, dq, soft,
                   ste_start);
@@ -479,10 +545,9 @@ IterScalars iter_scalars_at(int t) {
   IterScalars s{};
   s.t = t;
   s.nan_at = -1;
-  s.b1t = pow(0.9, (double)t);
-  s.b2t = pow(0.999, (double)t);
-  s.inv_bc1 = (float)(1.0 / (1.0 - s.b1t * 0.9));
-  s.inv_sqrt_bc2 = (float)(1.0 / sqrt(1.0 - s.b2t * 0.999));
+  const float2 bc = adam_bc_host(t + 1);
+  s.inv_bc1 = bc.x;
+  s.inv_sqrt_bc2 = bc.y;
   return s;
 }
 

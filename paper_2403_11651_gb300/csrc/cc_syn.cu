@@ -405,54 +405,57 @@ __device__ __forceinline__ void tile_xy(const SynTileGeo& t, int tile, int& y0, 
 }
 
 // A thread's share of a halo tile load: elements i = threadIdx.x + 256 k of the
-// 3 x kSHR x (kSTX + 2) halo, with their shared-memory index and their offset from the
-// tile's first pixel in a [3][H][W] plane set, computed once per kernel.  Tiles whose halo
-// lies inside the image load at base + offset; border tiles clamp each coordinate.  The
+// 3 x (kSTY + 2 HALO) x (kSTX + 2 HALO) region around a tile, with their shared-memory
+// index (rows RS floats apart, channels CS) and their offset from the tile's first pixel
+// in a [3][H][W] plane set, computed once per kernel.  Tiles whose region lies inside the
+// image load at base + offset; border tiles clamp each coordinate (replicate padding).  The
 // values pass through registers so that a kernel can issue the next tile's loads before
 // it computes the current one.
-constexpr int kHaloN = 3 * kSHR * (kSTX + 2);
-constexpr int kHaloK = (kHaloN + 255) / 256;
-struct HaloPlan {
-  int sidx[kHaloK];   // -1: no element for this thread
-  int goff[kHaloK];
+template <int HALO, int RS, int CS>
+struct HaloPlanT {
+  static constexpr int R = kSTY + 2 * HALO, C = kSTX + 2 * HALO, N = 3 * R * C;
+  static constexpr int K = (N + 255) / 256;
+  static_assert(C <= RS && R * RS <= CS, "halo region does not fit its layout");
+  int sidx[K];   // -1: no element for this thread
+  int goff[K];
   int H, W;
   __device__ __forceinline__ void init(int H_, int W_) {
     H = H_;
     W = W_;
 #pragma unroll
-    for (int k = 0; k < kHaloK; ++k) {
+    for (int k = 0; k < K; ++k) {
       const int i = threadIdx.x + 256 * k;
-      const int n = kSHR * (kSTX + 2);
-      const int ci = i / n, rc = i - ci * n;
-      const int r = rc / (kSTX + 2), c = rc - r * (kSTX + 2);
-      sidx[k] = i < kHaloN ? ci * kSHS + r * kSHX + c : -1;
-      goff[k] = ci * H * W + (r - 1) * W + (c - 1);
+      const int ci = i / (R * C), rc = i - ci * (R * C);
+      const int r = rc / C, c = rc - r * C;
+      sidx[k] = i < N ? ci * CS + r * RS + c : -1;
+      goff[k] = ci * H * W + (r - HALO) * W + (c - HALO);
     }
   }
-  __device__ __forceinline__ void load(float (&v)[kHaloK], const float* __restrict__ h, int y0,
+  __device__ __forceinline__ void load(float (&v)[K], const float* __restrict__ h, int y0,
                                        int x0) const {
-    if (y0 >= 1 && x0 >= 1 && y0 + kSTY < H && x0 + kSTX < W) {
+    if (y0 >= HALO && x0 >= HALO && y0 + kSTY + HALO <= H && x0 + kSTX + HALO <= W) {
       const float* base = h + y0 * W + x0;
 #pragma unroll
-      for (int k = 0; k < kHaloK; ++k) v[k] = sidx[k] >= 0 ? __ldg(base + goff[k]) : 0.f;
+      for (int k = 0; k < K; ++k) v[k] = sidx[k] >= 0 ? __ldg(base + goff[k]) : 0.f;
       return;
     }
 #pragma unroll
-    for (int k = 0; k < kHaloK; ++k) {
+    for (int k = 0; k < K; ++k) {
       const int i = threadIdx.x + 256 * k;
-      const int n = kSHR * (kSTX + 2);
-      const int ci = i / n, rc = i - ci * n;
-      const int r = rc / (kSTX + 2), c = rc - r * (kSTX + 2);
-      const int gy = clampi(y0 - 1 + r, 0, H - 1), gx = clampi(x0 - 1 + c, 0, W - 1);
+      const int ci = i / (R * C), rc = i - ci * (R * C);
+      const int r = rc / C, c = rc - r * C;
+      const int gy = clampi(y0 - HALO + r, 0, H - 1), gx = clampi(x0 - HALO + c, 0, W - 1);
       v[k] = sidx[k] >= 0 ? __ldg(h + ci * H * W + gy * W + gx) : 0.f;
     }
   }
-  __device__ __forceinline__ void store(float* s, const float (&v)[kHaloK]) const {
+  __device__ __forceinline__ void store(float* s, const float (&v)[K]) const {
 #pragma unroll
-    for (int k = 0; k < kHaloK; ++k)
+    for (int k = 0; k < K; ++k)
       if (sidx[k] >= 0) s[sidx[k]] = v[k];
   }
 };
+using HaloPlan = HaloPlanT<1, kSHX, kSHS>;
+constexpr int kHaloK = HaloPlan::K;
 
 // the 27 inputs of pixel (ty, tx) of the tile: v[ci * 9 + (dy + 1) * 3 + dx + 1]
 __device__ __forceinline__ void gather_halo(float (&v)[27], const float* s, int ty, int tx) {
@@ -518,18 +521,21 @@ __device__ __forceinline__ void conv_adjoint(float (&acc)[3], const float* s_dz,
 // channel ci = t / 85 and the pixels q = t % 85 + 85 j of the tile; it adds the 27 products
 // dz[o][q] h[ci][q + tap] (o < 3, 9 taps) and the bias terms dz[o][q] into registers that
 // persist over the CTA's tiles.  s_dz: [3][256], s_h: the layer input's halo tile.
+// s_h points at the tap (-1, -1) of the tile's first pixel in a layout of rows RS and
+// channels CS floats apart (the one-pixel halo tile by default).
 constexpr int kWG = 85;                        // pixel groups per channel
+template <int RS = kSHX, int CS = kSHS>
 __device__ __forceinline__ void conv_wgrad(float (&acc)[30], const float* s_dz, const float* s_h) {
   const int t = threadIdx.x;
   if (t >= 3 * kWG) return;
   const int ci = t / kWG;
   for (int q = t - ci * kWG; q < 256; q += kWG) {
-    const float* hh = s_h + ci * kSHS + (q >> 5) * kSHX + (q & 31);
+    const float* hh = s_h + ci * CS + (q >> 5) * RS + (q & 31);
     float hv[9];
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-      for (int dx = 0; dx < 3; ++dx) hv[dy * 3 + dx] = hh[dy * kSHX + dx];
+      for (int dx = 0; dx < 3; ++dx) hv[dy * 3 + dx] = hh[dy * RS + dx];
 #pragma unroll
     for (int o = 0; o < 3; ++o) {
       const float d = s_dz[o * 256 + q];
@@ -741,6 +747,194 @@ __global__ void __launch_bounds__(256, 3) k_conv3_mid(ConvArgs a) {
     __syncthreads();
   }
   conv_wgrad_store(wacc, s_all, a.part);
+}
+
+// NR = 2 in a pass with gradients: the three 3x3 kernels above in one.  On 8 x 32 tiles,
+// from h_0 staged with a 3-pixel halo and x with a 1-pixel halo (replicate-clamped):
+//   A: h_1 = h_0 + ReLU(conv_0(h_0) + b_0) on the tile and a 2-pixel halo, and the sign of
+//      layer 0's pre-activation z_0 on the tile;
+//   B: x_hat = h_1 + conv_1(h_1) + b_1 and g = dL/dx_hat = 2 (x_hat - x) / (3HW) on the tile
+//      and a 1-pixel halo (the halo's g is recomputed, not read back); x_hat, g and the
+//      distortion partial of the tile;
+//   C: on the tile, layer 1's weight gradient (g (x) h_1), its input gradient
+//      dh = g + conv_1^T(g), layer 0's pre-activation gradient dz = [z_0 > 0] dh and weight
+//      gradient (dz (x) h_0).  dh and dz go to HBM for the 1x1 backward.
+// A halo position is computed at its clamped pixel, so that it holds what the replicate
+// padding of the next layer reads.  Neither h_1 nor the halo's g leaves the CTA.
+constexpr int kP3X = kSTX + 7, kP3S = (kSTY + 6) * kP3X + 1;   // h_0 with a 3-pixel halo
+constexpr int kP2X = kSTX + 5, kP2S = (kSTY + 4) * kP2X + 1;   // h_1 with a 2-pixel halo
+struct PairSmem {
+  static constexpr int H0 = 0, H1 = H0 + 3 * kP3S, G = H1 + 3 * kP2S, X = G + 3 * kSHS,
+                       DZ1 = X + 3 * kSHS, DZ0 = DZ1 + 768, M0 = DZ0 + 768, END = M0 + 768;
+  static constexpr int FLOATS = END > kWG * 84 ? END : kWG * 84;
+};
+
+// Element i = threadIdx.x + 256 k of the 3 x (kSTY + 2 HALO) x (kSTX + 2 HALO) region around
+// a tile, clamped to the image, without per-thread index tables (register budget).
+template <int HALO, int RS, int CS>
+struct HaloLoad {
+  static constexpr int R = kSTY + 2 * HALO, C = kSTX + 2 * HALO, N = 3 * R * C;
+  static constexpr int K = (N + 255) / 256;
+  static_assert(C <= RS && R * RS <= CS, "halo region does not fit its layout");
+  static __device__ __forceinline__ void load(float (&v)[K], const float* __restrict__ h,
+                                              int y0, int x0, int H, int W) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int i = threadIdx.x + 256 * k;
+      const int ci = i / (R * C), rc = i - ci * (R * C);
+      const int r = rc / C, c = rc - r * C;
+      const int gy = clampi(y0 - HALO + r, 0, H - 1), gx = clampi(x0 - HALO + c, 0, W - 1);
+      // past the region (i >= N) the address stays inside the three planes
+      v[k] = i < N ? __ldg(h + (ci < 3 ? ci : 2) * H * W + gy * W + gx) : 0.f;
+    }
+  }
+  static __device__ __forceinline__ void store(float* s, const float (&v)[K]) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int i = threadIdx.x + 256 * k;
+      const int ci = i / (R * C), rc = i - ci * (R * C);
+      const int r = rc / C, c = rc - r * C;
+      if (i < N) s[ci * CS + r * RS + c] = v[k];
+    }
+  }
+};
+
+// the 27 inputs of a 3x3 layer at a pixel whose clamped tap rows and columns are rr, cc in
+// a staged layout of rows RS and channels CS floats apart
+template <int RS, int CS>
+__device__ __forceinline__ void gather_at(float (&v)[27], const float* s, const int (&rr)[3],
+                                          const int (&cc)[3]) {
+#pragma unroll
+  for (int ci = 0; ci < 3; ++ci)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx)
+        v[ci * 9 + dy * 3 + dx] = s[ci * CS + rr[dy] * RS + cc[dx]];
+}
+
+__global__ void __launch_bounds__(256, 2) k_conv3_pair(ConvArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  using L3 = HaloLoad<3, kP3X, kP3S>;
+  using L1 = HaloLoad<1, kSHX, kSHS>;
+  __shared__ float s_all[PairSmem::FLOATS];
+  __shared__ float s_tmp[8];
+  float* s_h0 = s_all + PairSmem::H0;
+  float* s_h1 = s_all + PairSmem::H1;
+  float* s_g = s_all + PairSmem::G;
+  float* s_x = s_all + PairSmem::X;
+  float* s_dz1 = s_all + PairSmem::DZ1;
+  float* s_dz0 = s_all + PairSmem::DZ0;
+  float* s_m0 = s_all + PairSmem::M0;
+  const int H = a.t.H, W = a.t.W, HW = H * W;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float dsum = 0.f;
+  float w1[30], w0[30];
+#pragma unroll
+  for (int k = 0; k < 30; ++k) w1[k] = w0[k] = 0.f;
+  float n3[L3::K], n1[L1::K];
+  if (blockIdx.x < a.t.n_tiles) {
+    int y0, x0;
+    tile_xy(a.t, blockIdx.x, y0, x0);
+    L3::load(n3, a.hin, y0, x0, H, W);
+    L1::load(n1, a.x, y0, x0, H, W);
+  }
+  for (int tile = blockIdx.x; tile < a.t.n_tiles; tile += gridDim.x) {
+    int y0, x0;
+    tile_xy(a.t, tile, y0, x0);
+    L3::store(s_h0, n3);
+    L1::store(s_x, n1);
+    __syncthreads();
+    if (tile + (int)gridDim.x < a.t.n_tiles) {
+      int ny0, nx0;
+      tile_xy(a.t, tile + gridDim.x, ny0, nx0);
+      L3::load(n3, a.hin, ny0, nx0, H, W);
+      L1::load(n1, a.x, ny0, nx0, H, W);
+    }
+    // A: h_1 over the tile and a 2-pixel halo
+    for (int i = threadIdx.x; i < (kSTY + 4) * (kSTX + 4); i += 256) {
+      const int r = i / (kSTX + 4), c = i - r * (kSTX + 4);
+      const int py = clampi(y0 - 2 + r, 0, H - 1), px = clampi(x0 - 2 + c, 0, W - 1);
+      int rr[3], cc[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        rr[d] = clampi(py + d - 1, 0, H - 1) - (y0 - 3);
+        cc[d] = clampi(px + d - 1, 0, W - 1) - (x0 - 3);
+      }
+      float v[27], z[3];
+      gather_at<kP3X, kP3S>(v, s_h0, rr, cc);
+      conv_z<0>(z, v);
+#pragma unroll
+      for (int o = 0; o < 3; ++o) s_h1[o * kP2S + r * kP2X + c] = v[o * 9 + 4] + fmaxf(z[o], 0.f);
+      const int qy = r - 2, qx = c - 2;
+      if ((unsigned)qy < (unsigned)kSTY && (unsigned)qx < (unsigned)kSTX) {
+#pragma unroll
+        for (int o = 0; o < 3; ++o) s_m0[o * 256 + qy * kSTX + qx] = z[o] > 0.f ? 1.f : 0.f;
+      }
+    }
+    __syncthreads();
+    // B: x_hat and g over the tile and a 1-pixel halo
+    for (int i = threadIdx.x; i < (kSTY + 2) * (kSTX + 2); i += 256) {
+      const int r = i / (kSTX + 2), c = i - r * (kSTX + 2);
+      const int py = clampi(y0 - 1 + r, 0, H - 1), px = clampi(x0 - 1 + c, 0, W - 1);
+      int rr[3], cc[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        rr[d] = clampi(py + d - 1, 0, H - 1) - (y0 - 2);
+        cc[d] = clampi(px + d - 1, 0, W - 1) - (x0 - 2);
+      }
+      float v[27], z[3];
+      gather_at<kP2X, kP2S>(v, s_h1, rr, cc);
+      conv_z<1>(z, v);
+      const int qy = r - 1, qx = c - 1;
+      const bool in_tile = (unsigned)qy < (unsigned)kSTY && (unsigned)qx < (unsigned)kSTX;
+      const bool valid = in_tile && y0 + qy < H && x0 + qx < W;
+#pragma unroll
+      for (int o = 0; o < 3; ++o) {
+        const float xh = v[o * 9 + 4] + z[o];
+        const float d = xh - s_x[o * kSHS + r * kSHX + c];
+        const float g = d * a.dscale;
+        s_g[o * kSHS + r * kSHX + c] = g;
+        if (in_tile) s_dz1[o * 256 + qy * kSTX + qx] = valid ? g : 0.f;
+        if (valid) {
+          const int p = o * HW + (y0 + qy) * W + x0 + qx;
+          a.hout[p] = xh;
+          a.dxhat[p] = g;
+          dsum = fmaf(d, d, dsum);
+        }
+      }
+    }
+    __syncthreads();
+    // C: layer 1's weight gradient, its input gradient, layer 0's pre-activation gradient
+    conv_wgrad<kP2X, kP2S>(w1, s_dz1, s_h1 + kP2X + 1);
+    {
+      const int y = y0 + ty, x = x0 + tx;
+      float dz[3] = {0.f, 0.f, 0.f};
+      if (y < H && x < W) {
+        float dh[3];
+#pragma unroll
+        for (int ci = 0; ci < 3; ++ci) dh[ci] = s_g[ci * kSHS + (ty + 1) * kSHX + tx + 1];
+        conv_adjoint<1>(dh, s_g, ty, tx, y, x, y0, x0, H, W);
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+          dz[o] = s_m0[o * 256 + threadIdx.x] > 0.f ? dh[o] : 0.f;
+          const int p = o * HW + y * W + x;
+          a.dh[p] = dh[o];
+          a.dz[p] = dz[o];
+        }
+      }
+#pragma unroll
+      for (int o = 0; o < 3; ++o) s_dz0[o * 256 + threadIdx.x] = dz[o];
+    }
+    __syncthreads();
+    conv_wgrad<kP3X, kP3S>(w0, s_dz0, s_h0 + 2 * kP3X + 2);
+    __syncthreads();
+  }
+  const float t = block_sum<256>(dsum, s_tmp);
+  if (threadIdx.x == 0) a.part_d[blockIdx.x] = t;
+  conv_wgrad_store(w1, s_all, a.part + (size_t)gridDim.x * 84);
+  conv_wgrad_store(w0, s_all, a.part);
 }
 
 // ------------------------------------------------------------------ synthesis 1x1 layers
@@ -1058,7 +1252,7 @@ int syn_tile_count(const Geo& g) { return tile_geo(g).n_tiles; }
 
 cudaError_t syn_forward(const Arch& ar, const Geo& g, const float* yhat, const UpPlan& up,
                         const float* x, float* hbuf, float* dxhat, float* part_d,
-                        float* part_conv, int grid, cudaStream_t st) {
+                        float* part_conv, int grid, cudaStream_t st, float* dh, float* dz) {
   const int HW = g.H * g.W;
   Syn1x1Args s = make_1x1(g, yhat, up);
   s.h2 = hbuf;
@@ -1080,6 +1274,13 @@ cudaError_t syn_forward(const Arch& ar, const Geo& g, const float* yhat, const U
   c.hin = hbuf;
   c.hout = hbuf + (size_t)3 * HW;
   if (ar.NR == 1) return launch_k(k_conv3_last<0>, dim3(grid), dim3(256), 0, st, c);
+  if (dh && dz) {
+    c.hout = hbuf + (size_t)6 * HW;
+    c.dh = dh;
+    c.dz = dz;
+    c.part = part_conv;
+    return launch_k(k_conv3_pair, dim3(grid), dim3(256), 0, st, c);
+  }
   if ((e = launch_k(k_conv3_fwd<0>, dim3(grid), dim3(256), 0, st, c)) != cudaSuccess) return e;
   c.hin = hbuf + (size_t)3 * HW;
   c.hout = hbuf + (size_t)6 * HW;
@@ -1089,7 +1290,7 @@ cudaError_t syn_forward(const Arch& ar, const Geo& g, const float* yhat, const U
 // dhbuf holds NR + 1 gradient planes-of-3: dhbuf[NR] = dL/dx_hat (written by the forward).
 cudaError_t syn_backward(const Arch& ar, const Geo& g, const float* yhat, const UpPlan& up,
                          float* hbuf, float* dhbuf, float* dz, float* gsyn, float* part_conv,
-                         float* part_syn, int grid, cudaStream_t st) {
+                         float* part_syn, int grid, cudaStream_t st, bool convs_done) {
   const int HW = g.H * g.W;
   const float* dxhat = dhbuf + (size_t)ar.NR * 3 * HW;
   Syn1x1Args s = make_1x1(g, yhat, up);
@@ -1102,8 +1303,10 @@ cudaError_t syn_backward(const Arch& ar, const Geo& g, const float* yhat, const 
     c.dh = dhbuf + (size_t)3 * HW;
     c.dz = dz;
     c.part = part_conv;
-    cudaError_t e = launch_k(k_conv3_mid, dim3(grid), dim3(256), 0, st, c);
-    if (e != cudaSuccess) return e;
+    if (!convs_done) {
+      cudaError_t e = launch_k(k_conv3_mid, dim3(grid), dim3(256), 0, st, c);
+      if (e != cudaSuccess) return e;
+    }
     s.dhout = c.dh;
     s.dz0 = dz;
   } else {

@@ -20,9 +20,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 KERNELS = ["k_arm_fb", "k_arm_fwd", "k_arm_image", "k_syn_image", "k_quantize", "k_up_fwd", "k_up_bwd",
-           "k_syn1x1_fwd", "k_syn1x1_bwd", "k_conv3_fwd", "k_conv3_last", "k_conv3_mid",
+           "k_syn1x1_fwd", "k_syn1x1_bwd", "k_conv3_fwd", "k_conv3_last", "k_conv3_mid", "k_conv3_pair",
            "k_ctx_gather", "k_reduce_sections", "k_param_update", "k_latent_update", "k_finish",
-           "k_image_to_planar", "k_planar_to_hwc", "k_rate_noalloc", "k_sum_tiles"]
+           "k_image_to_planar", "k_planar_to_hwc", "k_rate_noalloc", "k_sum_tiles",
+           "finish_begin", "finish_end", "param_block_done"]
 
 
 class TraceRec(ctypes.Structure):

@@ -27,3 +27,11 @@ def test_arm_flops_per_launch():
     # forward, input gradient and weight gradient: three passes of 2 FLOP per MAC
     assert bench.arm_flops_per_launch(d, n_lat) == pytest.approx(6 * per_latent * n_lat, rel=1e-12)
     assert per_latent == pytest.approx(1200) and n_lat == 524256
+
+
+def test_arm_traffic_tied_to_profiled_sources(monkeypatch):
+    """The ARM kernel's DRAM bytes are reported only for the sources they were measured on."""
+    monkeypatch.setattr(bench, "ARM_COUNTER_SOURCES_SHA256", bench.arm_sources_sha256())
+    assert bench.arm_traffic() == bench.ARM_DRAM_BYTES_PER_LAUNCH
+    monkeypatch.setattr(bench, "ARM_COUNTER_SOURCES_SHA256", "0" * 64)
+    assert bench.arm_traffic() is None
