@@ -315,8 +315,11 @@ int cc_decode_bitstream(const uint8_t* bs, size_t nbytes, void* cuda_stream,
  * 1 .. 4, and a 3x3 stride-1 convolution of the image giving level 0; levels 5 and 6 are
  * 0.  It is trained on latents the encoder reached (loss: the sum over levels 0 .. 4 of
  * each level's mean squared error), with Adam (beta 0.9 / 0.999, eps 1e-8,
- * bias-corrected).  FP32.  Every cc_warm_* call runs on the stream given at creation; one
- * predictor is not used from two threads at once.
+ * bias-corrected).  The three 32-to-32-channel convolutions run on the tensor cores with
+ * BF16 operands (inputs, weights and output gradients rounded to nearest BF16, ties to
+ * even) and FP32 accumulation, in the forward pass and both gradients; the rest is FP32.
+ * Every cc_warm_* call runs on the stream given at creation; one predictor is not used
+ * from two threads at once.
  * Flat parameter order: c1 (W 32 x 3 x 3 x 3, b 32), c2 .. c4 (W 32 x 32 x 3 x 3, b 32),
  * heads 1 .. 4 (W 32, b 1), head 0 (W 3 x 3 x 3, b 1).
  * cc_warm_create: predictor for H x W images (H, W >= 16); params (host or device,
@@ -326,11 +329,14 @@ int cc_decode_bitstream(const uint8_t* bs, size_t nbytes, void* cuda_stream,
  * cc_warm_loss_grad: loss against target latents (host or device, flat latent order;
  *   levels 5, 6 ignored) and, if grads_out is not NULL, its gradient (host or device,
  *   flat parameter order).  Synchronises.
- * cc_warm_train_step: cc_warm_loss_grad then one Adam step with learning rate lr (queued
- *   on the stream; the next call, or cc_warm_get_params, sees it).
+ * cc_warm_train_step: the loss and its gradient, then one Adam step with learning rate
+ *   lr, queued on the stream (the next call, or cc_warm_get_params, sees it).  With loss
+ *   in host memory it synchronises, writes the loss and takes no step on a non-finite
+ *   one; with loss in device memory the loss is copied there on the stream, and with loss
+ *   NULL it is not written: neither synchronises nor checks.
  * Errors: CC_EINVAL (NULL pointer, H or W outside 16 .. 16384), CC_ENOMEM, CC_ECUDA,
  *   CC_ENONFINITE (loss not finite: *loss written, no gradient copied out, no Adam
- *   step taken). */
+ *   step taken), CC_ETIMEOUT (a bounded tensor-core wait gave up; results invalid). */
 typedef struct cc_warm cc_warm;
 int cc_warm_param_count(int* n_params);
 int cc_warm_create(int H, int W, const float* params, void* cuda_stream, cc_warm** out);

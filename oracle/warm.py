@@ -36,16 +36,49 @@ def param_shapes():
     return out
 
 
-def forward(x: torch.Tensor, P: dict):
-    """x: [3, H, W] -> [latent level 0 .. 4] (each [h_l, w_l])."""
+def to_bf16(t: torch.Tensor) -> torch.Tensor:
+    """t rounded to the nearest BF16 value (8 significand bits, ties to even), kept in FP64."""
+    return t.to(torch.bfloat16).to(DT)
+
+
+class ConvBF16(torch.autograd.Function):
+    """conv2d with stride 2 and zero padding 1 whose operands are rounded to BF16 wherever
+    the convolution is evaluated: the forward pass rounds the input and the weights, the
+    backward pass rounds the output gradient and uses the rounded input and weights for the
+    input gradient, the weight gradient and the bias gradient (the sum of the rounded output
+    gradient).  Every sum is FP64.  This is the arithmetic of the tensor-core layers
+    (BF16 operands, wide accumulation)."""
+
+    @staticmethod
+    def forward(ctx, a, w, b):
+        ab, wb = to_bf16(a), to_bf16(w)
+        ctx.save_for_backward(ab, wb)
+        return F.conv2d(ab, wb, b, stride=2, padding=1)
+
+    @staticmethod
+    def backward(ctx, g):
+        ab, wb = ctx.saved_tensors
+        gb = to_bf16(g)
+        da = torch.nn.grad.conv2d_input(ab.shape, wb, gb, stride=2, padding=1)
+        dw = torch.nn.grad.conv2d_weight(ab, wb.shape, gb, stride=2, padding=1)
+        return da, dw, gb.sum(dim=(0, 2, 3))
+
+
+def forward(x: torch.Tensor, P: dict, bf16: bool = False):
+    """x: [3, H, W] -> [latent level 0 .. 4] (each [h_l, w_l]).  With bf16, the 32-to-32
+    channel convolutions (conv 2 .. 4) take BF16-rounded operands (ConvBF16)."""
     a = x.unsqueeze(0)
     lv = [F.conv2d(a, P["h0.w"], P["h0.b"], stride=1, padding=1)[0, 0]]
     for i in (1, 2, 3, 4):
-        a = torch.relu(F.conv2d(a, P[f"c{i}.w"], P[f"c{i}.b"], stride=2, padding=1))
+        if bf16 and i > 1:
+            z = ConvBF16.apply(a, P[f"c{i}.w"], P[f"c{i}.b"])
+        else:
+            z = F.conv2d(a, P[f"c{i}.w"], P[f"c{i}.b"], stride=2, padding=1)
+        a = torch.relu(z)
         lv.append(F.conv2d(a, P[f"h{i}.w"], P[f"h{i}.b"])[0, 0])
     return lv
 
 
-def loss(x: torch.Tensor, P: dict, targets):
+def loss(x: torch.Tensor, P: dict, targets, bf16: bool = False):
     """sum over the predicted levels of the mean squared error."""
-    return sum(((p - t) ** 2).mean() for p, t in zip(forward(x, P), targets))
+    return sum(((p - t) ** 2).mean() for p, t in zip(forward(x, P, bf16), targets))

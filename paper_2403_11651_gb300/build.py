@@ -27,7 +27,8 @@ LIB = os.path.join(BUILD, "libcoolchic.so")
 TRACE_LIB = os.path.join(BUILD, "libcoolchic_trace.so")
 SOURCES = ["cc_arm.cu", "cc_syn.cu", "cc_iter.cu", "cc_capi.cu", "cc_noalloc.cu", "cc_codec.cu", "cc_warm.cu"]
 HEADERS = [os.path.join(CSRC, "cc_internal.cuh"), os.path.join(CSRC, "cc_laplace.cuh"),
-           os.path.join(CSRC, "cc_tc.cuh"), os.path.join(ROOT, "include", "coolchic.h")]
+           os.path.join(CSRC, "cc_tc.cuh"), os.path.join(CSRC, "cc_tc16.cuh"),
+           os.path.join(ROOT, "include", "coolchic.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-Xcompiler", "-ffp-contract=off"]

@@ -501,11 +501,22 @@ def cc_warm_loss_grad(w, rgb_hwc, target_latents, grads_out=None) -> float:
     return loss.value
 
 
-def cc_warm_train_step(w, rgb_hwc, target_latents, lr: float) -> float:
+def cc_warm_train_step(w, rgb_hwc, target_latents, lr: float, with_loss: bool = True,
+                       loss_out=None):
+    """One training step.  Returns the loss (synchronising); with loss_out (a device
+    float64 tensor, or its element) the loss is written there on the stream and None is
+    returned; with with_loss=False nothing is written (queued only)."""
+    if loss_out is not None:
+        _check(_lib().cc_warm_train_step(w, _ptr(rgb_hwc), _ptr(target_latents), float(lr),
+                                         ctypes.cast(ctypes.c_void_p(loss_out.data_ptr()),
+                                                     POINTER(c_double))),
+               "cc_warm_train_step")
+        return None
     loss = c_double()
     _check(_lib().cc_warm_train_step(w, _ptr(rgb_hwc), _ptr(target_latents), float(lr),
-                                     ctypes.byref(loss)), "cc_warm_train_step")
-    return loss.value
+                                     ctypes.byref(loss) if with_loss else None),
+           "cc_warm_train_step")
+    return loss.value if with_loss else None
 
 
 def cc_warm_get_params(w, out=None):

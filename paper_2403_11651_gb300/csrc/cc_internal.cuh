@@ -139,6 +139,22 @@ struct SectionTable {
   int n;
 };
 
+// a + b as the unevaluated pair (s, e) with s + e = a + b exactly (Knuth's TwoSum)
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = a + b, v = s - a;
+  return make_float2(s, (a - (s - v)) + (b - v));
+}
+
+// (a.x + a.y) + (b.x + b.y) in float-float arithmetic (Dekker): the exact sum of the high
+// parts plus the low parts, renormalised.  For sums of non-negative terms the relative
+// error is a few units of 2^-44.
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float2 s = two_sum(a.x, b.x);
+  const float e = s.y + (a.y + b.y);
+  const float h = s.x + e;
+  return make_float2(h, e - (h - s.x));
+}
+
 // Scalars of the current iteration, written on the device.
 struct IterScalars {
   int t;              // index of the current iteration (0-based)

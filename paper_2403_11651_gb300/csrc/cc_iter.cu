@@ -197,22 +197,6 @@ cudaError_t adam_bc_upload(cudaStream_t st) {
                                  cudaMemcpyHostToDevice, st);
 }
 
-// a + b as the unevaluated pair (s, e) with s + e = a + b exactly (Knuth's TwoSum)
-__device__ __forceinline__ float2 two_sum(float a, float b) {
-  const float s = a + b, v = s - a;
-  return make_float2(s, (a - (s - v)) + (b - v));
-}
-
-// (a.x + a.y) + (b.x + b.y) in float-float arithmetic (Dekker): the exact sum of the high
-// parts plus the low parts, renormalised.  For the non-negative partial sums added here
-// the relative error is a few units of 2^-44.
-__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
-  const float2 s = two_sum(a.x, b.x);
-  const float e = s.y + (a.y + b.y);
-  const float h = s.x + e;
-  return make_float2(h, e - (h - s.x));
-}
-
 // D, R and the loss of the pass from the per-CTA partial sums, and the loss log entry of
 // iteration t.  The partials are summed in float-float arithmetic over 256 virtual lanes
 // (all loads of a lane issued together) and a tree, in a fixed order; run by one block of

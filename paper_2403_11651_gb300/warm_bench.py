@@ -201,19 +201,27 @@ def experiment(a, pool):
     dec = (dec_sum / n_train).astype(np.float32)
     t_data = time.perf_counter() - t0
 
-    # 2. the predictor
+    # 2. the predictor: training pairs resident in device memory, one loss per step written
+    # to device memory, read once per epoch
+    import torch
     w = cc.cc_warm_create(S, S, syn.warm_initial_parameters(0))
     wt = None
     try:
+        d_img = torch.from_numpy(np.stack(images)).cuda()
+        d_lat = torch.from_numpy(np.stack(lat)).cuda()
+        d_loss = torch.zeros(n_train, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         losses = []
         order = np.random.default_rng(0)
         for ep in range(a.epochs):
-            tot = 0.0
             for i in order.permutation(n_train):
-                tot += cc.cc_warm_train_step(w, images[i], lat[i], a.lr)
-            losses.append(tot / n_train)
+                cc.cc_warm_train_step(w, d_img[i], d_lat[i], a.lr, loss_out=d_loss[i])
+            losses.append(float(d_loss.mean()))
+            if not np.isfinite(losses[-1]):
+                raise RuntimeError(f"predictor loss not finite in epoch {ep}")
         t_train = time.perf_counter() - t0
+        t_step_ms = t_train / max(1, a.epochs * n_train) * 1e3
         if (TH, TW) == (S, S):
             wt = w
         else:
@@ -277,7 +285,7 @@ def experiment(a, pool):
                     f"{TH}x{TW} images, 2300-MAC decoder, {a.iters} iterations (last 20 % "
                     f"straight-through); ablations on {n_ablate} held-out images",
         "train_requested": a.train, "epochs": a.epochs, "lr": a.lr,
-        "data_s": t_data, "predictor_train_s": t_train,
+        "data_s": t_data, "predictor_train_s": t_train, "predictor_step_ms": t_step_ms,
         "predictor_loss_first_last_epoch": [losses[0], losses[-1]],
         "reached": sum(h is not None for h in hits), "of": len(hits),
         "mean_iters_to_plain_final": float(np.mean([h for h in hits if h is not None]))

@@ -1,5 +1,14 @@
-"""Warm-start predictor on the GPU against the FP64 oracle (oracle/warm.py): forward,
-loss and every parameter gradient; Adam steps lower the loss."""
+"""Warm-start predictor on the GPU against the oracle (oracle/warm.py) in its BF16 reading
+(conv 2 .. 4 on BF16 operands, every sum FP64): forward, loss and every parameter
+gradient; Adam steps lower the loss.
+
+Tolerances: the GPU accumulates in FP32 (relative 1e-6 over 288 terms), and where its FP32
+value of an operand and the oracle's FP64 value fall on two sides of a BF16 rounding
+boundary (a few elements per layer at these sizes) one operand differs by one BF16 unit
+(2^-8 relative).  Predictions within 1e-3 of the largest value, the loss within
+relative 1e-4, every parameter-gradient group within 2e-3 of its largest entry.  The
+prediction of levels 2 .. 4 must also be at least three times closer to the BF16 reading
+than to the FP64 one: the tensor-core layers really take BF16 operands."""
 import numpy as np
 import pytest
 import torch
@@ -41,23 +50,28 @@ def test_forward_loss_gradients(H, W, seed):
         cc.cc_warm_free(w)
     x = torch.tensor(rgb.astype(np.float64) / 255.0).permute(2, 0, 1).contiguous()
     P = _oracle(flat)
-    ref = ow.forward(x, P)
+    ref = ow.forward(x, P, bf16=True)
+    ref64 = ow.forward(x, P)
     k = 0
     for l, (h, ww) in enumerate(shapes):
         got = pred[k:k + h * ww].reshape(h, ww)
         if l < 5:
             r = ref[l].detach().numpy()
-            assert np.abs(got - r).max() <= 1e-5 * max(1.0, float(np.abs(r).max()))
+            err = np.abs(got - r).max()
+            assert err <= 1e-3 * max(1.0, float(np.abs(r).max())), (l, err)
+            if l >= 2:
+                err64 = np.abs(got - ref64[l].detach().numpy()).max()
+                assert 3 * err <= err64, (l, err, err64)
         else:
             assert not got.any()
         k += h * ww
-    L = ow.loss(x, P, [torch.tensor(t.astype(np.float64)) for t in target[:5]])
+    L = ow.loss(x, P, [torch.tensor(t.astype(np.float64)) for t in target[:5]], bf16=True)
     L.backward()
-    assert abs(loss - float(L)) <= 1e-5 * float(L)
+    assert abs(loss - float(L)) <= 1e-4 * float(L)
     k = 0
     for name, shape in ow.param_shapes():
         n = int(np.prod(shape))
-        assert_group_close(g[k:k + n].reshape(shape), P[name].grad.numpy(), 1e-4, name)
+        assert_group_close(g[k:k + n].reshape(shape), P[name].grad.numpy(), 2e-3, name)
         k += n
 
 
@@ -106,3 +120,33 @@ def test_host_and_device_buffers_agree():
     assert l_host == l_dev
     assert np.array_equal(g_host, g_dev.cpu().numpy())
     assert np.array_equal(p_host, p_dev.cpu().numpy())
+
+
+def test_train_step_loss_destinations_agree():
+    """A training step replays captured graphs; the loss can go to host memory (checked,
+    synchronising), to device memory (queued) or nowhere.  All three give the same
+    parameters bit for bit, and the same losses."""
+    H, W = 40, 72
+    flat = syn.warm_initial_parameters(7)
+    rgb = torch.from_numpy(syn.synthetic_image(H, W, 7)).cuda()
+    n_lat = sum(-(-H // (1 << l)) * -(-W // (1 << l)) for l in range(7))
+    tgt = torch.from_numpy(np.random.default_rng(7).normal(0, 1.0, n_lat).astype(np.float32)).cuda()
+    d_loss = torch.zeros(6, dtype=torch.float64, device="cuda")
+    out, host = [], []
+    for mode in ("host", "device", "none"):
+        w = cc.cc_warm_create(H, W, flat)
+        try:
+            for k in range(6):
+                lr = 1e-3 if k < 3 else 5e-4
+                if mode == "host":
+                    host.append(cc.cc_warm_train_step(w, rgb, tgt, lr))
+                elif mode == "device":
+                    cc.cc_warm_train_step(w, rgb, tgt, lr, loss_out=d_loss[k])
+                else:
+                    cc.cc_warm_train_step(w, rgb, tgt, lr, with_loss=False)
+            out.append(cc.cc_warm_get_params(w))
+        finally:
+            cc.cc_warm_free(w)
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+    assert host == d_loss.cpu().tolist()
+    assert not np.array_equal(out[0], flat)

@@ -127,3 +127,83 @@ def test_forward_wiring_by_loops(H, W):
     got = ow.forward(torch.tensor(x, dtype=ow.DT), P)
     for l in range(5):
         np.testing.assert_allclose(got[l].detach().numpy(), want[l], rtol=1e-12, atol=1e-12)
+
+
+# ---- the BF16 reading of the tensor-core layers (conv 2 .. 4)
+
+def test_bf16_rounding_is_nearest_even():
+    """to_bf16 keeps 8 significand bits, rounding to nearest with ties to even; an FP64
+    value goes through FP32 first (the GPU rounds its FP32 activations)."""
+    u = 2.0 ** -7                                   # BF16 spacing just above 1
+    cases = [(1.0 + u / 2, 1.0),                    # tie, 1.0 is even
+             (1.0 + 3 * u / 2, 1.0 + 2 * u),        # tie, 1 + 2u is even
+             (1.0 + u / 2 + 2.0 ** -20, 1.0 + u),   # above the tie
+             (1.0 + u / 2 - 2.0 ** -20, 1.0),       # below the tie
+             (-(1.0 + 3 * u / 2), -(1.0 + 2 * u)),
+             (1.0 + u / 2 + 2.0 ** -40, 1.0),       # within FP32 rounding of the tie
+             (0.75, 0.75), (0.0, 0.0)]
+    got = ow.to_bf16(torch.tensor([c for c, _ in cases], dtype=torch.float64)).tolist()
+    assert got == [e for _, e in cases]
+
+
+def _bf16_rand(shape, gen):
+    return ow.to_bf16(torch.randn(shape, generator=gen, dtype=torch.float64))
+
+
+def test_bf16_conv_is_the_plain_conv_on_bf16_values():
+    """With input, weights and output gradient already BF16 values the rounding does
+    nothing: ConvBF16 equals the plain stride-2 convolution and its gradients."""
+    gen = torch.Generator().manual_seed(3)
+    a = _bf16_rand((1, 32, 11, 14), gen).requires_grad_(True)
+    w = _bf16_rand((32, 32, 3, 3), gen).requires_grad_(True)
+    b = torch.randn(32, generator=gen, dtype=torch.float64).requires_grad_(True)
+    g = _bf16_rand((1, 32, 6, 7), gen)
+    out = ow.ConvBF16.apply(a, w, b)
+    da, dw, db = torch.autograd.grad(out, (a, w, b), g)
+    ref = torch.nn.functional.conv2d(a, w, b, stride=2, padding=1)
+    ra, rw, rb = torch.autograd.grad(ref, (a, w, b), g)
+    assert torch.allclose(out, ref, rtol=1e-13, atol=1e-13)
+    for x, y in ((da, ra), (dw, rw), (db, rb)):
+        assert torch.allclose(x, y, rtol=1e-12, atol=1e-12)
+
+
+def test_bf16_conv_rounds_every_operand():
+    """On general values the forward moves by no more than the operands' rounding allows
+    (relative 2^-9 each, so 2^-8 + 2^-18 per product), and does move; the backward uses the
+    rounded output gradient: it equals the plain gradients of the rounded operands taken
+    with the rounded output gradient, and differs from those with the unrounded one."""
+    gen = torch.Generator().manual_seed(4)
+    a = torch.randn((1, 32, 9, 10), generator=gen, dtype=torch.float64)
+    w = torch.randn((32, 32, 3, 3), generator=gen, dtype=torch.float64)
+    b = torch.randn(32, generator=gen, dtype=torch.float64)
+    out = ow.ConvBF16.apply(a, w, b)
+    plain = torch.nn.functional.conv2d(a, w, b, stride=2, padding=1)
+    bound = torch.nn.functional.conv2d(a.abs(), w.abs(), None, stride=2, padding=1) * (2.0 ** -8 + 2.0 ** -18)
+    assert bool(((out - plain).abs() <= bound).all())
+    assert float((out - plain).abs().max()) > 0.0
+    g = torch.randn(out.shape, generator=gen, dtype=torch.float64)
+    ar = ow.to_bf16(a).requires_grad_(True)
+    wr = ow.to_bf16(w).requires_grad_(True)
+    br = b.clone().requires_grad_(True)
+    a1, w1, b1 = a.clone().requires_grad_(True), w.clone().requires_grad_(True), b.clone().requires_grad_(True)
+    got = torch.autograd.grad(ow.ConvBF16.apply(a1, w1, b1), (a1, w1, b1), g)
+    ref = torch.autograd.grad(torch.nn.functional.conv2d(ar, wr, br, stride=2, padding=1),
+                              (ar, wr, br), ow.to_bf16(g))
+    unr = torch.autograd.grad(torch.nn.functional.conv2d(ar, wr, br, stride=2, padding=1),
+                              (ar, wr, br), g)
+    for x, y, z in zip(got, ref, unr):
+        assert torch.allclose(x, y, rtol=1e-12, atol=1e-12)
+        assert float((x - z).abs().max()) > 0.0
+
+
+def test_bf16_predictor_close_to_fp64():
+    """The BF16 reading changes the whole predictor's output by about BF16 precision."""
+    x = torch.tensor(syn.synthetic_image(40, 56, 2).astype(np.float64) / 255.0).permute(2, 0, 1)
+    P = _params(2)
+    ref = ow.forward(x, P)
+    got = ow.forward(x, P, bf16=True)
+    assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1])   # FP64 layers
+    for l in (2, 3, 4):
+        d = float((got[l] - ref[l]).abs().max())
+        scale = float(ref[l].abs().max())
+        assert 0.0 < d < 2e-2 * scale, (l, d, scale)
