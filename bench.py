@@ -317,70 +317,74 @@ def run_ours(a, cfgd):
     assert len(read) == n_e2e and all(math.isfinite(v) for v in read)
     e2e_value = replica_throughput(e2e_s * 1e3, world, H, W, n_e2e)
 
-    # the full schedule once, for time to the final RD cost of the plain method
-    ctx2 = cc.cc_init_image(cfg, rgb, H, W, init, stream)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    cc.cc_encode_iters(ctx2, cfgd["total_iters"])
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    full_s = ev0.elapsed_time(ev1) / 1e3
-    final = cc.cc_rd_cost(ctx2, True)
-    # the latent bitstream of the trained image: GPU encode, then GPU decode (each timed
-    # on its second call; the first builds the frequency tables and allocates)
-    for _ in range(2):
-        t0 = time.perf_counter()
-        bs = cc.cc_write_bitstream(ctx2, cfg, H, W)
-        enc_ms = 1e3 * (time.perf_counter() - t0)
-    y_int = np.rint(cc.cc_get_latents(ctx2, n_lat)).astype(np.int32)
-    cc.cc_free(ctx2)
-    for _ in range(2):
-        t0 = time.perf_counter()
-        x_dec, lat, lat_ms = cc.cc_decode_bitstream(bs)
-        dec_ms = 1e3 * (time.perf_counter() - t0)
-    # the bitstream's parts: parameters (and header) against the latent substreams
-    n_params = cc.cc_param_count(cfg)
-    latent_bytes = len(bs) - 20 - 4 * n_params
-    mse = float(np.mean((np.clip(x_dec, 0.0, 1.0).astype(np.float64)
-                         - rgb.astype(np.float64) / 255.0) ** 2))
-    codec = {"workload": f"{H}x{W} after the full schedule", "bytes": len(bs),
-             "bpp": 8.0 * len(bs) / (H * W), "model_rate_bpp": final[1],
-             "parameter_bytes": 4 * n_params, "latent_bytes": latent_bytes,
-             "latent_bpp": 8.0 * latent_bytes / (H * W),
-             "psnr_db": 10.0 * math.log10(1.0 / mse),
-             "encode_ms": enc_ms, "latent_decode_ms": lat_ms,
-             "decode_ms": dec_ms, "latents_exact": bool(np.array_equal(lat, y_int)),
-             "note": "decode_ms: whole cc_decode_bitstream call (context set-up, upload, "
-                     "wavefront latent decode, upsampling and synthesis, image to host); "
-                     "latent_bytes: row lengths and substreams; parameter_bytes: raw float32 "
-                     "(the 20-byte header aside); psnr_db of the decoded image clamped to "
-                     "[0, 1]"}
+    # the legs after the timed iterations (skipped with --main-only, for profiling)
+    legs = not a.main_only
+    full_s = final = codec = c1 = None
+    if legs:
+        # the full schedule once, for time to the final RD cost of the plain method
+        ctx2 = cc.cc_init_image(cfg, rgb, H, W, init, stream)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        cc.cc_encode_iters(ctx2, cfgd["total_iters"])
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        full_s = ev0.elapsed_time(ev1) / 1e3
+        final = cc.cc_rd_cost(ctx2, True)
+        # the latent bitstream of the trained image: GPU encode, then GPU decode (each timed
+        # on its second call; the first builds the frequency tables and allocates)
+        for _ in range(2):
+            t0 = time.perf_counter()
+            bs = cc.cc_write_bitstream(ctx2, cfg, H, W)
+            enc_ms = 1e3 * (time.perf_counter() - t0)
+        y_int = np.rint(cc.cc_get_latents(ctx2, n_lat)).astype(np.int32)
+        cc.cc_free(ctx2)
+        for _ in range(2):
+            t0 = time.perf_counter()
+            x_dec, lat, lat_ms = cc.cc_decode_bitstream(bs)
+            dec_ms = 1e3 * (time.perf_counter() - t0)
+        # the bitstream's parts: parameters (and header) against the latent substreams
+        n_params = cc.cc_param_count(cfg)
+        latent_bytes = len(bs) - 20 - 4 * n_params
+        mse = float(np.mean((np.clip(x_dec, 0.0, 1.0).astype(np.float64)
+                             - rgb.astype(np.float64) / 255.0) ** 2))
+        codec = {"workload": f"{H}x{W} after the full schedule", "bytes": len(bs),
+                 "bpp": 8.0 * len(bs) / (H * W), "model_rate_bpp": final[1],
+                 "parameter_bytes": 4 * n_params, "latent_bytes": latent_bytes,
+                 "latent_bpp": 8.0 * latent_bytes / (H * W),
+                 "psnr_db": 10.0 * math.log10(1.0 / mse),
+                 "encode_ms": enc_ms, "latent_decode_ms": lat_ms,
+                 "decode_ms": dec_ms, "latents_exact": bool(np.array_equal(lat, y_int)),
+                 "note": "decode_ms: whole cc_decode_bitstream call (context set-up, upload, "
+                         "wavefront latent decode, upsampling and synthesis, image to host); "
+                         "latent_bytes: row lengths and substreams; parameter_bytes: raw float32 "
+                         "(the 20-byte header aside); psnr_db of the decoded image clamped to "
+                         "[0, 1]"}
 
-    # the first configuration (256 x 256, 8-input ARM): latency-bound, reported for context
-    d1 = cc.load_config("c1")
-    cfg1 = cc.make_config(d1, seed=rank)
-    rgb1 = syn.synthetic_image(d1["H"], d1["W"], rank)
-    ctx1 = cc.cc_init_image(cfg1, rgb1, d1["H"], d1["W"], None, stream)
-    cc.cc_encode_iters(ctx1, a.warmup)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n1 = 200
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    cc.cc_encode_iters(ctx1, n1)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    c1_ms = e0.elapsed_time(e1) / n1
-    cc.cc_free(ctx1)
-    c1 = {"workload": f"{d1['H']}x{d1['W']} synthetic image, first configuration "
-                      f"(ARM 8-8-8-2, 8x8 upsampling, synthesis 7-8-3 + 2 x 3x3)",
-          "ms_per_iter": c1_ms, "value": d1["H"] * d1["W"] / (c1_ms * 1e3), "unit": UNIT,
-          "note": f"{n1} iterations back to back in CUDA graphs, L2 not flushed (the whole "
-                  f"state fits in L2); latency-bound"}
+        # the first configuration (256 x 256, 8-input ARM): latency-bound, reported for context
+        d1 = cc.load_config("c1")
+        cfg1 = cc.make_config(d1, seed=rank)
+        rgb1 = syn.synthetic_image(d1["H"], d1["W"], rank)
+        ctx1 = cc.cc_init_image(cfg1, rgb1, d1["H"], d1["W"], None, stream)
+        cc.cc_encode_iters(ctx1, a.warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n1 = 200
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        cc.cc_encode_iters(ctx1, n1)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        c1_ms = e0.elapsed_time(e1) / n1
+        cc.cc_free(ctx1)
+        c1 = {"workload": f"{d1['H']}x{d1['W']} synthetic image, first configuration "
+                          f"(ARM 8-8-8-2, 8x8 upsampling, synthesis 7-8-3 + 2 x 3x3)",
+              "ms_per_iter": c1_ms, "value": d1["H"] * d1["W"] / (c1_ms * 1e3), "unit": UNIT,
+              "note": f"{n1} iterations back to back in CUDA graphs, L2 not flushed (the whole "
+                      f"state fits in L2); latency-bound"}
 
     # several small images at once (separately loaded library copies as concurrent lanes)
     # against one at a time; identical final RD costs required
     batch = None
-    if rank == 0:
+    if rank == 0 and legs:
         try:
             from paper_2403_11651_gb300 import batch_bench
             from paper_2403_11651_gb300.batch import autotune
@@ -405,7 +409,7 @@ def run_ours(a, cfgd):
     # learned warm start against plain overfitting on held-out images: iterations and
     # seconds to the plain run's final RD cost (within 1 %)
     warm = None
-    if rank == 0:
+    if rank == 0 and legs:
         try:
             from concurrent.futures import ThreadPoolExecutor
             from paper_2403_11651_gb300 import warm_bench
@@ -442,7 +446,7 @@ def run_ours(a, cfgd):
     # the same iteration written with plain PyTorch eager operations (autograd backward,
     # torch.optim.Adam) on the same GPU and image: what the hand-written kernels gain
     eager = None
-    if rank == 0:
+    if rank == 0 and legs:
         try:
             from paper_2403_11651_gb300.eager_baseline import EagerIteration
             it = EagerIteration(rgb, cfgd, syn.initial_parameters(
@@ -504,7 +508,7 @@ def run_ours(a, cfgd):
         "gpu_launches": kernels * a.steps,
         "time_to_final_rd_s": {"iters": cfgd["total_iters"], "seconds": full_s,
                                "final_hard_rd": {"D": final[0], "R_bpp": final[1],
-                                                 "cost": final[2]}},
+                                                 "cost": final[2]}} if legs else None,
         "bitstream": codec,
         "first_configuration": c1,
         "batch": batch,
@@ -532,6 +536,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--main-only", action="store_true",
+                    help="only the timed iterations and their end-to-end counterpart (for "
+                         "profiling): no batch, warm-start, bitstream, schedule or eager legs")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3

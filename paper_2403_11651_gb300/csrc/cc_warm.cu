@@ -72,17 +72,28 @@ __global__ void __launch_bounds__(256) k_wconv(const float* __restrict__ in, int
   out[q] = relu ? fmaxf(acc, 0.f) : acc;
 }
 
-// squared error of one level: d/dpred = 2 diff / n and a per-block partial sum of
-// diff^2 / n in float-float arithmetic (fixed order)
-__global__ void __launch_bounds__(256) k_wloss(const float* __restrict__ pred,
-                                               const float* __restrict__ target, int n,
+// squared error of the predicted levels 0 .. 4 in one grid: block b belongs to the level
+// l with first[l] <= b < first[l + 1]; d/dpred = 2 diff / n_l and a per-block partial sum of
+// diff^2 / n_l in float-float arithmetic (fixed order)
+struct LossLevels {
+  int first[6];        // first block of each level, first[5] = total
+  long long off[5];    // level offsets in flat latent order
+  int n[5];
+};
+__global__ void __launch_bounds__(256) k_wloss(LossLevels lv, const float* __restrict__ pred,
+                                               const float* __restrict__ target,
                                                float* __restrict__ dpred,
                                                float2* __restrict__ part) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  int l = 0;
+#pragma unroll
+  for (int k = 1; k < 5; ++k) l = (int)blockIdx.x >= lv.first[k] ? k : l;
+  const int n = lv.n[l];
+  const int p = ((int)blockIdx.x - lv.first[l]) * blockDim.x + threadIdx.x;
   float e = 0.f;
   if (p < n) {
-    const float d = pred[p] - target[p];
-    dpred[p] = 2.f * d / (float)n;
+    const long long q = lv.off[l] + p;
+    const float d = pred[q] - target[q];
+    dpred[q] = 2.f * d / (float)n;
     e = d * d / (float)n;
   }
   __shared__ float2 red[256];
@@ -189,8 +200,9 @@ __global__ void __launch_bounds__(256) k_whead_top(const float* __restrict__ act
 // partial sums over a range of kWPix pixels (fixed order inside the block), then
 // k_wsum_parts sums the blocks in block order.
 constexpr int kWPix = 256;
+constexpr int kWPix1 = 64;    // conv 1: eight pixels per thread
 
-// conv 1: block b covers output pixels [b kWPix, (b + 1) kWPix); thread (co = t % 32,
+// conv 1: block b covers output pixels [b kWPix1, (b + 1) kWPix1); thread (co = t % 32,
 // g = t / 32) sums the pixels g, g + 8, ... of the range; part[b][co][k]: k < 27 the
 // weight w[co][ci][tap] (k = ci * 9 + tap), k = 27 the bias
 __global__ void __launch_bounds__(256) k_wc1_wgrad_part(const float* __restrict__ dact, int Ho,
@@ -200,8 +212,8 @@ __global__ void __launch_bounds__(256) k_wc1_wgrad_part(const float* __restrict_
   float acc[28];
 #pragma unroll
   for (int k = 0; k < 28; ++k) acc[k] = 0.f;
-  const int p1 = min(Ho * Wo, (blockIdx.x + 1) * kWPix);
-  for (int p = blockIdx.x * kWPix + g; p < p1; p += 8) {
+  const int p1 = min(Ho * Wo, (blockIdx.x + 1) * kWPix1);
+  for (int p = blockIdx.x * kWPix1 + g; p < p1; p += 8) {
     const int oy = p / Wo, ox = p - oy * Wo;
     const float d = dact[(long long)p * kWCh + co];
     acc[27] += d;
@@ -230,15 +242,15 @@ __global__ void __launch_bounds__(256) k_wc1_wgrad_part(const float* __restrict_
 }
 
 // head 0 (3x3, 3 -> 1, stride 1, on the image): block b covers pixels
-// [b 4 kWPix, (b + 1) 4 kWPix), four per thread; part[b][k]: k < 27 the weight, 27 the bias
+// [b kWPix, (b + 1) kWPix), one per thread; part[b][k]: k < 27 the weight, 27 the bias
 __global__ void __launch_bounds__(256) k_whead0_wgrad_part(const float* __restrict__ dpred,
                                                            const float* __restrict__ x, int H,
                                                            int W, float* __restrict__ part) {
   float acc[28];
 #pragma unroll
   for (int k = 0; k < 28; ++k) acc[k] = 0.f;
-  const int p1 = min(H * W, (blockIdx.x + 1) * 4 * kWPix);
-  for (int p = blockIdx.x * 4 * kWPix + threadIdx.x; p < p1; p += blockDim.x) {
+  const int p1 = min(H * W, (blockIdx.x + 1) * kWPix);
+  for (int p = blockIdx.x * kWPix + threadIdx.x; p < p1; p += blockDim.x) {
     const int y = p / W, xx = p - y * W;
     const float d = dpred[p];
     acc[27] += d;
@@ -267,15 +279,27 @@ __global__ void __launch_bounds__(256) k_whead0_wgrad_part(const float* __restri
   if (threadIdx.x < 28) part[(long long)blockIdx.x * 28 + threadIdx.x] = red[threadIdx.x][0];
 }
 
-// a 1x1 head on a pixel-major activation: block b covers pixels [b kWPix, (b + 1) kWPix);
-// part[b][c]: c < 32 sum_p act[p][c] dpred[p], c = 32 sum_p dpred[p]
-__global__ void __launch_bounds__(256) k_whead_wgrad_part(const float* __restrict__ act,
-                                                          const float* __restrict__ dpred, int n,
-                                                          float* __restrict__ part) {
+// the 1x1 heads of levels 1 .. 4 on their pixel-major activations, in one grid: block b
+// belongs to level i + 1 with first[i] <= b < first[i + 1] and covers that level's pixels
+// [(b - first[i]) kWPix, ...); part[b][c]: c < 32 sum_p act[p][c] dpred[p], c = 32 the sum
+// of dpred
+struct HeadLevels {
+  const float* act[4];
+  const float* dpred[4];
+  int n[4];
+  int first[5];
+};
+__global__ void __launch_bounds__(256) k_whead_wgrad_part(HeadLevels hl, float* __restrict__ part) {
+  int i = 0;
+#pragma unroll
+  for (int k = 1; k < 4; ++k) i = (int)blockIdx.x >= hl.first[k] ? k : i;
+  const float* act = hl.act[i];
+  const float* dpred = hl.dpred[i];
+  const int n = hl.n[i], b = (int)blockIdx.x - hl.first[i];
   const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
   float aw = 0.f, ab = 0.f;
-  const int p1 = min(n, (blockIdx.x + 1) * kWPix);
-  for (int p = blockIdx.x * kWPix + g; p < p1; p += 8) {
+  const int p1 = min(n, (b + 1) * kWPix);
+  for (int p = b * kWPix + g; p < p1; p += 8) {
     const float d = dpred[p];
     aw = fmaf(act[(long long)p * kWCh + c], d, aw);
     ab += d;
@@ -292,15 +316,50 @@ __global__ void __launch_bounds__(256) k_whead_wgrad_part(const float* __restric
   }
 }
 
-// sum over blocks (in block order) of part[b][j], j < ncols; column j goes to dw[j] when
-// j % per < per - 1 (index (j / per) * (per - 1) + j % per), else to db[j / per]
+// sum of part[b][j] over blocks b in [b0, b1) by one warp: lane l adds the blocks
+// b0 + l, b0 + l + 32, ... (eight loads in flight), then the lanes are added in a fixed
+// tree; the result is in lane 0
+__device__ __forceinline__ float warp_col_sum(const float* __restrict__ part, int ncols, int j,
+                                              int b0, int b1) {
+  const int lane = threadIdx.x & 31;
+  float t = 0.f;
+  for (int b = b0 + lane; b < b1; b += 32 * 8) {
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int bb = b + 32 * q;
+      v[q] = bb < b1 ? part[(long long)bb * ncols + j] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += v[q];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  return t;
+}
+
+// the heads' gradients: out[33 i + c] = the sum over level i + 1's blocks of part[b][c]
+// (heads 1 .. 4 are consecutive [w (32), b] groups of the flat parameters); one warp per
+// output
+__global__ void __launch_bounds__(256) k_whead_wsum(HeadLevels hl, const float* __restrict__ part,
+                                                    float* __restrict__ out) {
+  const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (j >= 4 * (kWCh + 1)) return;
+  const int i = j / (kWCh + 1), c = j - i * (kWCh + 1);
+  const float t = warp_col_sum(part, kWCh + 1, c, hl.first[i], hl.first[i + 1]);
+  if ((threadIdx.x & 31) == 0) out[j] = t;
+}
+
+// the sum over blocks of part[b][j], j < ncols, one warp per column (warp_col_sum); column
+// j goes to dw[j] when j % per < per - 1 (index (j / per) * (per - 1) + j % per), else to
+// db[j / per]
 __global__ void __launch_bounds__(256) k_wsum_parts(const float* __restrict__ part, int nblocks,
                                                     int ncols, int per, float* __restrict__ dw,
                                                     float* __restrict__ db) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (j >= ncols) return;
-  float t = 0.f;
-  for (int b = 0; b < nblocks; ++b) t += part[(long long)b * ncols + j];
+  const float t = warp_col_sum(part, ncols, j, 0, nblocks);
+  if ((threadIdx.x & 31) != 0) return;
   const int r = j / per, k = j - r * per;
   if (k < per - 1) dw[r * (per - 1) + k] = t; else db[r] = t;
 }
@@ -338,7 +397,6 @@ constexpr long long kTcWaitBudget = 1ll << 30;   // SM clocks (about half a seco
 struct TcConv {
   const float* in;      // pixel-major input (Hi x Wi x 32) or, for the input gradient,
                         // the output gradient (Ho x Wo x 32)
-  const float* w;       // conv weights [co][ci][ky][kx] (flat parameter layout)
   const float* b;       // conv bias
   int Hi, Wi, Ho, Wo;
   float* out;           // forward: pixel-major activation; input gradient: dact of the input
@@ -350,6 +408,7 @@ struct TcConv {
   const float* dpred;   // input gradient
   const float* act_in;  // input gradient
   int* fault;           // set when the MMA wait gives up
+  const uint8_t* wimg;  // the layer's B operand image (k_wtc_prep), kTcBBytes
 };
 
 // stage 8 BF16 values (16 bytes) at row r, chunk kc of a K-major tile
@@ -357,10 +416,19 @@ __device__ __forceinline__ void tc_put(uint8_t* tile, int r, int kc, const float
   *reinterpret_cast<uint4*>(tile + (r >> 3) * kTcRG + kc * 128 + (r & 7) * 16) = pack_bf16x8(v);
 }
 
-// B for the forward pass: row n = output channel co, k = tap * 32 + ci -> w[co][ci][tap];
-// for the input gradient: row n = input channel ci, k = tap * 32 + co -> w[co][ci][tap]
-template <bool DGRAD>
-__device__ __forceinline__ void stage_weights(uint8_t* sB, const float* __restrict__ w) {
+// The B operands of conv 2 .. 4 as BF16 images in the staged K-major layout, made once
+// per pass from the parameters; a CTA copies its layer's image into shared memory with one
+// bulk copy.  Image 2 (i - 2) is conv i's forward B: row n = output channel co,
+// k = tap * 32 + ci -> w[co][ci][tap]; image 2 (i - 2) + 1 its input-gradient B: row n =
+// input channel ci, k = tap * 32 + co -> w[co][ci][tap].  Grid: one block per image.
+struct WImgArgs {
+  const float* w[3];   // conv 2 .. 4 weights (flat parameter layout)
+  uint8_t* img;        // 6 images of kTcBBytes
+};
+__global__ void __launch_bounds__(256) k_wtc_prep(WImgArgs a) {
+  const int im = blockIdx.x, dgrad = im & 1;
+  const float* __restrict__ w = a.w[im >> 1];
+  uint8_t* dst = a.img + (size_t)im * kTcBBytes;
   for (int c = threadIdx.x; c < kWCh * (kTcK / 8); c += blockDim.x) {
     const int n = c / (kTcK / 8), kc = c - n * (kTcK / 8);
     const int tap = kc >> 2, j0 = (kc & 3) * 8;
@@ -368,10 +436,19 @@ __device__ __forceinline__ void stage_weights(uint8_t* sB, const float* __restri
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int j = j0 + e;   // ci (forward) or co (input gradient)
-      v[e] = DGRAD ? w[(j * kWCh + n) * 9 + tap] : w[(n * kWCh + j) * 9 + tap];
+      v[e] = dgrad ? w[(j * kWCh + n) * 9 + tap] : w[(n * kWCh + j) * 9 + tap];
     }
-    tc_put(sB, n, kc, v);
+    tc_put(dst, n, kc, v);
   }
+}
+
+// one-dimensional bulk copy (TMA) of `bytes` from global to shared memory, completing the
+// transaction bytes on mbar; addresses 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      :: "r"(dst), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(mbar) : "memory");
 }
 
 // one thread issues the 18 MMAs of a tile and commits them to the barrier
@@ -394,11 +471,16 @@ __global__ void __launch_bounds__(128) k_wtc_conv(TcConv a) {
   uint8_t* sA = smem;
   uint8_t* sB = smem + kTcABytes;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kTcABytes + kTcBBytes);
+  uint64_t* wbar = bar + 1;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kTcABytes + kTcBBytes + 16);
   const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) tc_alloc(smem_u32(tslot), 32);
-  if (tid == 0) mbar_init(smem_u32(bar), 1);
-  stage_weights<DGRAD>(sB, a.w);
+  if (tid == 0) {
+    mbar_init(smem_u32(bar), 1);
+    mbar_init(smem_u32(wbar), 1);
+    mbar_expect_tx(smem_u32(wbar), kTcBBytes);
+    bulk_load(smem_u32(sB), a.wimg, kTcBBytes, smem_u32(wbar));
+  }
   // A: row m = this thread's pixel
   const int nq = DGRAD ? a.Hi * a.Wi : a.Ho * a.Wo;   // pixels of the result
   const int q = blockIdx.x * 128 + tid;
@@ -448,7 +530,23 @@ __global__ void __launch_bounds__(128) k_wtc_conv(TcConv a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  if (tid == 0) tile_mma(smem_u32(sA), smem_u32(sB), tmem, smem_u32(bar));
+  // the weights' bulk copy: waited for by the thread that issues the MMAs
+  bool wok = true;
+  if (tid == 0) {
+    wok = mbar_wait(smem_u32(wbar), 0, kTcWaitBudget);
+    if (wok) tile_mma(smem_u32(sA), smem_u32(sB), tmem, smem_u32(bar));
+  }
+  if (__syncthreads_or(wok ? 0 : 1)) {
+    // no MMA was issued: report; the copy gets another bounded wait before the CTA leaves
+    if (tid == 0) {
+      atomicExch(a.fault, 1);
+      mbar_wait(smem_u32(wbar), 0, kTcWaitBudget);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc_dealloc(tmem, 32);
+    return;
+  }
   const bool ok = mbar_wait(smem_u32(bar), 0, kTcWaitBudget);
   tc_fence_after();
   if (__syncthreads_or(ok ? 0 : 1)) {
@@ -621,23 +719,31 @@ __global__ void __launch_bounds__(128) k_wtc_wgrad(const float* __restrict__ in,
   if (warp == 0) tc_dealloc(tmem, 128);
 }
 
-// sum of the wgrad kernel's per-CTA partials in CTA order into the flat gradient:
-// dw[co][ci][tap] from row tap * 32 + ci, db[co] from row 288
+// sum of the wgrad kernel's per-CTA partials in CTA order (eight loads in flight per
+// thread) into the flat gradient: dw[co][ci][tap] from row tap * 32 + ci, db[co] from row 288
 __global__ void __launch_bounds__(256) k_wtc_wreduce(const float* __restrict__ part, int ctas,
                                                      float* __restrict__ dw,
                                                      float* __restrict__ db) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;   // row * 32 + co
   if (i >= kWgRows * kWCh) return;
-  float s = 0.f;
-  for (int c = 0; c < ctas; ++c) s += part[(long long)c * kWgRows * kWCh + i];
+  float t = 0.f;
+  for (int c0 = 0; c0 < ctas; c0 += 8) {
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      v[q] = c0 + q < ctas ? part[(long long)(c0 + q) * kWgRows * kWCh + i] : 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += v[q];
+  }
   const int k = i / kWCh, co = i - k * kWCh;
   if (k < kTcK) {
     const int tap = k / kWCh, ci = k - tap * kWCh;
-    dw[(co * kWCh + ci) * 9 + tap] = s;
+    dw[(co * kWCh + ci) * 9 + tap] = t;
   } else {
-    db[co] = s;
+    db[co] = t;
   }
 }
+
 
 
 }  // namespace
@@ -661,6 +767,7 @@ struct cc_warm {
   float* wpart;             // per-CTA partials of a tensor-core weight gradient
   int wg_ctas = 0;
   int* fault;               // a tensor-core wait gave up
+  uint8_t* wimg;            // BF16 B-operand images of conv 2 .. 4 (k_wtc_prep)
   WarmAdam* adam;           // device
   float lr = -1.f;          // the learning rate in adam->lr
   cudaGraphExec_t pass = nullptr;     // image to planar, forward, loss, gradients
@@ -685,11 +792,11 @@ int wfail(cudaError_t e, const char* what) {
 
 TcConv tc_args(cc_warm* c, int i) {
   TcConv a{};
-  a.w = c->params + c->L.c_w[i];
   a.b = c->params + c->L.c_b[i];
   a.Hi = c->h[i - 1]; a.Wi = c->w[i - 1];
   a.Ho = c->h[i]; a.Wo = c->w[i];
   a.fault = c->fault;
+  a.wimg = c->wimg + (size_t)2 * (i - 2) * kTcBBytes;   // forward; + kTcBBytes: input gradient
   return a;
 }
 
@@ -705,13 +812,20 @@ int warm_forward(cc_warm* c) {
   const WarmLayout& L = c->L;
   float* P = c->params;
   const Geo& g = c->geo;
-  WCK(cudaMemsetAsync(c->pred, 0, (size_t)g.n_lat * sizeof(float), c->st));
+  // levels 5 and 6 of pred stay 0 (zeroed at creation, never written)
   long long fo[kLevels];
   level_offsets(g, fo);
   // level 0: 3x3 stride 1 on the image
   k_wconv<<<blocks((long long)c->H * c->W), 256, 0, c->st>>>(c->x, 3, c->H, c->W, P + L.h_w[0],
                                                              P + L.h_b[0], c->pred + fo[0], 1,
                                                              c->H, c->W, 1, 0);
+  // the tensor-core layers' weights as BF16 operand images
+  {
+    WImgArgs wa;
+    for (int i = 2; i <= 4; ++i) wa.w[i - 2] = P + L.c_w[i];
+    wa.img = c->wimg;
+    k_wtc_prep<<<6, 256, 0, c->st>>>(wa);
+  }
   // conv 1 (FP32) and head 1
   k_wc1_fwd<<<blocks((long long)c->h[1] * c->w[1]), 256, 0, c->st>>>(
       c->x, c->H, c->W, P + L.c_w[1], P + L.c_b[1], P + L.h_w[1], P + L.h_b[1], c->act[1],
@@ -740,26 +854,34 @@ int warm_backward(cc_warm* c, const float* target) {
   float* G = c->grads;
   long long fo[kLevels];
   level_offsets(g, fo);
-  int nb = 0;
+  LossLevels lv;
+  lv.first[0] = 0;
   for (int l = 0; l <= 4; ++l) {
-    const int n = g.h[l] * g.w[l];
-    k_wloss<<<blocks(n), 256, 0, c->st>>>(c->pred + fo[l], target + fo[l], n, c->dpred + fo[l],
-                                          c->part + nb);
-    nb += blocks(n);
+    lv.n[l] = g.h[l] * g.w[l];
+    lv.off[l] = fo[l];
+    lv.first[l + 1] = lv.first[l] + blocks(lv.n[l]);
   }
-  k_wloss_sum<<<1, 256, 0, c->st>>>(c->part, nb, c->loss);
+  k_wloss<<<lv.first[5], 256, 0, c->st>>>(lv, c->pred, target, c->dpred, c->part);
+  k_wloss_sum<<<1, 256, 0, c->st>>>(c->part, lv.first[5], c->loss);
   // level 0 head (3x3 on the image): weight gradient only
   {
-    const int nbk = (c->H * c->W + 4 * kWPix - 1) / (4 * kWPix);
+    const int nbk = (c->H * c->W + kWPix - 1) / kWPix;
     k_whead0_wgrad_part<<<nbk, 256, 0, c->st>>>(c->dpred + fo[0], c->x, c->H, c->W, c->wpart);
-    k_wsum_parts<<<1, 256, 0, c->st>>>(c->wpart, nbk, 28, 28, G + L.h_w[0], G + L.h_b[0]);
+    k_wsum_parts<<<(28 + 7) / 8, 256, 0, c->st>>>(c->wpart, nbk, 28, 28, G + L.h_w[0],
+                                               G + L.h_b[0]);
   }
-  // heads 1 .. 4
-  for (int i = 1; i <= 4; ++i) {
-    const int n = c->h[i] * c->w[i], nbk = (n + kWPix - 1) / kWPix;
-    k_whead_wgrad_part<<<nbk, 256, 0, c->st>>>(c->act[i], c->dpred + fo[i], n, c->wpart);
-    k_wsum_parts<<<1, 256, 0, c->st>>>(c->wpart, nbk, kWCh + 1, kWCh + 1, G + L.h_w[i],
-                                       G + L.h_b[i]);
+  // heads 1 .. 4 (after head 0's sums have read c->wpart: same stream)
+  {
+    HeadLevels hl;
+    hl.first[0] = 0;
+    for (int i = 1; i <= 4; ++i) {
+      hl.act[i - 1] = c->act[i];
+      hl.dpred[i - 1] = c->dpred + fo[i];
+      hl.n[i - 1] = c->h[i] * c->w[i];
+      hl.first[i] = hl.first[i - 1] + (hl.n[i - 1] + kWPix - 1) / kWPix;
+    }
+    k_whead_wgrad_part<<<hl.first[4], 256, 0, c->st>>>(hl, c->wpart);
+    k_whead_wsum<<<(4 * (kWCh + 1) + 7) / 8, 256, 0, c->st>>>(hl, c->wpart, G + L.h_w[1]);
   }
   // conv 4's output gradient comes from head 4 only
   {
@@ -783,15 +905,16 @@ int warm_backward(cc_warm* c, const float* target) {
     a.hw = P + L.h_w[i - 1];
     a.dpred = c->dpred + fo[i - 1];
     a.act_in = c->act[i - 1];
+    a.wimg += kTcBBytes;
     const int ni = c->h[i - 1] * c->w[i - 1];
     k_wtc_conv<true><<<(ni + 127) / 128, 128, kTcSmem, c->st>>>(a);
   }
   // conv 1's weight gradient (its input, the image, needs none)
   {
-    const int nbk = (c->h[1] * c->w[1] + kWPix - 1) / kWPix;
+    const int nbk = (c->h[1] * c->w[1] + kWPix1 - 1) / kWPix1;
     k_wc1_wgrad_part<<<nbk, 256, 0, c->st>>>(c->dact[1], c->h[1], c->w[1], c->x, c->H, c->W,
                                              c->wpart);
-    k_wsum_parts<<<(kWCh * 28 + 255) / 256, 256, 0, c->st>>>(c->wpart, nbk, kWCh * 28, 28,
+    k_wsum_parts<<<(kWCh * 28 + 7) / 8, 256, 0, c->st>>>(c->wpart, nbk, kWCh * 28, 28,
                                                             G + L.c_w[1], G + L.c_b[1]);
   }
   WCK(cudaGetLastError());
@@ -929,13 +1052,16 @@ int cc_warm_create(int H, int W, const float* params, void* stream, cc_warm** ou
   const size_t o_part = take((size_t)c->n_part * sizeof(float2));
   const size_t o_loss = take(sizeof(double));
   const size_t o_adam = take(sizeof(WarmAdam));
+  const size_t o_wimg = take((size_t)6 * kTcBBytes);
   const size_t o_fault = take(sizeof(int));
   c->wg_ctas = 64;
   // partial sums: the tensor-core weight gradients', conv 1's, head 0's and the heads'
-  const size_t nb1 = ((size_t)c->h[1] * c->w[1] + kWPix - 1) / kWPix;
-  const size_t nb0 = ((size_t)H * W + 4 * kWPix - 1) / (4 * kWPix);
+  const size_t nb1 = ((size_t)c->h[1] * c->w[1] + kWPix1 - 1) / kWPix1;
+  const size_t nb0 = ((size_t)H * W + kWPix - 1) / kWPix;
+  size_t nbh = 0;   // blocks of the heads' partial sums, levels 1 .. 4
+  for (int i = 1; i <= 4; ++i) nbh += ((size_t)c->h[i] * c->w[i] + kWPix - 1) / kWPix;
   const size_t wpart_floats = std::max({(size_t)c->wg_ctas * kWgRows * kWCh, nb1 * kWCh * 28,
-                                        nb0 * 28, nb1 * (kWCh + 1)});
+                                        nb0 * 28, nbh * (kWCh + 1)});
   const size_t o_wpart = take(wpart_floats * sizeof(float));
   cudaError_t e = cudaMalloc(&c->mem, off);
   if (e != cudaSuccess) { delete c; return CC_ENOMEM; }
@@ -950,6 +1076,7 @@ int cc_warm_create(int H, int W, const float* params, void* stream, cc_warm** ou
   c->img = (uint8_t*)(b + o_img); c->part = (float2*)(b + o_part);
   c->loss = (double*)(b + o_loss); c->fault = (int*)(b + o_fault);
   c->adam = (WarmAdam*)(b + o_adam);
+  c->wimg = (uint8_t*)(b + o_wimg);
   c->wpart = (float*)(b + o_wpart);
   if ((e = cudaFuncSetAttribute(k_wtc_conv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kTcSmem)) != cudaSuccess ||

@@ -145,11 +145,61 @@ def parser():
                          "plain for the whole schedule, and warm-started until every image "
                          "reaches its plain run's final cost")
     ap.add_argument("--lanes", type=int, default=8)
+    ap.add_argument("--step-time", action="store_true",
+                    help="only time the predictor's training step at --size (inputs in device "
+                         "memory, the loss written to device memory)")
     return ap
+
+
+def step_time(S: int, steps: int = 200, warmup: int = 10) -> dict:
+    """Device time per training step of the predictor on one S x S image: image, target and
+    loss in device memory, CUDA events around `steps` queued steps."""
+    import torch
+    n_lat = sum(h * w for h, w in cc.level_shapes(S, S))
+    rgb = torch.from_numpy(syn.synthetic_image(S, S, 1)).cuda()
+    tgt = torch.from_numpy(np.random.default_rng(1).normal(0, 1.0, n_lat)
+                           .astype(np.float32)).cuda()
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    w = cc.cc_warm_create(S, S, syn.warm_initial_parameters(1), stream)
+    try:
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                cc.cc_warm_train_step(w, rgb, tgt, 1e-3, loss_out=loss)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                cc.cc_warm_train_step(w, rgb, tgt, 1e-3, loss_out=loss)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        gflop = 2.0 * warm_macs_per_step(S) / 1e9
+        return {"size": S, "step_ms": ms, "gflop_per_step": gflop,
+                "tflops": gflop / ms, "loss": float(loss.cpu()[0])}
+    finally:
+        cc.cc_warm_free(w)
+
+
+def warm_macs_per_step(S: int) -> int:
+    """Multiply-adds of one training step at S x S: conv 1 forward and weight gradient,
+    conv 2 .. 4 forward, input and weight gradients, head 0 forward and weight gradient,
+    heads 1 .. 4 forward, weight and input gradients."""
+    h = [S]
+    for _ in range(4):
+        h.append((h[-1] + 1) // 2)
+    px = [x * x for x in h]
+    macs = 2 * px[1] * 32 * 27                      # conv 1: forward, weight gradient
+    macs += sum(3 * px[i] * 32 * 288 for i in (2, 3, 4))
+    macs += 2 * px[0] * 27                          # head 0
+    macs += sum(3 * px[i] * 32 for i in (1, 2, 3, 4))
+    return macs
 
 
 def main(argv=None):
     a = parser().parse_args(argv)
+    if a.step_time:
+        print(json.dumps(step_time(a.size)))
+        return
     # the synthetic images are made on the host cores while the GPU overfits (a spawned
     # pool, started before this process's first CUDA call)
     pool = ProcessPoolExecutor(max_workers=max(1, min(8, (os.cpu_count() or 2) - 2)),
