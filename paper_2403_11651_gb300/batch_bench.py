@@ -2,7 +2,7 @@
 other, printed as one JSON line.
 
     python -m paper_2403_11651_gb300.batch_bench [--images 32] [--iters 300] [--lanes 8]
-                                                 [--max-pixels N] [--autotune]
+                                                 [--max-pixels N] [--autotune] [--small t300]
 
 Workload: images of sizes drawn uniformly from 256x256, 512x768, 768x512, 1024x1024 and
 1920x1080 (seeded synthetic images), half with the first configuration's decoder and half
@@ -26,13 +26,15 @@ from . import synthetic as syn
 SIZES = [(256, 256), (512, 768), (768, 512), (1024, 1024), (1080, 1920)]
 
 
-def workload(n: int, seed: int, max_pixels: int = 0):
+def workload(n: int, seed: int, max_pixels: int = 0, small: str = "c1"):
+    """n seeded images: sizes uniform over SIZES (at most max_pixels each), even-numbered
+    images with the decoder of configuration `small`, odd ones with the 2300-MAC one."""
     rng = np.random.default_rng(seed)
     sizes = [s for s in SIZES if not max_pixels or s[0] * s[1] <= max_pixels]
     items = []
     for k in range(n):
         H, W = sizes[int(rng.integers(len(sizes)))]
-        d = dict(cc.load_config("c1" if k % 2 == 0 else "c2"))
+        d = dict(cc.load_config(small if k % 2 == 0 else "c2"))
         d["lam"] = float(math.exp(rng.uniform(math.log(1e-4), math.log(1e-2))))
         cfg = cc.make_config(d, seed=k)
         init = cc.flatten_params(syn.initial_parameters(syn.ArchSizes.from_config(d), k), cfg)
@@ -61,8 +63,11 @@ def main(argv=None):
     ap.add_argument("--max-pixels", type=int, default=0,
                     help="only the sizes with at most this many pixels (0: all)")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--small", default="c1",
+                    help="configuration of the even-numbered images' decoder (c1: the first "
+                         "configuration; t300: Table 1's 300-MAC row)")
     a = ap.parse_args(argv)
-    items = workload(a.images, a.seed, a.max_pixels)
+    items = workload(a.images, a.seed, a.max_pixels, a.small)
     sizes = [s for s in SIZES if not a.max_pixels or s[0] * s[1] <= a.max_pixels]
     px = sum(rgb.shape[0] * rgb.shape[1] for rgb, _, _, _ in items)
     lanes, chunk, tune = a.lanes, 16, None
@@ -76,7 +81,7 @@ def main(argv=None):
     small = [i for i, (rgb, _, _, _) in enumerate(items) if rgb.shape[0] * rgb.shape[1] <= 512 * 768]
     print(json.dumps({
         "workload": f"{a.images} images ({px / 1e6:.1f} Mpixel), sizes in {sizes}, "
-                    f"half first configuration / half 2300-MAC, lambda log-uniform "
+                    f"half {a.small} / half 2300-MAC decoders, lambda log-uniform "
                     f"[1e-4, 1e-2], {a.iters} iterations each",
         "plain_s": t_plain, "batched_s": t_batch, "lanes": lanes, "chunk": chunk,
         "autotune": tune,
