@@ -207,3 +207,26 @@ def test_bf16_predictor_close_to_fp64():
         d = float((got[l] - ref[l]).abs().max())
         scale = float(ref[l].abs().max())
         assert 0.0 < d < 2e-2 * scale, (l, d, scale)
+
+
+def test_step_work_count_matches_the_oracle_layers():
+    """warm_bench's multiply-add count of a training step equals the one read off the
+    oracle's layers: every convolution's output elements times its inputs per output, once
+    forward, once for the weight gradient and once for the input gradient where one is
+    needed (not into the image)."""
+    from paper_2403_11651_gb300 import warm_bench
+    for S in (64, 100, 512):
+        x = torch.zeros(3, S, S, dtype=torch.float64)
+        P = _params(0)
+        a = x.unsqueeze(0)
+        total = 0
+        # head 0: forward and weight gradient
+        total += 2 * S * S * 27
+        for i in (1, 2, 3, 4):
+            w = P[f"c{i}.w"]
+            a = torch.relu(torch.nn.functional.conv2d(a, w, P[f"c{i}.b"], stride=2, padding=1))
+            per_out = w.shape[1] * 9
+            passes = 2 if i == 1 else 3
+            total += passes * a.numel() * per_out
+            total += 3 * a.shape[2] * a.shape[3] * w.shape[0]    # head i: forward, weight, input
+        assert warm_bench.warm_macs_per_step(S) == total, S
