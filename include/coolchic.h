@@ -21,10 +21,11 @@
  *   - the context owns its device memory (or borrows a caller workspace) until cc_free;
  *   - all GPU work of a context is issued on the stream given to cc_init_image;
  *   - the contexts of one device share its constant-memory weight banks (every pass loads
- *     its own weights first): passes of two contexts must not overlap in time, so issue
- *     them on one stream or synchronise between them.  The banks belong to the loaded
- *     library: contexts created through separately loaded copies of it have their own
- *     and may run concurrently;
+ *     its own weights first).  The library orders their passes itself: each call that
+ *     runs passes makes its stream wait for the previous such call on the device, from
+ *     any context, stream or host thread, so passes of two contexts never overlap on the
+ *     GPU (they run one after another).  The banks belong to the loaded library: contexts
+ *     created through separately loaded copies of it have their own and run concurrently;
  *   - the images are 8-bit RGB, row-major, channels last (H x W x 3); the library uses
  *     x = v / 255 in float32.
  *

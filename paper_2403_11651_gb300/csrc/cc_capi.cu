@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <cstdlib>
+#include <mutex>
 #include <vector>
 
 #include "cc_internal.cuh"
@@ -27,6 +28,40 @@ int fail_cuda(cudaError_t e, const char* what) {
     cudaError_t e_ = (call);                             \
     if (e_ != cudaSuccess) return fail_cuda(e_, #call);  \
   } while (0)
+
+// The contexts of one device share this library's __constant__ weight banks.  Every
+// operation that loads the banks and runs kernels on them takes a turn: under one
+// process-wide lock its stream waits for the end of the previous turn on the device (an
+// event), the work is enqueued, and the event is recorded after it.  Turns of one device
+// thus run one after another on the GPU, whatever streams and host threads issue them.
+std::mutex g_turn_mu;
+std::vector<cudaEvent_t> g_turn_end;   // per device
+
+class BankTurn {
+ public:
+  BankTurn(int dev, cudaStream_t s) : lock_(g_turn_mu), dev_(dev), s_(s) {
+    if ((int)g_turn_end.size() <= dev) g_turn_end.resize(dev + 1, nullptr);
+    if (g_turn_end[dev]) err_ = cudaStreamWaitEvent(s, g_turn_end[dev], 0);
+  }
+  // records the end of the turn after the work enqueued so far on the stream
+  cudaError_t end() {
+    if (err_ != cudaSuccess || ended_) return err_;
+    ended_ = true;
+    if (!g_turn_end[dev_])
+      err_ = cudaEventCreateWithFlags(&g_turn_end[dev_], cudaEventDisableTiming);
+    if (err_ == cudaSuccess) err_ = cudaEventRecord(g_turn_end[dev_], s_);
+    return err_;
+  }
+  cudaError_t status() const { return err_; }
+  ~BankTurn() { end(); }
+
+ private:
+  std::lock_guard<std::mutex> lock_;
+  int dev_;
+  cudaStream_t s_;
+  cudaError_t err_ = cudaSuccess;
+  bool ended_ = false;
+};
 
 #define CKE(call)                                        \
   do {                                                   \
@@ -771,6 +806,8 @@ int cc_encode_iters(cc_ctx* c, int n_iters) {
     int e = build_graph(c, 16, &c->g16);
     if (e) return e;
   }
+  BankTurn turn(c->dev, c->st);
+  CK(turn.status());
   int left = n_iters;
   while (left >= 16) {
     CK(cudaGraphLaunch(c->g16, c->st));
@@ -780,6 +817,7 @@ int cc_encode_iters(cc_ctx* c, int n_iters) {
     CK(cudaGraphLaunch(c->g1, c->st));
     --left;
   }
+  CK(turn.end());
   c->iter += n_iters;
   return CC_OK;
 }
@@ -843,7 +881,12 @@ int cc_debug_inject(cc_ctx* c, int fault, int at_iteration) {
 int cc_rd_cost(cc_ctx* c, int hard_round, double* D, double* R_bpp, double* cost) {
   if (!c) return CC_EINVAL;
   CK(cudaSetDevice(c->dev));
-  CK(enqueue_pass(c, c->st, hard_round ? 1 : 3, false, false, nullptr, false));
+  {
+    BankTurn turn(c->dev, c->st);
+    CK(turn.status());
+    CK(enqueue_pass(c, c->st, hard_round ? 1 : 3, false, false, nullptr, false));
+    CK(turn.end());
+  }
   IterScalars h;
   int e = sync_copy_scalars(c, &h);
   if (e) return e;
@@ -858,13 +901,18 @@ int cc_decode(cc_ctx* c, float* rgb_out_hwc) {
   CK(cudaSetDevice(c->dev));
   const Arch& a = c->arch;
   const size_t HW = (size_t)c->HW;
-  CK(syn_upload(c->params, c->lay, a, c->syn_image, c->st));
-  CK(quantize_launch(c->geo, c->y, c->yhat, c->yhat_bord, c->noise, 1, c->sc, c->ste_start, c->cfg.seed, -1,
-                     0.f, nullptr, c->st));
-  CK(up_forward(a, c->geo, c->yhat, c->up, c->grid_syn, c->st));
-  CK(syn_forward(a, c->geo, c->yhat, c->up, c->x, c->hbuf, c->dhbuf + (size_t)a.NR * 3 * HW,
-                 c->part_d, c->part_conv, c->grid_tiles, c->st));
-  CK(syn_decode(a, c->geo, c->hbuf + (size_t)a.NR * 3 * HW, c->dz, c->st));
+  {
+    BankTurn turn(c->dev, c->st);
+    CK(turn.status());
+    CK(syn_upload(c->params, c->lay, a, c->syn_image, c->st));
+    CK(quantize_launch(c->geo, c->y, c->yhat, c->yhat_bord, c->noise, 1, c->sc, c->ste_start,
+                       c->cfg.seed, -1, 0.f, nullptr, c->st));
+    CK(up_forward(a, c->geo, c->yhat, c->up, c->grid_syn, c->st));
+    CK(syn_forward(a, c->geo, c->yhat, c->up, c->x, c->hbuf, c->dhbuf + (size_t)a.NR * 3 * HW,
+                   c->part_d, c->part_conv, c->grid_tiles, c->st));
+    CK(syn_decode(a, c->geo, c->hbuf + (size_t)a.NR * 3 * HW, c->dz, c->st));
+    CK(turn.end());
+  }
   CK(cudaMemcpyAsync(rgb_out_hwc, c->dz, 3 * HW * sizeof(float), cudaMemcpyDefault, c->st));
   CK(cudaStreamSynchronize(c->st));
   return CC_OK;
@@ -884,7 +932,12 @@ int cc_forward_backward(cc_ctx* c, const float* noise_override, int hard, float*
   } else if (hard == 0) {
     qmode = 3;
   }
-  CK(enqueue_pass(c, c->st, qmode, true, false, c->grad_scratch, false));
+  {
+    BankTurn turn(c->dev, c->st);
+    CK(turn.status());
+    CK(enqueue_pass(c, c->st, qmode, true, false, c->grad_scratch, false));
+    CK(turn.end());
+  }
   if (grads_out)
     CK(cudaMemcpyAsync(grads_out, c->grad_scratch,
                        (size_t)(c->geo.n_lat + c->lay.total) * sizeof(float), cudaMemcpyDefault,
@@ -991,7 +1044,13 @@ int cc_profile_phases(cc_ctx* c, int reps, float* ms_out) {
   double acc[CC_N_PHASES] = {0};
   int rc = CC_OK;
   for (int r = 0; r < reps && rc == CC_OK; ++r) {
-    cudaError_t e = enqueue_pass(c, c->st, 0, true, true, nullptr, true, ev);
+    cudaError_t e;
+    {
+      BankTurn turn(c->dev, c->st);
+      e = turn.status();
+      if (e == cudaSuccess) e = enqueue_pass(c, c->st, 0, true, true, nullptr, true, ev);
+      if (e == cudaSuccess) e = turn.end();
+    }
     if (e != cudaSuccess) { rc = fail_cuda(e, "profiled pass"); break; }
     if ((e = cudaEventSynchronize(ev[7])) != cudaSuccess) { rc = fail_cuda(e, "event sync"); break; }
     for (int k = 0; k < CC_N_PHASES; ++k) {
@@ -1196,8 +1255,14 @@ int cc_write_bitstream(cc_ctx* c, uint8_t* out, size_t capacity, size_t* nbytes)
   CK(d_off.alloc((size_t)cg.rows * sizeof(long long)));
   CK(cudaMemcpyAsync(d_tab.p, tab.data(), codec_table_bytes(), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(d_flag.p, 0, sizeof(int), st));
-  CK(codec_upload_arm(q.data(), a.N, a.NL, st));
-  CK(codec_symbols(cg, c->geo, c->y, c->offs, a.N, a.NL, d_sym.as<int2>(), d_flag.as<int>(), st));
+  {
+    BankTurn turn(c->dev, st);
+    CK(turn.status());
+    CK(codec_upload_arm(q.data(), a.N, a.NL, st));
+    CK(codec_symbols(cg, c->geo, c->y, c->offs, a.N, a.NL, d_sym.as<int2>(), d_flag.as<int>(),
+                     st));
+    CK(turn.end());
+  }
   CK(codec_encode_rows(cg, d_sym.as<int2>(), d_tab.as<uint16_t>(), d_rows.as<uint8_t>(),
                        d_len.as<int>(), d_flag.as<int>(), st));
   std::vector<int> len((size_t)cg.rows);
@@ -1307,12 +1372,17 @@ int cc_decode_bitstream(const uint8_t* bs, size_t nbytes, void* cuda_stream, flo
   CK(cudaMemcpyAsync(d_off.p, row_off.data(), row_off.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_len.p, row_len.data(), row_len.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(d_flag.p, 0, sizeof(int), st));
-  CK(codec_upload_arm(q.data(), a.N, a.NL, st));
-  CK(cudaEventRecord(c->ev_a0, st));
-  CK(codec_decode(cg, a.N, a.NL, d_tab.as<uint16_t>(), d_bytes.as<uint8_t>(),
-                  d_off.as<long long>(), d_len.as<int>(), d_planes.as<int>(), d_prog.as<int>(),
-                  d_flag.as<int>(), st));
-  CK(cudaEventRecord(c->ev_a1, st));
+  {
+    BankTurn turn(c->dev, st);
+    CK(turn.status());
+    CK(codec_upload_arm(q.data(), a.N, a.NL, st));
+    CK(cudaEventRecord(c->ev_a0, st));
+    CK(codec_decode(cg, a.N, a.NL, d_tab.as<uint16_t>(), d_bytes.as<uint8_t>(),
+                    d_off.as<long long>(), d_len.as<int>(), d_planes.as<int>(),
+                    d_prog.as<int>(), d_flag.as<int>(), st));
+    CK(cudaEventRecord(c->ev_a1, st));
+    CK(turn.end());
+  }
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

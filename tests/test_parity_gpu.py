@@ -495,3 +495,39 @@ def test_arm_wait_timeout_rolls_back():
     finally:
         a.close()
         b.close()
+
+
+def test_contexts_on_two_streams_take_turns():
+    """Two contexts of one loaded library share its constant-memory weight banks.  Driven
+    alternately on two streams with no host synchronisation between the calls, each must
+    give the losses and state it gives alone: the library orders their passes on the GPU."""
+    d1, d2 = config_dict("c2", total_iters=200), config_dict("c1", total_iters=200)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    rgb1, rgb2 = syn.synthetic_image(64, 96, 21), syn.synthetic_image(48, 80, 22)
+
+    def make(d, rgb, H, W, seed, stream):
+        cfg = cc.make_config(d, seed=seed)
+        init = cc.flatten_params(syn.initial_parameters(syn.ArchSizes.from_config(d), seed), cfg)
+        return cc.cc_init_image(cfg, rgb, H, W, init, stream)
+
+    alone = []
+    for d, rgb, H, W, seed in ((d1, rgb1, 64, 96, 21), (d2, rgb2, 48, 80, 22)):
+        ctx = make(d, rgb, H, W, seed, None)
+        try:
+            cc.cc_encode_iters(ctx, 40)
+            alone.append((cc.cc_get_losses(ctx, 0, 40), cc.cc_get_state(ctx)))
+        finally:
+            cc.cc_free(ctx)
+    a = make(d1, rgb1, 64, 96, 21, s1)
+    b = make(d2, rgb2, 48, 80, 22, s2)
+    try:
+        for _ in range(5):
+            cc.cc_encode_iters(a, 8)
+            cc.cc_encode_iters(b, 8)
+        torch.cuda.synchronize()
+        for ctx, (losses, state) in ((a, alone[0]), (b, alone[1])):
+            assert np.array_equal(cc.cc_get_losses(ctx, 0, 40), losses)
+            assert cc.cc_get_state(ctx) == state
+    finally:
+        cc.cc_free(a)
+        cc.cc_free(b)
