@@ -941,7 +941,7 @@ __global__ void __launch_bounds__(256, 2) k_conv3_pair(ConvArgs a) {
 
 struct Syn1x1Args {
   const float* feat[kLevels];   // level-0 latents, then the upsampled planes of l = 1..6
-  float* h2;                    // [3][HW] output of the C-3 layer (forward)
+  float* h2;                    // [3][HW] output of the C-3 layer (written forward, read backward)
   const float* dhout;           // [3][HW] output gradient of 3x3 layer 0 (backward)
   const float* dz0;             // [3][HW] its pre-activation gradient (backward)
   float* dfeat[kLevels];        // gradient of each feature plane
@@ -960,6 +960,8 @@ struct Syn1x1W {
   static constexpr int M = C / 2;   // channel pairs
 };
 
+// Two pixels per thread (p and p + 256 of the block's 512), so that every weight pair
+// loaded from the bank serves both.
 template <int C>
 __global__ void __launch_bounds__(256) k_syn1x1_fwd(Syn1x1Args a) {
   pdl_wait();
@@ -969,26 +971,43 @@ __global__ void __launch_bounds__(256) k_syn1x1_fwd(Syn1x1Args a) {
   const float2* wa = reinterpret_cast<const float2*>(c_syn + Wt::WAT);   // [7][M]
   const float2* ba = reinterpret_cast<const float2*>(c_syn + Wt::BA);    // [M]
   const float2* wb = reinterpret_cast<const float2*>(c_syn + Wt::WBR);   // [3][M]
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.HW; p += gridDim.x * blockDim.x) {
-    float2 fd[kLevels];
+  for (int p0 = blockIdx.x * 512 + threadIdx.x; p0 < a.HW; p0 += gridDim.x * 512) {
+    const int p1 = p0 + 256;
+    const bool v1 = p1 < a.HW;
+    float2 fa[kLevels], fb[kLevels];
 #pragma unroll
     for (int k = 0; k < kLevels; ++k) {
-      const float v = __ldg(a.feat[k] + p);
-      fd[k] = make_float2(v, v);
+      const float u = __ldg(a.feat[k] + p0), v = v1 ? __ldg(a.feat[k] + p1) : 0.f;
+      fa[k] = make_float2(u, u);
+      fb[k] = make_float2(v, v);
     }
-    float2 z2p[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    float2 za2[3], zb2[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) za2[j] = zb2[j] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-      float2 z = ba[m];
+      float2 za = ba[m], zb = za;
 #pragma unroll
-      for (int k = 0; k < kLevels; ++k) z = __ffma2_rn(wa[k * M + m], fd[k], z);
-      const float2 h = make_float2(fmaxf(z.x, 0.f), fmaxf(z.y, 0.f));
+      for (int k = 0; k < kLevels; ++k) {
+        const float2 w = wa[k * M + m];
+        za = __ffma2_rn(w, fa[k], za);
+        zb = __ffma2_rn(w, fb[k], zb);
+      }
+      const float2 ha = make_float2(fmaxf(za.x, 0.f), fmaxf(za.y, 0.f));
+      const float2 hb = make_float2(fmaxf(zb.x, 0.f), fmaxf(zb.y, 0.f));
 #pragma unroll
-      for (int j = 0; j < 3; ++j) z2p[j] = __ffma2_rn(wb[j * M + m], h, z2p[j]);
+      for (int j = 0; j < 3; ++j) {
+        const float2 w = wb[j * M + m];
+        za2[j] = __ffma2_rn(w, ha, za2[j]);
+        zb2[j] = __ffma2_rn(w, hb, zb2[j]);
+      }
     }
 #pragma unroll
-    for (int j = 0; j < 3; ++j)
-      a.h2[j * a.HW + p] = fmaxf(c_syn[Wt::BB + j] + (z2p[j].x + z2p[j].y), 0.f);
+    for (int j = 0; j < 3; ++j) {
+      const float bj = c_syn[Wt::BB + j];
+      a.h2[j * a.HW + p0] = fmaxf(bj + (za2[j].x + za2[j].y), 0.f);
+      if (v1) a.h2[j * a.HW + p1] = fmaxf(bj + (zb2[j].x + zb2[j].y), 0.f);
+    }
   }
 }
 
@@ -1045,8 +1064,6 @@ __global__ void __launch_bounds__(256, 2) k_syn1x1_bwd(Syn1x1Args a) {
   const float2* wa = reinterpret_cast<const float2*>(c_syn + Wt::WAT);
   const float2* ba = reinterpret_cast<const float2*>(c_syn + Wt::BA);
   const float2* wb = reinterpret_cast<const float2*>(c_syn + Wt::WBR);
-  const float2* wab = reinterpret_cast<const float2*>(c_synb + Wt::WAT);
-  const float2* wbb = reinterpret_cast<const float2*>(c_synb + Wt::WBR);
   const int tx = tid & 31, ty = tid >> 5;
   HaloPlan hp;
   hp.init(a.t.H, a.t.W);
@@ -1079,52 +1096,52 @@ __global__ void __launch_bounds__(256, 2) k_syn1x1_bwd(Syn1x1Args a) {
       for (int j = 0; j < 3; ++j) dh2[j] = __ldg(a.dhout + j * a.HW + p);
       conv_adjoint<0>(dh2, s_halo, ty, tx, y, x, y0, x0, a.t.H, a.t.W);
     }
-    // recompute z1, h1, z2
+    // dz2 = [h2 > 0] dh2: the ReLU mask of the C-3 layer from the forward's stored output
+    float dz2[3] = {0.f, 0.f, 0.f};
+    if (valid) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) dz2[j] = __ldg(a.h2 + j * a.HW + p) > 0.f ? dh2[j] : 0.f;
+    }
+    *reinterpret_cast<float4*>(s_dz2 + tid * SD) = make_float4(dz2[0], dz2[1], dz2[2], 0.f);
+    // One loop over the hidden channel pairs: recompute z1 and h1 = ReLU(z1), then
+    // dh1 = W_b^T dz2, dz1 = [z1 > 0] dh1 and df += W_a^T dz1, each W_a pair loaded once for
+    // both of its uses; h1 and dz1 go to the staged rows of the weight gradient.
     float2 fd[kLevels];
 #pragma unroll
     for (int k = 0; k < kLevels; ++k) fd[k] = make_float2(f[k], f[k]);
-    float2 h1[M];
-    float2 z2p[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-      float2 z = ba[m];
-#pragma unroll
-      for (int k = 0; k < kLevels; ++k) z = __ffma2_rn(wa[k * M + m], fd[k], z);
-      h1[m] = make_float2(fmaxf(z.x, 0.f), fmaxf(z.y, 0.f));
-#pragma unroll
-      for (int j = 0; j < 3; ++j) z2p[j] = __ffma2_rn(wb[j * M + m], h1[m], z2p[j]);
-    }
-    float* hrow = s_h1 + tid * SZ;
-#pragma unroll
-    for (int m = 0; m < M; m += 2)
-      *reinterpret_cast<float4*>(hrow + 2 * m) =
-          valid ? make_float4(h1[m].x, h1[m].y, h1[m + 1].x, h1[m + 1].y)
-                : make_float4(0.f, 0.f, 0.f, 0.f);
-    *reinterpret_cast<float4*>(hrow + C) = make_float4(valid ? 1.f : 0.f, 0.f, 0.f, 0.f);
-    float dz2[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      dz2[j] = c_syn[Wt::BB + j] + (z2p[j].x + z2p[j].y) > 0.f ? dh2[j] : 0.f;
-    *reinterpret_cast<float4*>(s_dz2 + tid * SD) = make_float4(dz2[0], dz2[1], dz2[2], 0.f);
-    // backward: dh1 = W_b^T dz2, dz1 = [h1 > 0] dh1, df = W_a^T dz1
     const float2 g0 = make_float2(dz2[0], dz2[0]), g1 = make_float2(dz2[1], dz2[1]),
                  g2 = make_float2(dz2[2], dz2[2]);
     float2 dfp[kLevels];
 #pragma unroll
     for (int k = 0; k < kLevels; ++k) dfp[k] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-      float2 dh = __fmul2_rn(wbb[m], g0);
-      dh = __ffma2_rn(wbb[M + m], g1, dh);
-      dh = __ffma2_rn(wbb[2 * M + m], g2, dh);
-      h1[m] = make_float2(h1[m].x > 0.f ? dh.x : 0.f, h1[m].y > 0.f ? dh.y : 0.f);   // dz1
-#pragma unroll
-      for (int k = 0; k < kLevels; ++k) dfp[k] = __ffma2_rn(wab[k * M + m], h1[m], dfp[k]);
-    }
+    float* hrow = s_h1 + tid * SZ;
     float* zrow = s_dz1 + tid * SZ;
 #pragma unroll
-    for (int m = 0; m < M; m += 2)
-      *reinterpret_cast<float4*>(zrow + 2 * m) = make_float4(h1[m].x, h1[m].y, h1[m + 1].x, h1[m + 1].y);
+    for (int m = 0; m < M; m += 2) {
+      float2 hh[2], dd[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        float2 w[kLevels];
+#pragma unroll
+        for (int k = 0; k < kLevels; ++k) w[k] = wa[k * M + m + u];
+        float2 z = ba[m + u];
+#pragma unroll
+        for (int k = 0; k < kLevels; ++k) z = __ffma2_rn(w[k], fd[k], z);
+        const float2 h = make_float2(fmaxf(z.x, 0.f), fmaxf(z.y, 0.f));
+        float2 dh = __fmul2_rn(wb[m + u], g0);
+        dh = __ffma2_rn(wb[M + m + u], g1, dh);
+        dh = __ffma2_rn(wb[2 * M + m + u], g2, dh);
+        const float2 dz = make_float2(h.x > 0.f ? dh.x : 0.f, h.y > 0.f ? dh.y : 0.f);
+#pragma unroll
+        for (int k = 0; k < kLevels; ++k) dfp[k] = __ffma2_rn(w[k], dz, dfp[k]);
+        hh[u] = h;
+        dd[u] = dz;
+      }
+      *reinterpret_cast<float4*>(hrow + 2 * m) =
+          valid ? make_float4(hh[0].x, hh[0].y, hh[1].x, hh[1].y) : make_float4(0.f, 0.f, 0.f, 0.f);
+      *reinterpret_cast<float4*>(zrow + 2 * m) = make_float4(dd[0].x, dd[0].y, dd[1].x, dd[1].y);
+    }
+    *reinterpret_cast<float4*>(hrow + C) = make_float4(valid ? 1.f : 0.f, 0.f, 0.f, 0.f);
     float* frow = s_f + tid * SF;
 #pragma unroll
     for (int k = 0; k < kLevels; ++k) frow[k] = f[k];
@@ -1204,8 +1221,8 @@ __global__ void __launch_bounds__(256, 2) k_syn1x1_bwd(Syn1x1Args a) {
 // ------------------------------------------------------------------ drivers
 
 template <int C>
-static cudaError_t syn1x1_fwd_t(const Syn1x1Args& a, int grid, cudaStream_t st) {
-  return launch_k(k_syn1x1_fwd<C>, dim3(grid), dim3(256), 0, st, a);
+static cudaError_t syn1x1_fwd_t(const Syn1x1Args& a, cudaStream_t st) {
+  return launch_k(k_syn1x1_fwd<C>, dim3((a.HW + 511) / 512), dim3(256), 0, st, a);
 }
 
 template <int C>
@@ -1258,9 +1275,9 @@ cudaError_t syn_forward(const Arch& ar, const Geo& g, const float* yhat, const U
   s.h2 = hbuf;
   cudaError_t e;
   switch (ar.C) {
-    case 8: e = syn1x1_fwd_t<8>(s, grid, st); break;
-    case 16: e = syn1x1_fwd_t<16>(s, grid, st); break;
-    case 40: e = syn1x1_fwd_t<40>(s, grid, st); break;
+    case 8: e = syn1x1_fwd_t<8>(s, st); break;
+    case 16: e = syn1x1_fwd_t<16>(s, st); break;
+    case 40: e = syn1x1_fwd_t<40>(s, st); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
@@ -1314,6 +1331,7 @@ cudaError_t syn_backward(const Arch& ar, const Geo& g, const float* yhat, const 
     s.dhout = dxhat;
     s.dz0 = dxhat;
   }
+  s.h2 = hbuf;
   s.dfeat[0] = gsyn + g.off[0];
   for (int l = 1; l < kLevels; ++l) s.dfeat[l] = up.dplane[l][0];
   s.part = part_syn;
