@@ -2,9 +2,9 @@
 iteration runs in the CUDA library).
 
 The decoder weights of a context live in the library's ``__constant__`` banks, which all
-contexts of one loaded library share, so their passes must not overlap in time.  Each
-separately loaded copy of the shared library registers its own device module and so owns
-its own banks.  ``BatchOverfitter`` deals the images to ``lanes`` copies: lane i's images
+contexts of one loaded library share, so the library runs their passes one after another
+on the GPU.  Each separately loaded copy of the shared library registers its own device
+module and so owns its own banks, and contexts of different copies run concurrently.  ``BatchOverfitter`` deals the images to ``lanes`` copies: lane i's images
 take turns on the lane's stream (``chunk`` iterations each), and the lanes run
 concurrently -- small, latency-bound images then share the GPU instead of each leaving it
 mostly idle.  Every image runs exactly the iterations it would run alone (same kernels,
